@@ -1,0 +1,643 @@
+/*
+ * ps_oracle.c -- plain, slow, FP64 CPU definition of PlanarSplatting's
+ * differentiable planar-primitive rendering (arxiv 2412.03451, Sec. 3.2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA path is
+ * checked against.  Only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark may load it.  It shares no code, header, table or helper
+ * with the CUDA library, and the CUDA library never calls it.
+ *
+ * Every function brute-forces the definition: every plane is tested at every
+ * pixel, there is no tiling, no culling and no reordering beyond what the
+ * paper states.  Build with -ffp-contract=off so that no multiply-add is
+ * fused: the binning function below must give the same integers as any other
+ * implementation of the same strict formula.
+ *
+ * Conventions (readings of the paper, listed with reasons in the design
+ * notes of the repository):
+ *   plane k: center p (3), quaternion q = (w,x,y,z) (4), radii
+ *            r = (r^x+, r^x-, r^y+, r^y-) (4)                     [Eq. 1]
+ *   v^x, v^y, n = columns 0,1,2 of R(q/|q|), Hamilton convention [Eq. 2-3]
+ *   camera v: world->camera [R|t] row-major 3x4, intrinsics (fx,fy,cx,cy),
+ *             OpenCV frame; pixel (i,j) ray d = ((i+.5-cx)/fx, (j+.5-cy)/fy, 1)
+ *   intersection depth t = ((p_c - o).n_c)/(d.n_c) with o = 0; since d_z = 1
+ *             t is the camera z-depth                              [Eq. 4]
+ *   P_X = (t d - p_c).v^x_c, P_Y likewise                           [Eq. 6]
+ *   w_X = min(1, 2 sigmoid(5 lambda (r_X - |P_X|))), r_X = r^x+ if P_X > 0
+ *             else r^x-; w_Y likewise                               [Eq. 7-8]
+ *   w = w_X if w_X < w_Y else w_Y                                   [Eq. 9]
+ *   keep w >= w_min (1e-4) and z_near < t < z_far and |d.n_c| > 1e-6,
+ *   sort by (t, plane id), keep the first M (30)          [Sec. 3.2, Blending]
+ *   D = sum T_j w_j t_j, N = sum T_j w_j n_c,j, T_j = prod_{i<j} (1 - w_i)
+ *                                                                  [Eq. 11-13]
+ *   loss = a_cos sum |1 - N.N*| + a_l1n sum ||N - N*||_1 + a_depth sum |D - D*|
+ *             over pixels with D* > 0                              [Eq. 14]
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAXCAND 4096
+
+/* ------------------------------------------------------------------------ */
+/* Plane frame: Eq. 2-3.  Hamilton rotation matrix of the unit quaternion.   */
+/* Returns 0 if |q| is zero or not finite.                                   */
+static int plane_axes(const double* q, double* qn_out, double qhat[4],
+                      double vx[3], double vy[3], double n[3])
+{
+    double s = sqrt(((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3]);
+    if (!(s > 0.0) || !isfinite(s)) return 0;
+    double w = q[0] / s, x = q[1] / s, y = q[2] / s, z = q[3] / s;
+    if (qn_out) *qn_out = s;
+    if (qhat) { qhat[0] = w; qhat[1] = x; qhat[2] = y; qhat[3] = z; }
+    /* R = [[1-2(y^2+z^2), 2(xy-wz), 2(xz+wy)],
+            [2(xy+wz), 1-2(x^2+z^2), 2(yz-wx)],
+            [2(xz-wy), 2(yz+wx), 1-2(x^2+y^2)]]                             */
+    vx[0] = 1.0 - 2.0 * (y * y + z * z);
+    vx[1] = 2.0 * (x * y + w * z);
+    vx[2] = 2.0 * (x * z - w * y);
+    vy[0] = 2.0 * (x * y - w * z);
+    vy[1] = 1.0 - 2.0 * (x * x + z * z);
+    vy[2] = 2.0 * (y * z + w * x);
+    n[0] = 2.0 * (x * z + w * y);
+    n[1] = 2.0 * (y * z - w * x);
+    n[2] = 1.0 - 2.0 * (x * x + y * y);
+    return 1;
+}
+
+static void rot_apply(const double* Rt /* 3x4 row major */, const double a[3], double out[3])
+{
+    for (int i = 0; i < 3; ++i)
+        out[i] = (Rt[4 * i + 0] * a[0] + Rt[4 * i + 1] * a[1]) + Rt[4 * i + 2] * a[2];
+}
+
+static void rot_apply_T(const double* Rt, const double a[3], double out[3])
+{
+    for (int i = 0; i < 3; ++i)
+        out[i] = (Rt[0 + i] * a[0] + Rt[4 + i] * a[1]) + Rt[8 + i] * a[2];
+}
+
+static double dot3(const double a[3], const double b[3])
+{
+    return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+/* Camera-frame quantities of one plane in one view. */
+typedef struct {
+    int ok;
+    double qs, qhat[4];
+    double vx[3], vy[3], n[3];       /* world axes (Eq. 2-3)  */
+    double pc[3], vxc[3], vyc[3], nc[3];
+    double r[4];                     /* radii after the single-radii option */
+    double pcn;                      /* |p_c|, scale of the FP32 noise model */
+} plane_cam;
+
+static void plane_to_cam(const double* p, const double* q, const double* r,
+                         const double* Rt, int single_radii, plane_cam* o)
+{
+    o->ok = plane_axes(q, &o->qs, o->qhat, o->vx, o->vy, o->n);
+    if (!o->ok) return;
+    double tmp[3];
+    rot_apply(Rt, p, tmp);
+    for (int i = 0; i < 3; ++i) o->pc[i] = tmp[i] + Rt[4 * i + 3];
+    rot_apply(Rt, o->vx, o->vxc);
+    rot_apply(Rt, o->vy, o->vyc);
+    rot_apply(Rt, o->n, o->nc);
+    o->pcn = sqrt(dot3(o->pc, o->pc));
+    o->r[0] = r[0]; o->r[1] = single_radii ? r[0] : r[1];
+    o->r[2] = r[2]; o->r[3] = single_radii ? r[2] : r[3];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binning specification (screen bounds of the expanded rectangle).          */
+/* The rectangle is widened by delta on every side; delta is the margin at   */
+/* which 2 sigmoid(-5 lambda delta) = w_min, so every (pixel, plane) pair    */
+/* that survives the w >= w_min filter of Sec. 3.2 lies inside it.  The quad */
+/* is clipped to z >= z_near, projected, and its pixel bbox, padded by one   */
+/* pixel and clamped to the image, is divided by the tile size.  The depth   */
+/* key is the smallest z of the clipped polygon: a lower bound on the depth  */
+/* t of every surviving intersection.  Plain + - * / sqrt in FP64, no FMA.   */
+/* rect = (tx0, ty0, tx1, ty1) inclusive; culled planes get (0,0,-1,-1).     */
+void or_bin_records(int K, int V,
+                    const double* center, const double* quat, const double* radii,
+                    const double* w2c, const double* intr, int H, int W,
+                    int tile_w, int tile_h, double delta, double z_near, double z_far,
+                    int single_radii, int* rect, double* key, float* key_f32)
+{
+    for (int v = 0; v < V; ++v) {
+        const double* Rt = w2c + 12 * v;
+        double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
+        double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
+        for (int k = 0; k < K; ++k) {
+            int* rc = rect + 4 * ((long)v * K + k);
+            rc[0] = 0; rc[1] = 0; rc[2] = -1; rc[3] = -1;
+            key[(long)v * K + k] = INFINITY;
+            key_f32[(long)v * K + k] = INFINITY;
+            plane_cam pc;
+            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, single_radii, &pc);
+            if (!pc.ok) continue;
+            double exp_ = pc.r[0] + delta, exm = pc.r[1] + delta;
+            double eyp = pc.r[2] + delta, eym = pc.r[3] + delta;
+            /* corners in order (+x,+y), (-x,+y), (-x,-y), (+x,-y) */
+            double ax[4] = {exp_, -exm, -exm, exp_};
+            double ay[4] = {eyp, eyp, -eym, -eym};
+            double C[4][3];
+            for (int c = 0; c < 4; ++c)
+                for (int i = 0; i < 3; ++i)
+                    C[c][i] = (pc.pc[i] + ax[c] * pc.vxc[i]) + ay[c] * pc.vyc[i];
+            /* Sutherland-Hodgman against the half space z >= z_near */
+            double P[8][3];
+            int np = 0;
+            for (int e = 0; e < 4; ++e) {
+                const double* a = C[e];
+                const double* b = C[(e + 1) & 3];
+                int ina = a[2] >= z_near, inb = b[2] >= z_near;
+                if (ina) { P[np][0] = a[0]; P[np][1] = a[1]; P[np][2] = a[2]; ++np; }
+                if (ina != inb) {
+                    double s = (z_near - a[2]) / (b[2] - a[2]);
+                    P[np][0] = a[0] + s * (b[0] - a[0]);
+                    P[np][1] = a[1] + s * (b[1] - a[1]);
+                    P[np][2] = z_near;
+                    ++np;
+                }
+            }
+            if (np == 0) continue;
+            double kmin = P[0][2];
+            for (int i = 1; i < np; ++i) if (P[i][2] < kmin) kmin = P[i][2];
+            if (!(kmin < z_far)) continue;
+            double umin = 0, umax = 0, vmin = 0, vmax = 0;
+            int bad = 0;
+            for (int i = 0; i < np; ++i) {
+                double u = fx * (P[i][0] / P[i][2]) + cx;
+                double vv = fy * (P[i][1] / P[i][2]) + cy;
+                if (isnan(u) || isnan(vv)) bad = 1;
+                if (i == 0) { umin = umax = u; vmin = vmax = vv; }
+                else {
+                    if (u < umin) umin = u;
+                    if (u > umax) umax = u;
+                    if (vv < vmin) vmin = vv;
+                    if (vv > vmax) vmax = vv;
+                }
+            }
+            if (bad) continue;
+            double px0 = floor(umin) - 1.0, px1 = floor(umax) + 1.0;
+            double py0 = floor(vmin) - 1.0, py1 = floor(vmax) + 1.0;
+            if (px1 < 0.0 || px0 > (double)(W - 1) || py1 < 0.0 || py0 > (double)(H - 1)) continue;
+            if (px0 < 0.0) px0 = 0.0;
+            if (py0 < 0.0) py0 = 0.0;
+            if (px1 > (double)(W - 1)) px1 = (double)(W - 1);
+            if (py1 > (double)(H - 1)) py1 = (double)(H - 1);
+            rc[0] = (int)px0 / tile_w; rc[1] = (int)py0 / tile_h;
+            rc[2] = (int)px1 / tile_w; rc[3] = (int)py1 / tile_h;
+            key[(long)v * K + k] = kmin;
+            /* largest float not above kmin (round toward -inf) */
+            float kf = (float)kmin;
+            if ((double)kf > kmin) kf = nextafterf(kf, -INFINITY);
+            key_f32[(long)v * K + k] = kf;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-(pixel, plane) evaluation of Eq. 4 and Eq. 6-9.                       */
+typedef struct {
+    int k;            /* plane index */
+    double t, w;      /* depth and weight */
+    double m, mX, mY; /* margins r - |P| */
+    double PX, PY, den;
+    int branchX;      /* 1 if w came from the X side (w_X < w_Y) */
+} cand;
+
+static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+/* w_X or w_Y of Eq. 7-8 with the clamp to 1 */
+static double side_weight(double lambda, double m)
+{
+    double w = 2.0 * sigmoid(5.0 * lambda * m);
+    return w < 1.0 ? w : 1.0;
+}
+
+/* Evaluates plane pc at ray d.  Returns 1 and fills c when t is in range and
+   the ray is not grazing; the weight filter is applied by the caller.       */
+static int eval_pair(const plane_cam* pc, const double d[3], double lambda,
+                     double z_near, double z_far, cand* c)
+{
+    double den = dot3(d, pc->nc);
+    if (!(fabs(den) > 1e-6)) return 0;
+    double t = dot3(pc->pc, pc->nc) / den;
+    if (!(t > z_near && t < z_far)) return 0;
+    double x[3] = {t * d[0] - pc->pc[0], t * d[1] - pc->pc[1], t * d[2] - pc->pc[2]};
+    double PX = dot3(x, pc->vxc), PY = dot3(x, pc->vyc);
+    double rX = PX > 0.0 ? pc->r[0] : pc->r[1];
+    double rY = PY > 0.0 ? pc->r[2] : pc->r[3];
+    double mX = rX - fabs(PX), mY = rY - fabs(PY);
+    double wX = side_weight(lambda, mX), wY = side_weight(lambda, mY);
+    c->t = t; c->den = den; c->PX = PX; c->PY = PY; c->mX = mX; c->mY = mY;
+    if (wX < wY) { c->w = wX; c->branchX = 1; c->m = mX; }
+    else { c->w = wY; c->branchX = 0; c->m = mY; }
+    return 1;
+}
+
+static int cand_cmp(const void* a, const void* b)
+{
+    const cand* x = (const cand*)a;
+    const cand* y = (const cand*)b;
+    if (x->t < y->t) return -1;
+    if (x->t > y->t) return 1;
+    return (x->k > y->k) - (x->k < y->k);
+}
+
+typedef struct {
+    double lambda, w_min, z_near, z_far;
+    int M, single_radii;
+} or_set;
+
+/* Gathers, filters and sorts the candidates of one pixel.  Returns the
+   number of candidates (before the top-M cut).  Also reports the smallest
+   distance of any in-range plane's margin to the filter edge -delta, the
+   closest pair of sorted depths, etc., for the conditioning flags.          */
+static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], const or_set* S,
+                            double delta, double eta, cand* out, int* near_filter)
+{
+    int nc = 0;
+    *near_filter = 0;
+    for (int k = 0; k < K; ++k) {
+        if (!pcs[k].ok) continue;
+        cand c;
+        if (!eval_pair(&pcs[k], d, S->lambda, S->z_near, S->z_far, &c)) continue;
+        double eps = eta * (1.0 + fabs(c.t) + pcs[k].pcn);
+        if (fabs(c.m + delta) < eps) *near_filter = 1;
+        if (fabs(c.t - S->z_near) < eps || fabs(c.t - S->z_far) < eps) *near_filter = 1;
+        if (!(c.w >= S->w_min)) continue;
+        c.k = k;
+        if (nc < OR_MAXCAND) out[nc++] = c;
+    }
+    qsort(out, nc, sizeof(cand), cand_cmp);
+    return nc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward render (Eq. 11-13), brute force over all planes.                  */
+/* Outputs per pixel: depth, normal (camera frame), alpha = sum T_j w_j,     */
+/* n_sel = number composited (<= M), n_cand = number of (plane) candidates   */
+/* with w >= w_min and t in range (the algorithmic pair count), and ill:     */
+/*   bit 0: FP32 rounding (a margin error of eta (1 + t + |p_c|)) could      */
+/*          move D or N by more than tol_d/2 or tol_n/2, or flip the filter, */
+/*          the depth order or the z range;                                  */
+/*   bit 1: bit 0, or the min / sign branch of a weighted, partly            */
+/*          transparent entry is within eta of flipping (gradients only).    */
+/* Rows [row0, row1) of every view are rendered; others are left untouched.  */
+void or_render(int K, int V, const double* center, const double* quat, const double* radii,
+               const double* w2c, const double* intr, int H, int W,
+               double lambda, double w_min, double z_near, double z_far, int M, int single_radii,
+               double delta, double eta, double tol_d, double tol_n, int row0, int row1,
+               double* depth, double* normal, double* alpha, int* n_sel, int* n_cand, int* ill)
+{
+    or_set S = {lambda, w_min, z_near, z_far, M, single_radii};
+    plane_cam* pcs = (plane_cam*)malloc(sizeof(plane_cam) * (size_t)(K > 0 ? K : 1));
+    for (int v = 0; v < V; ++v) {
+        const double* Rt = w2c + 12 * v;
+        for (int k = 0; k < K; ++k)
+            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, single_radii, &pcs[k]);
+        double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
+        double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
+#pragma omp parallel
+        {
+            cand* cs = (cand*)malloc(sizeof(cand) * OR_MAXCAND);
+            double* Tj = (double*)malloc(sizeof(double) * (size_t)(M + 1));
+#pragma omp for schedule(dynamic, 1)
+            for (int j = row0; j < row1; ++j) {
+                for (int i = 0; i < W; ++i) {
+                    long pix = ((long)v * H + j) * W + i;
+                    double d[3] = {((double)i + 0.5 - cx) / fx, ((double)j + 0.5 - cy) / fy, 1.0};
+                    int near_filter;
+                    int nc = pixel_candidates(pcs, K, d, &S, delta, eta, cs, &near_filter);
+                    int ns = nc < M ? nc : M;
+                    double T = 1.0, D = 0.0, N[3] = {0, 0, 0}, A = 0.0;
+                    for (int s = 0; s < ns; ++s) {
+                        const plane_cam* p = &pcs[cs[s].k];
+                        double tw = T * cs[s].w;
+                        Tj[s] = T;
+                        D += tw * cs[s].t;
+                        N[0] += tw * p->nc[0]; N[1] += tw * p->nc[1]; N[2] += tw * p->nc[2];
+                        A += tw;
+                        T = T * (1.0 - cs[s].w);
+                    }
+                    /* conditioning */
+                    int bad_val = near_filter, bad_grad = 0;
+                    for (int s = 0; s + 1 < nc && s < M; ++s) {
+                        double e = eta * (1.0 + fabs(cs[s + 1].t));
+                        if (cs[s + 1].t - cs[s].t < e) bad_val = 1;
+                    }
+                    /* sensitivity of D, N to the margins: back-to-front sums */
+                    double Ab = 0.0, Bb[3] = {0, 0, 0};
+                    double sD = 0.0, sN[3] = {0, 0, 0};
+                    for (int s = ns - 1; s >= 0; --s) {
+                        const plane_cam* p = &pcs[cs[s].k];
+                        double w = cs[s].w, t = cs[s].t, m = cs[s].m;
+                        double e = eta * (1.0 + fabs(t) + p->pcn);
+                        double slope;
+                        if (fabs(m) < e) slope = 2.5 * lambda;      /* max of dw/dm near the kink */
+                        else if (m < 0.0) {
+                            double sg = sigmoid(5.0 * lambda * m);
+                            slope = 10.0 * lambda * sg * (1.0 - sg);
+                        } else slope = 0.0;
+                        double gD = Tj[s] * (t - Ab);
+                        sD += fabs(gD) * slope * e;
+                        for (int c = 0; c < 3; ++c) sN[c] += fabs(Tj[s] * (p->nc[c] - Bb[c])) * slope * e;
+                        if (Tj[s] > 0.0 && m < e) {
+                            if (fabs(cs[s].mX - cs[s].mY) < e) bad_grad = 1;
+                            double Pa = cs[s].branchX ? cs[s].PX : cs[s].PY;
+                            if (fabs(Pa) < e) bad_grad = 1;
+                        }
+                        Ab = w * t + (1.0 - w) * Ab;
+                        for (int c = 0; c < 3; ++c) Bb[c] = w * p->nc[c] + (1.0 - w) * Bb[c];
+                    }
+                    if (sD > 0.5 * tol_d) bad_val = 1;
+                    if (sN[0] > 0.5 * tol_n || sN[1] > 0.5 * tol_n || sN[2] > 0.5 * tol_n) bad_val = 1;
+                    depth[pix] = D;
+                    normal[3 * pix + 0] = N[0]; normal[3 * pix + 1] = N[1]; normal[3 * pix + 2] = N[2];
+                    if (alpha) alpha[pix] = A;
+                    if (n_sel) n_sel[pix] = ns;
+                    if (n_cand) n_cand[pix] = nc;
+                    if (ill) ill[pix] = (bad_val ? 3 : 0) | (bad_grad ? 2 : 0);
+                }
+            }
+            free(cs);
+            free(Tj);
+        }
+    }
+    free(pcs);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Render loss, Eq. 14, with its gradient with respect to D and N.           */
+/* Pixels with gt_depth <= 0 are not supervised.  view_sums[v] =             */
+/* (sum |1 - N.N*|, sum ||N - N*||_1, sum |D - D*|, number of valid pixels). */
+/* Returns the total loss.  sgn(0) = 0.                                       */
+static double sgn(double x) { return (x > 0.0) - (x < 0.0); }
+
+double or_loss(int V, int H, int W, const double* depth, const double* normal,
+               const double* gt_depth, const double* gt_normal,
+               double a_cos, double a_l1n, double a_depth,
+               double* dLdD, double* dLdN, double* view_sums)
+{
+    double total = 0.0;
+    long HW = (long)H * W;
+    for (int v = 0; v < V; ++v) {
+        double sc = 0, sl = 0, sd = 0, cnt = 0;
+        for (long p = 0; p < HW; ++p) {
+            long pix = (long)v * HW + p;
+            const double* N = normal + 3 * pix;
+            const double* Ns = gt_normal + 3 * pix;
+            if (!(gt_depth[pix] > 0.0)) {
+                dLdD[pix] = 0.0;
+                dLdN[3 * pix] = dLdN[3 * pix + 1] = dLdN[3 * pix + 2] = 0.0;
+                continue;
+            }
+            double cosv = 1.0 - dot3(N, Ns);
+            double l1 = fabs(N[0] - Ns[0]) + fabs(N[1] - Ns[1]) + fabs(N[2] - Ns[2]);
+            double dd = depth[pix] - gt_depth[pix];
+            sc += fabs(cosv); sl += l1; sd += fabs(dd); cnt += 1.0;
+            dLdD[pix] = a_depth * sgn(dd);
+            for (int c = 0; c < 3; ++c)
+                dLdN[3 * pix + c] = -a_cos * sgn(cosv) * Ns[c] + a_l1n * sgn(N[c] - Ns[c]);
+        }
+        if (view_sums) {
+            view_sums[4 * v + 0] = sc; view_sums[4 * v + 1] = sl;
+            view_sums[4 * v + 2] = sd; view_sums[4 * v + 3] = cnt;
+        }
+        total += a_cos * sc + a_l1n * sl + a_depth * sd;
+    }
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backward: gradient of sum_pixels (dLdD . D + dLdN . N) with respect to    */
+/* every plane's center, quaternion and radii.  Per pixel the composited     */
+/* list is rebuilt, the adjoint of Eq. 11-13 is taken back to front          */
+/*   A_{n+1} = 0, A_j = w_j t_j + (1 - w_j) A_{j+1}                          */
+/*   dD/dw_j = T_j (t_j - A_{j+1}),  dD/dt_j = T_j w_j,  dN/dn_j = T_j w_j   */
+/* (no division by 1 - w), and chained through Eq. 9, 7-8, 6, 4 and 2-3 to   */
+/* the world parameters.  The clamp min(1, .) has derivative 0 at m >= 0.   */
+void or_backward(int K, int V, const double* center, const double* quat, const double* radii,
+                 const double* w2c, const double* intr, int H, int W,
+                 double lambda, double w_min, double z_near, double z_far, int M, int single_radii,
+                 const double* dLdD, const double* dLdN,
+                 double* g_center, double* g_quat, double* g_radii)
+{
+    or_set S = {lambda, w_min, z_near, z_far, M, single_radii};
+    memset(g_center, 0, sizeof(double) * 3 * (size_t)K);
+    memset(g_quat, 0, sizeof(double) * 4 * (size_t)K);
+    memset(g_radii, 0, sizeof(double) * 4 * (size_t)K);
+    plane_cam* pcs = (plane_cam*)malloc(sizeof(plane_cam) * (size_t)(K > 0 ? K : 1));
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    double* acc = (double*)calloc((size_t)nthreads * 11 * (size_t)K, sizeof(double));
+    /* per-view camera-frame gradient accumulators, chained to world per view */
+    for (int v = 0; v < V; ++v) {
+        const double* Rt = w2c + 12 * v;
+        for (int k = 0; k < K; ++k)
+            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, single_radii, &pcs[k]);
+        double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
+        double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
+#pragma omp parallel
+        {
+            int tid = 0;
+#ifdef _OPENMP
+            tid = omp_get_thread_num();
+#endif
+            double* my = acc + (size_t)tid * 11 * K;
+            cand* cs = (cand*)malloc(sizeof(cand) * OR_MAXCAND);
+            double* Tj = (double*)malloc(sizeof(double) * (size_t)(M + 1));
+#pragma omp for schedule(static)
+            for (int j = 0; j < H; ++j) {
+                for (int i = 0; i < W; ++i) {
+                    long pix = ((long)v * H + j) * W + i;
+                    double gD = dLdD[pix];
+                    const double* gN = dLdN + 3 * pix;
+                    if (gD == 0.0 && gN[0] == 0.0 && gN[1] == 0.0 && gN[2] == 0.0) continue;
+                    double d[3] = {((double)i + 0.5 - cx) / fx, ((double)j + 0.5 - cy) / fy, 1.0};
+                    int nf;
+                    int nc = pixel_candidates(pcs, K, d, &S, 0.0, 0.0, cs, &nf);
+                    int ns = nc < M ? nc : M;
+                    double T = 1.0;
+                    for (int s = 0; s < ns; ++s) { Tj[s] = T; T = T * (1.0 - cs[s].w); }
+                    double A = 0.0, B[3] = {0, 0, 0};
+                    for (int s = ns - 1; s >= 0; --s) {
+                        const cand* c = &cs[s];
+                        const plane_cam* p = &pcs[c->k];
+                        double w = c->w, t = c->t;
+                        double gw = Tj[s] * (gD * (t - A) + gN[0] * (p->nc[0] - B[0]) +
+                                             gN[1] * (p->nc[1] - B[1]) + gN[2] * (p->nc[2] - B[2]));
+                        double gt = Tj[s] * w * gD;
+                        double gnc[3] = {Tj[s] * w * gN[0], Tj[s] * w * gN[1], Tj[s] * w * gN[2]};
+                        A = w * t + (1.0 - w) * A;
+                        for (int q = 0; q < 3; ++q) B[q] = w * p->nc[q] + (1.0 - w) * B[q];
+                        /* Eq. 7-9: w = min(1, 2 sigmoid(5 lambda m)) on the active side */
+                        double gm = 0.0;
+                        if (c->m < 0.0) {
+                            double sg = sigmoid(5.0 * lambda * c->m);
+                            gm = gw * 10.0 * lambda * sg * (1.0 - sg);
+                        }
+                        double gr[4] = {0, 0, 0, 0};
+                        double gPX = 0.0, gPY = 0.0;
+                        if (c->branchX) {
+                            /* m_X = r_X - |P_X| */
+                            if (c->PX > 0.0) gr[0] += gm; else gr[1] += gm;
+                            gPX = -gm * sgn(c->PX);
+                        } else {
+                            if (c->PY > 0.0) gr[2] += gm; else gr[3] += gm;
+                            gPY = -gm * sgn(c->PY);
+                        }
+                        if (single_radii) { gr[0] += gr[1]; gr[1] = 0.0; gr[2] += gr[3]; gr[3] = 0.0; }
+                        /* Eq. 6: P = (t d - p_c) . v_c */
+                        double x[3] = {t * d[0] - p->pc[0], t * d[1] - p->pc[1], t * d[2] - p->pc[2]};
+                        double gpc[3], gvxc[3], gvyc[3];
+                        gt += gPX * dot3(d, p->vxc) + gPY * dot3(d, p->vyc);
+                        for (int q = 0; q < 3; ++q) {
+                            gpc[q] = -gPX * p->vxc[q] - gPY * p->vyc[q];
+                            gvxc[q] = gPX * x[q];
+                            gvyc[q] = gPY * x[q];
+                        }
+                        /* Eq. 4: t = (p_c . n_c) / (d . n_c) */
+                        double den = c->den;
+                        for (int q = 0; q < 3; ++q) {
+                            gpc[q] += gt * p->nc[q] / den;
+                            gnc[q] += gt * (p->pc[q] - t * d[q]) / den;
+                        }
+                        /* camera frame -> world: p_c = R p + t, a_c = R a */
+                        double gp[3], gvx[3], gvy[3], gn[3];
+                        rot_apply_T(Rt, gpc, gp);
+                        rot_apply_T(Rt, gvxc, gvx);
+                        rot_apply_T(Rt, gvyc, gvy);
+                        rot_apply_T(Rt, gnc, gn);
+                        /* Eq. 2-3: columns of the Hamilton matrix of qhat */
+                        double w_ = p->qhat[0], xq = p->qhat[1], yq = p->qhat[2], zq = p->qhat[3];
+                        /* G[i][c]: gradient w.r.t. R_ic, column c = (vx, vy, n)[c] */
+                        double G[3][3];
+                        for (int q = 0; q < 3; ++q) { G[q][0] = gvx[q]; G[q][1] = gvy[q]; G[q][2] = gn[q]; }
+                        double dRw[3][3] = {{0, -2 * zq, 2 * yq}, {2 * zq, 0, -2 * xq}, {-2 * yq, 2 * xq, 0}};
+                        double dRx[3][3] = {{0, 2 * yq, 2 * zq}, {2 * yq, -4 * xq, -2 * w_}, {2 * zq, 2 * w_, -4 * xq}};
+                        double dRy[3][3] = {{-4 * yq, 2 * xq, 2 * w_}, {2 * xq, 0, 2 * zq}, {-2 * w_, 2 * zq, -4 * yq}};
+                        double dRz[3][3] = {{-4 * zq, -2 * w_, 2 * xq}, {2 * w_, -4 * zq, 2 * yq}, {2 * xq, 2 * yq, 0}};
+                        double gqh[4] = {0, 0, 0, 0};
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) {
+                                gqh[0] += G[a][b] * dRw[a][b];
+                                gqh[1] += G[a][b] * dRx[a][b];
+                                gqh[2] += G[a][b] * dRy[a][b];
+                                gqh[3] += G[a][b] * dRz[a][b];
+                            }
+                        /* qhat = q / |q| */
+                        double proj = gqh[0] * w_ + gqh[1] * xq + gqh[2] * yq + gqh[3] * zq;
+                        double gq[4] = {(gqh[0] - w_ * proj) / p->qs, (gqh[1] - xq * proj) / p->qs,
+                                        (gqh[2] - yq * proj) / p->qs, (gqh[3] - zq * proj) / p->qs};
+                        double* o = my + 11 * (size_t)c->k;
+                        for (int q = 0; q < 3; ++q) o[q] += gp[q];
+                        for (int q = 0; q < 4; ++q) o[3 + q] += gq[q];
+                        for (int q = 0; q < 4; ++q) o[7 + q] += gr[q];
+                    }
+                }
+            }
+            free(cs);
+            free(Tj);
+        }
+    }
+    for (int tid = 0; tid < nthreads; ++tid) {
+        const double* my = acc + (size_t)tid * 11 * K;
+        for (int k = 0; k < K; ++k) {
+            for (int q = 0; q < 3; ++q) g_center[3 * k + q] += my[11 * k + q];
+            for (int q = 0; q < 4; ++q) g_quat[4 * k + q] += my[11 * k + 3 + q];
+            for (int q = 0; q < 4; ++q) g_radii[4 * k + q] += my[11 * k + 7 + q];
+        }
+    }
+    free(acc);
+    free(pcs);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact ray caster of hard rectangles: nearest plane whose rectangle        */
+/* (|P_X| <= r_X, |P_Y| <= r_Y, one-sided radii by sign) the pixel ray hits  */
+/* with z_near < t < z_far.  Used to make ground-truth depth and normal      */
+/* maps of synthetic rooms.  Pixels that hit nothing get depth 0, normal 0   */
+/* and plane_id -1.                                                          */
+void or_raycast(int K, int V, const double* center, const double* quat, const double* radii,
+                const double* w2c, const double* intr, int H, int W, double z_near, double z_far,
+                double* depth, double* normal, int* plane_id)
+{
+    plane_cam* pcs = (plane_cam*)malloc(sizeof(plane_cam) * (size_t)(K > 0 ? K : 1));
+    for (int v = 0; v < V; ++v) {
+        const double* Rt = w2c + 12 * v;
+        for (int k = 0; k < K; ++k)
+            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, 0, &pcs[k]);
+        double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
+        double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int j = 0; j < H; ++j) {
+            for (int i = 0; i < W; ++i) {
+                long pix = ((long)v * H + j) * W + i;
+                double d[3] = {((double)i + 0.5 - cx) / fx, ((double)j + 0.5 - cy) / fy, 1.0};
+                double best = INFINITY;
+                int bk = -1;
+                for (int k = 0; k < K; ++k) {
+                    const plane_cam* p = &pcs[k];
+                    if (!p->ok) continue;
+                    double den = dot3(d, p->nc);
+                    if (!(fabs(den) > 1e-6)) continue;
+                    double t = dot3(p->pc, p->nc) / den;
+                    if (!(t > z_near && t < z_far)) continue;
+                    double x[3] = {t * d[0] - p->pc[0], t * d[1] - p->pc[1], t * d[2] - p->pc[2]};
+                    double PX = dot3(x, p->vxc), PY = dot3(x, p->vyc);
+                    double rX = PX > 0.0 ? p->r[0] : p->r[1];
+                    double rY = PY > 0.0 ? p->r[2] : p->r[3];
+                    if (fabs(PX) > rX || fabs(PY) > rY) continue;
+                    if (t < best || (t == best && k < bk)) { best = t; bk = k; }
+                }
+                if (bk < 0) {
+                    depth[pix] = 0.0;
+                    normal[3 * pix] = normal[3 * pix + 1] = normal[3 * pix + 2] = 0.0;
+                } else {
+                    depth[pix] = best;
+                    for (int c = 0; c < 3; ++c) normal[3 * pix + c] = pcs[bk].nc[c];
+                }
+                if (plane_id) plane_id[pix] = bk;
+            }
+        }
+    }
+    free(pcs);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adam (Kingma & Ba), bias-corrected, as used in Sec. 3.3 with lr = 1e-3.   */
+/* After the update, values below clamp_min are raised to it (NaN: none).    */
+void or_adam(long n, double* param, const double* grad, double* m, double* v,
+             double lr, double b1, double b2, double eps, int step, double clamp_min)
+{
+    double bc1 = 1.0 - pow(b1, (double)step);
+    double bc2 = 1.0 - pow(b2, (double)step);
+    for (long i = 0; i < n; ++i) {
+        double g = grad[i];
+        m[i] = b1 * m[i] + (1.0 - b1) * g;
+        v[i] = b2 * v[i] + (1.0 - b2) * g * g;
+        double mh = m[i] / bc1, vh = v[i] / bc2;
+        param[i] -= lr * mh / (sqrt(vh) + eps);
+        if (!isnan(clamp_min) && param[i] < clamp_min) param[i] = clamp_min;
+    }
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
