@@ -1,0 +1,509 @@
+#!/usr/bin/env python3
+"""Throughput of PlanarSplatting's forward + backward plane splatting on GB300.
+
+Workload (the paper-scale single-scene configuration): a synthetic 8x10x3 m
+room with furniture, 2,000 ground-truth rectangles, 64 views at 640x480
+(fx = fy = 500) on a smooth trajectory; 3,000 planes initialised at random
+surface points with random orientation and radii 0.2 m; one step renders
+8 views (rotating through the 64), computes the Eq. 14 loss against the exact
+ground-truth depth/normal maps, back-propagates to the planes and takes an
+Adam step -- every call a libps kernel.  Inputs are synthetic (the paper's
+ScanNet scenes are not available) and resident in HBM.
+
+Metric: Mpixel-views/s = 8 * 640 * 480 / (time of one step) / 1e6, device
+time by CUDA events on the launching stream, L2 flushed (256 MB write) between
+steps outside the timed events.  `e2e` repeats it through host buffers (the
+step's ground-truth maps copied from pinned host memory and the loss sums
+read back, inside the timed region).  `roofline` reports the dominant kernel
+against the FP32 ALU peak, with its algorithmic work counted exactly by
+ps_count_pairs.  `cpu_baseline` times the FP64 oracle on a bounded sample.
+
+`--impl reference` times the oracle (the CPU definition of the method) on a
+bounded sample per step and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd splat Mpixel-views/s & time-to-depth-err≤2cm vs plain, 1×GB300"
+UNIT = "Mpixel-views/s"
+H, W, F = 480, 640, 500.0
+N_VIEWS, VIEWS_PER_STEP, N_GT, N_INIT = 64, 8, 2000, 3000
+
+# FP32 operation counts of the method's formulas (FMA = 2, MUFU op = 1), used
+# for the algorithmic work of the roofline:
+#   per candidate pair (Eq. 4, 6-9): d.n 4, t 2, d.v^x d.v^y 8, P_X P_Y 4,
+#     margins 2, min 1, weight 6                                       = 27
+#   per composited pair, forward (Eq. 11-13): T w 1, D 2, N 6, alpha 1,
+#     T(1 - w) 2                                                        = 12
+#   per composited pair, backward: T(1 - w) 2 + adjoint of Eq. 11-13 16
+#     + A, B updates 12 + Eq. 7-9 chain 5 + Eq. 6 chain 7 + Eq. 4 chain 8
+#     + record accumulation 16                                         = 66
+FLOP_CAND, FLOP_COMP_FWD, FLOP_COMP_BWD = 27, 12, 66
+SM_COUNT, FP32_LANES = 152, 128
+
+# DRAM traffic per launch of ps_splat_bwd's main kernel, from the ncu capture
+# summarised in profiles/ (valid only for the kernel source it was taken on).
+TRAFFIC = {"splat_bwd": None, "splat_fwd": None, "src_sha": None}
+
+
+def src_hash() -> str:
+    p = os.path.join(ROOT, "paper_2412_03451_gb300", "csrc", "ps_splat.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", default="16x16", choices=["16x16", "8x8", "32x8"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ttd", type=int, default=0,
+                    help="also fit up to this many iterations and report time to depth error <= 2 cm")
+    ap.add_argument("--start-ite", type=int, default=0, help="iteration (lambda schedule) to start at")
+    return ap.parse_args()
+
+
+def workload_config(args, world):
+    return {"workload": "synthetic room 8x10x3 m, %d GT rectangles, %d planes, %d of %d views "
+                        "per step at %dx%d" % (N_GT, N_INIT, VIEWS_PER_STEP, N_VIEWS, W, H),
+            "views_per_step": VIEWS_PER_STEP, "image": [H, W], "planes": N_INIT, "tile": args.tile,
+            "M": 30, "l2": "flushed between steps (256 MB write, outside the timed events)",
+            "start_iteration": args.start_ite, "replicas": world,
+            "seed": "scene 1000 + rank, init 2000 + rank"}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, path=None):
+        self.index = index
+        self.proc = None
+        self.path = path
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        if self.path:
+            try:
+                with open(self.path, "w") as f:
+                    f.write(out)
+            except OSError:
+                pass
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# Our arm.
+
+class Workload:
+    def __init__(self, rank: int, tile, device):
+        import numpy as np
+        import torch
+        from paper_2412_03451_gb300 import binding as B
+        from paper_2412_03451_gb300 import scenes as S
+        from paper_2412_03451_gb300 import splat as SP
+        self.torch, self.B, self.SP = torch, B, SP
+        self.room = S.large_room(1000 + rank, n_rect=N_GT, n_views=N_VIEWS, H=H, W=W, f=F)
+        self.init = S.surface_init(self.room, N_INIT, 2000 + rank)
+        cams = self.room.cams
+        # ground truth: exact ray casting of the GT rectangles with the library's hard mode
+        gtr = SP.Renderer([H] * N_VIEWS, [W] * N_VIEWS, [0] * N_VIEWS, [0, N_GT], tile=tile,
+                          device=device, flags=B.PS_HARD)
+        gtr.set_cameras(cams.w2c, cams.intr)
+        gflat = SP.planes_to_flat(self.room.gt.center, self.room.gt.quat, self.room.gt.radii,
+                                  device)
+        gtr.ensure_capacity(gflat, 300.0)
+        gtr.forward(gflat, 300.0)
+        torch.cuda.synchronize()
+        self.gt_depth = gtr.depth.clone()
+        self.gt_normal = gtr.normal.clone()
+        del gtr
+        self.r = SP.Renderer([H] * VIEWS_PER_STEP, [W] * VIEWS_PER_STEP, [0] * VIEWS_PER_STEP,
+                             [0, N_INIT], tile=tile, device=device)
+        nb = N_VIEWS // VIEWS_PER_STEP
+        self.r.preplan([cams.w2c[b * VIEWS_PER_STEP:(b + 1) * VIEWS_PER_STEP] for b in range(nb)],
+                       [cams.intr[b * VIEWS_PER_STEP:(b + 1) * VIEWS_PER_STEP] for b in range(nb)])
+        self.flat = SP.planes_to_flat(self.init.center, self.init.quat, self.init.radii, device)
+        self.fit = SP.Fitter(self.r, self.flat)
+        self.hw = H * W
+        self.np = np
+
+    def reset(self, ite=0):
+        SP = self.SP
+        self.flat.copy_(SP.planes_to_flat(self.init.center, self.init.quat, self.init.radii,
+                                          self.flat.device))
+        self.fit.m.zero_()
+        self.fit.v.zero_()
+        self.fit.ite = ite
+
+    def gt_slice(self, s):
+        b = (s % (N_VIEWS // VIEWS_PER_STEP)) * VIEWS_PER_STEP
+        n = VIEWS_PER_STEP * self.hw
+        return (self.gt_depth[b * self.hw:b * self.hw + n],
+                self.gt_normal[b * self.hw:b * self.hw + n])
+
+    def step(self, s, marks=None, gt=None):
+        self.r.select(s % (N_VIEWS // VIEWS_PER_STEP))
+        gd, gn = self.gt_slice(s) if gt is None else gt
+        return self.fit.step(gd, gn, marks=marks)
+
+    def grow_if_needed(self, s) -> bool:
+        """Checks the tile-list capacity for step s's views at the current state."""
+        self.r.select(s % (N_VIEWS // VIEWS_PER_STEP))
+        lam = self.B.lambda_schedule(self.fit.ite)
+        return self.r.ensure_capacity(self.flat, lam, headroom=1.6)
+
+
+def time_steps(wl, first, K, flush, counts_out=None):
+    """Times K steps starting at step index `first`; returns per-stage ms lists."""
+    torch = wl.torch
+    stages = {}
+    per_step = []
+    counts = torch.zeros(3, dtype=torch.int64, device=wl.flat.device)
+    tot = torch.zeros(3, dtype=torch.int64, device=wl.flat.device)
+    pairs = []
+    for i in range(K):
+        flush.zero_()
+        marks = []
+        wl.step(first + i, marks=marks)
+        pairs.append(marks)
+        if counts_out is not None:
+            wl.r.count_pairs(counts)
+            tot += counts
+    torch.cuda.synchronize()
+    for marks in pairs:
+        t0 = marks[0][1]
+        per_step.append(t0.elapsed_time(marks[-1][1]))
+        for (a, ea), (b, eb) in zip(marks[:-1], marks[1:]):
+            stages.setdefault(b, []).append(ea.elapsed_time(eb))
+    if counts_out is not None:
+        counts_out.extend(int(x) for x in tot.cpu().tolist())
+    return per_step, stages
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    device = "cuda:%d" % local_rank
+    torch.cuda.set_device(local_rank)
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    wl = Workload(rank, tile, device)
+    wl.reset(args.start_ite)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+
+    # warm-up (capacity checks happen here, never inside the timed region)
+    for i in range(max(args.warmup, 3)):
+        wl.grow_if_needed(i)
+        wl.step(i)
+    torch.cuda.synchronize()
+    first = max(args.warmup, 3)
+    for s in range(first, first + args.steps):
+        wl.grow_if_needed(s)   # state at the start of timing: make room for every view batch
+    wl.r.status.zero_()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank, os.path.join(ROOT, "gpurun_out", "clocks_r%d.csv" % rank)
+                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clk.start()
+    t_wall = time.perf_counter()
+    counts = []
+    per_step, stages = time_steps(wl, first, args.steps, flush, counts_out=counts)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    status = int(wl.r.status.item())
+    if status & (1 << B_CAP()):
+        raise RuntimeError("tile-list capacity overflow inside the timed region")
+
+    dev_ms = sum(per_step)
+    t_max = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    dev_ms = float(t_max.item())
+    pix = VIEWS_PER_STEP * H * W
+    value = world * pix * args.steps / (dev_ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (ALU-bound: FP32 work of the formulas)
+    tested, cand, comp = counts
+    fwd_ms = statistics.mean(stages["splat_fwd"])
+    bwd_ms = statistics.mean(stages["splat_bwd"])
+    K = args.steps
+    flops_fwd = (cand * FLOP_CAND + comp * FLOP_COMP_FWD) / K
+    flops_bwd = (cand * FLOP_CAND + comp * FLOP_COMP_BWD) / K
+    sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES * 2 * sm_clock * 1e6 / 1e12
+    dom = "splat_bwd" if bwd_ms >= fwd_ms else "splat_fwd"
+    dom_ms = max(fwd_ms, bwd_ms)
+    achieved = (flops_bwd if dom == "splat_bwd" else flops_fwd) / (dom_ms / 1e3) / 1e12
+    traffic = TRAFFIC.get(dom) if TRAFFIC.get("src_sha") == src_hash() else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_clock,
+                "per_launch": {"candidate_pairs": cand // K, "composited_pairs": comp // K,
+                               "tested_pairs": tested // K, "ms": round(dom_ms, 4)}}
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(args, world),
+        "stage_ms": {k: round(statistics.mean(v), 4) for k, v in stages.items()},
+        "wall_s_timed": round(wall, 4),
+        "roofline": roofline, "clocks": clocks,
+        "gpu_launches": 11 * args.steps,
+        "culling": {"tested_per_candidate": round(tested / max(cand, 1), 2)},
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(wl, args, first + args.steps, world)
+    if args.ttd:
+        result["time_to_2cm"] = run_ttd(wl, args.ttd)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        result["cpu_baseline"] = cpu_baseline(wl.room, wl.init, args.start_ite)
+    return result
+
+
+def B_CAP():
+    return 3
+
+
+def run_e2e(wl, args, first, world):
+    """Same metric through host buffers: each step copies its views' ground-truth
+    depth/normal maps from pinned host memory to the device and reads the loss
+    sums back, inside the timed region."""
+    import torch
+    dev = wl.flat.device
+    n = VIEWS_PER_STEP * wl.hw
+    host_d = wl.gt_depth.cpu().pin_memory()
+    host_n = wl.gt_normal.cpu().pin_memory()
+    dev_d = torch.empty(n, dtype=torch.float32, device=dev)
+    dev_n = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    out = torch.empty((VIEWS_PER_STEP, 4), dtype=torch.float64).pin_memory()
+    K = args.steps
+    for s in range(first, first + K):
+        wl.grow_if_needed(s)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record()
+    for i in range(K):
+        s = first + i
+        b = (s % (N_VIEWS // VIEWS_PER_STEP)) * VIEWS_PER_STEP
+        dev_d.copy_(host_d[b * wl.hw:b * wl.hw + n], non_blocking=True)
+        dev_n.copy_(host_n[b * wl.hw:b * wl.hw + n], non_blocking=True)
+        vs = wl.step(s, gt=(dev_d, dev_n))
+        out.copy_(vs, non_blocking=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = ev0.elapsed_time(ev1)
+    t = max(ms / 1e3, wall)
+    value = world * VIEWS_PER_STEP * H * W * K / t / 1e6
+    return {"value": round(value, 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(n * 4 + n * 12), "d2h_bytes_per_step": VIEWS_PER_STEP * 4 * 8,
+            "ms_per_step": round(t * 1e3 / K, 4)}
+
+
+def run_ttd(wl, max_iters):
+    """Wall time of the plain single-scene fit (from the initial planes, lambda
+    schedule from 0) until the mean |D - D_gt| over all 64 views is <= 2 cm,
+    checked every 8 steps (one pass over the views) with a forward-only render
+    of all views; evaluation time is excluded."""
+    import torch
+    from paper_2412_03451_gb300 import splat as SP
+    wl.reset(0)
+    ev = SP.Renderer([H] * N_VIEWS, [W] * N_VIEWS, [0] * N_VIEWS, [0, N_INIT],
+                     tile=wl.r.tile, device=wl.flat.device)
+    ev.set_cameras(wl.room.cams.w2c, wl.room.cams.intr)
+    nb = N_VIEWS // VIEWS_PER_STEP
+    spent = 0.0
+    err = float("nan")
+    hist = []
+    for it in range(0, max_iters, nb):
+        for s in range(it, it + nb):
+            wl.grow_if_needed(s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(it, it + nb):
+            wl.step(s)
+        torch.cuda.synchronize()
+        spent += time.perf_counter() - t0
+        if (it // nb) % 4 == 3 or it + nb >= max_iters:
+            lam = SP.B.lambda_schedule(wl.fit.ite)
+            ev.ensure_capacity(wl.flat, lam)
+            ev.forward(wl.flat, lam, alpha=False)
+            e = (ev.depth - wl.gt_depth).abs()
+            valid = wl.gt_depth > 0
+            err = float(e[valid].mean().item())
+            hist.append((wl.fit.ite, round(err, 5), round(spent, 3)))
+            if err <= 0.02:
+                return {"seconds": round(spent, 3), "iterations": wl.fit.ite, "depth_err_m": err,
+                        "reached": True, "history": hist[-6:]}
+    return {"seconds": round(spent, 3), "iterations": wl.fit.ite, "depth_err_m": err,
+            "reached": False, "history": hist[-6:]}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm).
+
+def oracle_sample_step(room, planes, views, rows, lam):
+    """One forward + loss + backward of the FP64 oracle on `rows` of `views`."""
+    import numpy as np
+    from oracle import oracle as O
+    cams = room.cams.subset(views)
+    z32 = float(np.float32(0.01))
+    gd, gn, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, cams.w2c, cams.intr, H, W,
+                          z_near=z32, rows=rows)
+    t0 = time.perf_counter()
+    o = O.render(planes.center, planes.quat, planes.radii, cams.w2c, cams.intr, H, W,
+                 float(np.float32(lam)), z_near=z32, rows=rows)
+    _, dD, dN, _ = O.loss(o["depth"], o["normal"], gd, gn)
+    keep = np.zeros(dD.shape, bool)
+    keep[:, rows[0]:rows[1]] = True
+    dD[~keep] = 0
+    dN[~keep] = 0
+    O.backward(planes.center, planes.quat, planes.radii, cams.w2c, cams.intr, H, W,
+               float(np.float32(lam)), dD, dN, z_near=z32)
+    return time.perf_counter() - t0, len(views) * (rows[1] - rows[0]) * W
+
+
+def cpu_baseline(room, init, ite, target_s=15.0):
+    from oracle import oracle as O
+    lam = O.lambda_schedule(ite)
+    views = list(range(VIEWS_PER_STEP))
+    r0 = H // 2
+    t, npx = oracle_sample_step(room, init, views, (r0, r0 + 2), lam)
+    rows = max(2, min(H, int(2 * target_s / max(t, 1e-3))))
+    r0 = max(0, H // 2 - rows // 2)
+    t, npx = oracle_sample_step(room, init, views, (r0, r0 + rows), lam)
+    return {"value": round(npx / t / 1e6, 6), "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": "rows %d-%d of the first %d views (%d pixel-views), forward + loss + backward "
+                      "of the FP64 brute-force oracle over all %d planes; %.1f s" %
+                      (r0, r0 + rows, len(views), npx, N_INIT, t)}
+
+
+def run_reference(args):
+    """The oracle as it stands, on the same workload and metric: each step
+    renders, scores and back-propagates a bounded sample of the step's views."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2412_03451_gb300 import scenes as S
+    room = S.large_room(1000, n_rect=N_GT, n_views=N_VIEWS, H=H, W=W, f=F)
+    init = S.surface_init(room, N_INIT, 2000)
+    lam = O.lambda_schedule(args.start_ite)
+    total_steps = args.steps + args.warmup
+    # size the sample so the whole run takes about two minutes
+    t, npx = oracle_sample_step(room, init, list(range(VIEWS_PER_STEP)), (H // 2, H // 2 + 1), lam)
+    per_row = t
+    rows = int(max(1, min(H, 120.0 / max(total_steps, 1) / max(per_row, 1e-3))))
+    times, pix = [], 0
+    for s in range(total_steps):
+        b = (s % (N_VIEWS // VIEWS_PER_STEP)) * VIEWS_PER_STEP
+        r0 = (37 * s) % (H - rows + 1)
+        t, npx = oracle_sample_step(room, init, list(range(b, b + VIEWS_PER_STEP)), (r0, r0 + rows),
+                                    lam)
+        if s >= args.warmup:
+            times.append(t)
+            pix += npx
+    value = pix / sum(times) / 1e6
+    sample = ("per step: %d rows x %d px of the step's %d views (%d pixel-views of %d), forward + "
+              "loss + backward of the FP64 brute-force oracle over all %d planes" %
+              (rows, W, VIEWS_PER_STEP, rows * W * VIEWS_PER_STEP, VIEWS_PER_STEP * H * W, N_INIT))
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * statistics.mean(times), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, 1),
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": O.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

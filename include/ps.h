@@ -1,0 +1,238 @@
+/*
+ * ps.h -- C ABI of libps, a GB300 (sm_103a) CUDA implementation of the
+ * differentiable planar-primitive rendering of PlanarSplatting
+ * (arxiv 2412.03451, Sec. 3.2) and of the Adam step that fits it (Sec. 3.3).
+ *
+ * The calls follow the paper's statement of the problem: learnable planes
+ * (Sec. 3.1) and posed views go in, depth and normal maps come out (Eq. 11-13),
+ * the render loss of Eq. 14 gives per-pixel gradients, and the backward pass
+ * turns them into gradients of every plane's center, quaternion and radii.
+ *
+ * Conventions shared by every call
+ *   - All buffers are owned by the caller.  "device" pointers are CUDA device
+ *     memory of the current device; "host" pointers are ordinary host memory.
+ *     The library allocates nothing and keeps no state between calls.
+ *   - Every call that launches work is asynchronous on the given stream, does
+ *     not synchronise and does not allocate, so it may be captured in a CUDA
+ *     graph.
+ *   - Errors that the host can see (null pointers, bad sizes, bad settings)
+ *     are returned before anything is launched.  A launch failure returns
+ *     PS_ERR_CUDA.  Errors found on the device (capacity overflow, non-finite
+ *     parameters) are OR-ed into the caller's device status word as
+ *     (1 << code); the caller reads it after the stream is synchronised.
+ *     No kernel traps or asserts.
+ *
+ * Plane parameters (Eq. 1-3), planes of all scenes concatenated, P planes:
+ *   center [P][3] f32, quat [P][4] f32 (w,x,y,z; any nonzero norm; v^x, v^y, n
+ *   are the columns of the Hamilton rotation matrix of quat/|quat|),
+ *   radii [P][4] f32 (r^x+, r^x-, r^y+, r^y-).
+ *
+ * Views (OpenCV camera: x right, y down, z forward).  Pixel (i, j) of a view
+ *   casts the ray d = ((i + 0.5 - cx)/fx, (j + 0.5 - cy)/fy, 1) from the
+ *   camera centre, so the intersection parameter t of Eq. 4 is the z-depth.
+ *   Views of one scene are consecutive; each view renders the planes of its
+ *   own scene.  Per-pixel buffers of all views are concatenated (view v starts
+ *   at pixel pix_off[v]); normals are 3 floats per pixel, in the camera frame.
+ *
+ * Records: one per (view, plane of the view's scene), view-major.  A record
+ *   holds the plane in camera coordinates as 16 floats
+ *   {n_c, n_c.p_c, v^x_c, v^x_c.p_c, v^y_c, v^y_c.p_c, r^x+, r^x-, r^y+, r^y-},
+ *   its tile rectangle (4 ints, inclusive, empty = (0,0,-1,-1)) and its depth
+ *   key (1 float: smallest camera z of the plane widened by the filter margin,
+ *   rounded down to f32).
+ *
+ * Tiles: each view is cut into tile_w x tile_h pixel tiles, numbered
+ *   row-major within a view and concatenated over views.  A tile list holds the
+ *   record ids whose tile rectangle covers the tile, sorted by (key, record id).
+ */
+#ifndef PS_H_
+#define PS_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ps_stream;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    PS_OK = 0,
+    PS_ERR_ARG = 1,        /* bad argument, reported by the host before any launch */
+    PS_ERR_CUDA = 2,       /* a CUDA launch or API call failed */
+    PS_ERR_CAPACITY = 3,   /* tile-list capacity too small; required size written back */
+    PS_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up */
+    PS_ERR_NONFINITE = 5   /* NaN/Inf plane parameters (the plane is culled) */
+} ps_status;
+
+/* ps_settings.flags */
+#define PS_SINGLE_RADII 1  /* use r^x+ for both X sides and r^y+ for both Y sides (the
+                              "w/o Double Radii" ablation, Sec. 4.3) */
+#define PS_HARD 2          /* hard rectangle: w = 1 inside (m >= 0), else filtered.
+                              Used to ray-cast ground truth; no backward. */
+
+#define PS_MAX_M 64        /* largest supported M (nearest intersections per ray) */
+
+/* Per-step settings.  Passed by host pointer; read on the host. */
+typedef struct ps_settings {
+    float lambda;          /* Eq. 10 value for this iteration */
+    float w_min;           /* filter threshold, 1e-4 (Sec. 3.2) */
+    float z_near, z_far;   /* valid intersection depth range (0.01, 100 m) */
+    double delta;          /* binning margin: 2 sigmoid(-5 lambda delta) = w_min; 0 with PS_HARD */
+    int M;                 /* nearest intersections kept per ray, 30 (Sec. 3.2), <= PS_MAX_M */
+    int tile_w, tile_h;    /* tile shape in pixels: 8x8, 16x16 or 32x8 */
+    int flags;             /* PS_SINGLE_RADII | PS_HARD */
+    float a_cos, a_l1n, a_depth;  /* Eq. 14 weights: alpha_1 = 5, alpha_1 = 5, alpha_2 = 1 */
+    int reserved;
+} ps_settings;
+
+/* Per-view descriptor, 128 bytes.  Filled on the host by ps_plan_views and
+   copied to the device by the caller. */
+typedef struct ps_view {
+    float w2c[12];         /* world-to-camera [R|t], row-major 3x4 */
+    float fx, fy, cx, cy;  /* intrinsics */
+    int H, W;              /* image size */
+    int tiles_x, tiles_y;  /* tile grid of this view */
+    int tile_off;          /* first global tile of this view */
+    int rec_off;           /* first record of this view */
+    int plane_off;         /* first plane (row of center/quat/radii) of the view's scene */
+    int K;                 /* planes in the view's scene */
+    long long pix_off;     /* first pixel of this view in per-pixel buffers */
+    int scene;             /* scene index */
+    int reserved[5];
+} ps_view;
+
+/* A batch of views: totals (host) and the descriptor array (device). */
+typedef struct ps_frame {
+    int n_views;           /* V */
+    int n_records;         /* sum over views of K */
+    int n_tiles;           /* sum over views of tiles_x * tiles_y */
+    int max_K;             /* largest K of any view */
+    long long n_pixels;    /* sum over views of H * W */
+    const ps_view* views;  /* device [V] */
+} ps_frame;
+
+/* Plane parameters (device), P planes in total. */
+typedef struct ps_planes {
+    int n_planes;          /* P */
+    int reserved;
+    const float* center;   /* [P][3] */
+    const float* quat;     /* [P][4] w,x,y,z */
+    const float* radii;    /* [P][4] x+, x-, y+, y- */
+} ps_planes;
+
+/* Fills the host array views_out[V] and the totals of *frame_out (whose
+   .views is left NULL for the caller to set to the device copy).
+   scene_of_view[V] (host, non-decreasing) and plane_ptr[S+1] (host, CSR of
+   the planes of each scene) describe the batch; w2c [V][12] and intr [V][4]
+   are host arrays.  Returns PS_ERR_ARG on inconsistent input.  Host only. */
+ps_status ps_plan_views(int n_views, const int* H, const int* W, const int* scene_of_view,
+                        int n_scenes, const int* plane_ptr, const float* w2c, const float* intr,
+                        int tile_w, int tile_h, ps_view* views_out, ps_frame* frame_out);
+
+/* Projection and culling (Sec. 3.1 Eq. 2-3 and Sec. 3.2 Eq. 4, 6-9).
+   For every (view, plane): normalise the quaternion, form v^x, v^y, n, move
+   them and the center to the camera frame, and write the 16-float record.
+   The tile rectangle and depth key come from the plane widened by
+   settings->delta on every side (every pair that passes the w >= w_min filter
+   lies inside), clipped to z >= z_near, projected, padded by one pixel and
+   clamped to the image; they are computed in FP64 with correctly rounded
+   + - * / sqrt only, so they are reproducible bit for bit.
+   rec [R][16] f32, rect [R][4] i32, key [R] f32 (device, written).
+   Non-finite or zero-norm parameters cull the plane and set PS_ERR_NONFINITE. */
+ps_status ps_project_cull(const ps_planes* planes, const ps_frame* frame,
+                          const ps_settings* settings, float* rec, int* rect, float* key,
+                          int* d_status, ps_stream stream);
+
+/* Bytes of scratch that ps_bin_tiles needs for this frame and capacity. */
+size_t ps_bin_workspace_bytes(const ps_frame* frame, long long capacity);
+
+/* Binning and depth ordering (the near-to-far sort of Sec. 3.2, "Blending
+   Composition", applied per tile to the conservative depth key).
+   Writes tile_ptr [n_tiles + 1] (device, CSR offsets) and tile_ent [capacity]
+   (device, record ids sorted by (key, record id) within each tile).  The
+   total number of entries goes to *d_required (device, 1 long long).  If it
+   exceeds capacity, PS_ERR_CAPACITY is set in *d_status, tile_ptr is still
+   complete, and the splat calls read only the first `capacity` entries.
+   ws (device, ws_bytes >= ps_bin_workspace_bytes) is scratch. */
+ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* settings, const int* rect,
+                       const float* key, int* tile_ptr, int* tile_ent, long long capacity,
+                       long long* d_required, void* ws, size_t ws_bytes, int* d_status,
+                       ps_stream stream);
+
+/* Forward splatting (Sec. 3.2, Eq. 4, 6-9, 11-13).  For every pixel: intersect
+   the ray with every plane of the pixel's tile list, weight it with
+   w = min(1, 2 sigmoid(5 lambda min(m_X, m_Y))) (m = r - |P| on the side given
+   by the sign of P), drop w < w_min and depths outside (z_near, z_far), keep
+   the M nearest by (t, record id) and composite front to back:
+   D = sum T_j w_j t_j, N = sum T_j w_j n_j, alpha = sum T_j w_j.
+   depth [n_pixels], normal [n_pixels][3], alpha [n_pixels] (device, written;
+   alpha may be NULL). */
+ps_status ps_splat_fwd(const ps_frame* frame, const ps_settings* settings, const float* rec,
+                       const float* key, const int* tile_ptr, const int* tile_ent,
+                       long long capacity, float* depth, float* normal, float* alpha,
+                       int* d_status, ps_stream stream);
+
+/* Render loss (Eq. 14) and its gradient with respect to the rendered maps.
+   Pixels with gt_depth <= 0 are not supervised (zero gradient).
+   dL_dD [n_pixels], dL_dN [n_pixels][3] (device, written);
+   view_sums [V][4] f64 (device, overwritten): per view the sums of
+   |1 - N.N*|, ||N - N*||_1, |D - D*| and the number of supervised pixels.
+   Loss = a_cos*sum0 + a_l1n*sum1 + a_depth*sum2.  sgn(0) = 0. */
+ps_status ps_loss(const ps_frame* frame, const ps_settings* settings, const float* depth,
+                  const float* normal, const float* gt_depth, const float* gt_normal,
+                  float* dL_dD, float* dL_dN, double* view_sums, ps_stream stream);
+
+/* Bytes of scratch that ps_splat_bwd needs (per-record gradient accumulators). */
+size_t ps_bwd_workspace_bytes(const ps_frame* frame);
+
+/* Backward splatting: gradient of sum(dL_dD * D + dL_dN . N) with respect to
+   every plane's center, quaternion and radii.  Recomputes each pixel's
+   composited list from the tile lists (no per-pixel state is stored by the
+   forward), takes the adjoint of Eq. 11-13 back to front
+   (A_j = w_j t_j + (1 - w_j) A_{j+1}, dD/dw_j = T_j (t_j - A_{j+1}); no
+   division by 1 - w), chains it through Eq. 9, 7-8, 6, 4 into per-record
+   gradients and then through the camera transform and Eq. 2-3 (with the
+   quaternion normalisation) into the world parameters.  The clamp
+   min(1, .) has derivative 0 where m >= 0.  Ties of Eq. 9 go to the Y side.
+   g_center [P][3], g_quat [P][4], g_radii [P][4] (device) are ACCUMULATED
+   into (the caller zeroes them).  ws (device, >= ps_bwd_workspace_bytes) is
+   scratch.  Float atomics make the summation order, and so the last bits,
+   vary from run to run. */
+ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* frame,
+                       const ps_settings* settings, const float* rec, const float* key,
+                       const int* tile_ptr, const int* tile_ent, long long capacity,
+                       const float* dL_dD, const float* dL_dN, float* g_center, float* g_quat,
+                       float* g_radii, void* ws, size_t ws_bytes, int* d_status,
+                       ps_stream stream);
+
+/* Adam (Kingma & Ba; Sec. 3.3, lr = 1e-3 for every group, App. A.2),
+   bias-corrected, on n floats in place: param, m, v (device, updated),
+   grad (device, read).  step counts from 1.  After the update every value
+   below clamp_min is raised to it; pass NaN for no clamp. */
+ps_status ps_adam_step(float* param, const float* grad, float* m, float* v, long long n,
+                       float lr, float b1, float b2, float eps, int step, float clamp_min,
+                       ps_stream stream);
+
+/* Work counts of one forward splat, for throughput and roofline reports:
+   d_counts[0] = pairs tested (tile-list entries x pixels of the tile inside the
+   image), d_counts[1] = candidate pairs (pairs that pass the w >= w_min and depth
+   filters of Sec. 3.2: the algorithmic pair count, independent of tiling),
+   d_counts[2] = composited pairs (per pixel, min(M, candidates up to and
+   including the nearest one with w = 1)).  d_counts (device, 3 long long) is
+   overwritten.  Walks every tile list completely; slower than ps_splat_fwd. */
+ps_status ps_count_pairs(const ps_frame* frame, const ps_settings* settings, const float* rec,
+                         const float* key, const int* tile_ptr, const int* tile_ent,
+                         long long capacity, long long* d_counts, ps_stream stream);
+
+/* Human-readable name of a status code. */
+const char* ps_status_string(ps_status status);
+
+/* Library version, for the binding's sanity check. */
+int ps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_H_ */

@@ -80,7 +80,7 @@ def _load():
             lib.or_loss.argtypes = [I, I, I, P, P, P, P, D, D, D, P, P, P]
             lib.or_loss.restype = D
             lib.or_backward.argtypes = [I, I, P, P, P, P, P, I, I, D, D, D, D, I, I, P, P, P, P, P]
-            lib.or_raycast.argtypes = [I, I, P, P, P, P, P, I, I, D, D, P, P, P]
+            lib.or_raycast.argtypes = [I, I, P, P, P, P, P, I, I, D, D, I, I, P, P, P]
             lib.or_adam.argtypes = [L, P, P, P, P, D, D, D, D, I, D]
             lib.or_num_threads.restype = I
             _lib = lib
@@ -221,16 +221,19 @@ def total_loss(center, quat, radii, w2c, intr, H, W, lam, gt_depth, gt_normal, *
     return loss(out["depth"], out["normal"], gt_depth, gt_normal)[0]
 
 
-def raycast(center, quat, radii, w2c, intr, H, W, z_near=Z_NEAR, z_far=Z_FAR):
-    """Exact hard-rectangle ray casting (ground truth for synthetic rooms)."""
+def raycast(center, quat, radii, w2c, intr, H, W, z_near=Z_NEAR, z_far=Z_FAR, rows=None):
+    """Exact hard-rectangle ray casting (ground truth for synthetic rooms).
+    Only rows [rows[0], rows[1]) are cast when rows is given (others stay 0)."""
     c, q, r = _f64(center), _f64(quat), _f64(radii)
     Rt, K_ = _f64(w2c).reshape(-1, 12), _f64(intr).reshape(-1, 4)
     K, V = c.shape[0], Rt.shape[0]
     D = np.zeros((V, H, W))
     N = np.zeros((V, H, W, 3))
-    pid = np.zeros((V, H, W), np.int32)
+    pid = np.full((V, H, W), -1, np.int32)
+    row0, row1 = (0, H) if rows is None else rows
     _load().or_raycast(K, V, _ptr(c), _ptr(q), _ptr(r), _ptr(Rt), _ptr(K_), H, W,
-                       float(z_near), float(z_far), _ptr(D), _ptr(N), _ptr(pid))
+                       float(z_near), float(z_far), int(row0), int(row1), _ptr(D), _ptr(N),
+                       _ptr(pid))
     return D, N, pid
 
 

@@ -568,10 +568,10 @@ void or_backward(int K, int V, const double* center, const double* quat, const d
 /* (|P_X| <= r_X, |P_Y| <= r_Y, one-sided radii by sign) the pixel ray hits  */
 /* with z_near < t < z_far.  Used to make ground-truth depth and normal      */
 /* maps of synthetic rooms.  Pixels that hit nothing get depth 0, normal 0   */
-/* and plane_id -1.                                                          */
+/* and plane_id -1.  Rows [row0, row1) of every view are cast.              */
 void or_raycast(int K, int V, const double* center, const double* quat, const double* radii,
                 const double* w2c, const double* intr, int H, int W, double z_near, double z_far,
-                double* depth, double* normal, int* plane_id)
+                int row0, int row1, double* depth, double* normal, int* plane_id)
 {
     plane_cam* pcs = (plane_cam*)malloc(sizeof(plane_cam) * (size_t)(K > 0 ? K : 1));
     for (int v = 0; v < V; ++v) {
@@ -581,7 +581,7 @@ void or_raycast(int K, int V, const double* center, const double* quat, const do
         double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
         double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
 #pragma omp parallel for schedule(dynamic, 1)
-        for (int j = 0; j < H; ++j) {
+        for (int j = row0; j < row1; ++j) {
             for (int i = 0; i < W; ++i) {
                 long pix = ((long)v * H + j) * W + i;
                 double d[3] = {((double)i + 0.5 - cx) / fx, ((double)j + 0.5 - cy) / fy, 1.0};

@@ -1,0 +1,241 @@
+"""ctypes binding of libps (include/ps.h), with the same function names.
+
+Argument marshalling only: every step of the rendering path runs in the CUDA
+kernels of libps.so.  Tensors are passed by data pointer; the stream is the
+current PyTorch stream unless one is given.  If the compiled library is
+missing, every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libps.so")
+
+PS_OK, PS_ERR_ARG, PS_ERR_CUDA, PS_ERR_CAPACITY, PS_ERR_TIMEOUT, PS_ERR_NONFINITE = range(6)
+PS_SINGLE_RADII = 1
+PS_HARD = 2
+PS_MAX_M = 64
+
+EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin_tiles",
+           "ps_splat_fwd", "ps_loss", "ps_bwd_workspace_bytes", "ps_splat_bwd", "ps_adam_step",
+           "ps_count_pairs", "ps_status_string", "ps_version")
+
+
+class PsSettings(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_float), ("w_min", ctypes.c_float),
+                ("z_near", ctypes.c_float), ("z_far", ctypes.c_float),
+                ("delta", ctypes.c_double), ("M", ctypes.c_int),
+                ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("flags", ctypes.c_int),
+                ("a_cos", ctypes.c_float), ("a_l1n", ctypes.c_float), ("a_depth", ctypes.c_float),
+                ("reserved", ctypes.c_int)]
+
+
+class PsView(ctypes.Structure):
+    _fields_ = [("w2c", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("tiles_x", ctypes.c_int), ("tiles_y", ctypes.c_int),
+                ("tile_off", ctypes.c_int), ("rec_off", ctypes.c_int), ("plane_off", ctypes.c_int),
+                ("K", ctypes.c_int), ("pix_off", ctypes.c_longlong), ("scene", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+class PsFrame(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int), ("n_records", ctypes.c_int),
+                ("n_tiles", ctypes.c_int), ("max_K", ctypes.c_int),
+                ("n_pixels", ctypes.c_longlong), ("views", ctypes.c_void_p)]
+
+
+class PsPlanes(ctypes.Structure):
+    _fields_ = [("n_planes", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("center", ctypes.c_void_p), ("quat", ctypes.c_void_p), ("radii", ctypes.c_void_p)]
+
+
+assert ctypes.sizeof(PsView) == 128
+assert ctypes.sizeof(PsSettings) == 56
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PsError(RuntimeError):
+    pass
+
+
+def load():
+    """Loads libps.so (built by paper_2412_03451_gb300._build); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise PsError("libps.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I, LL, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t
+        F, D = ctypes.c_float, ctypes.c_double
+        sig = {
+            "ps_plan_views": ([I, P, P, P, I, P, P, P, I, I, P, P], I),
+            "ps_project_cull": ([P, P, P, P, P, P, P, P], I),
+            "ps_bin_workspace_bytes": ([P, LL], SZ),
+            "ps_bin_tiles": ([P, P, P, P, P, P, LL, P, P, SZ, P, P], I),
+            "ps_splat_fwd": ([P, P, P, P, P, P, LL, P, P, P, P, P], I),
+            "ps_loss": ([P, P, P, P, P, P, P, P, P, P], I),
+            "ps_bwd_workspace_bytes": ([P], SZ),
+            "ps_splat_bwd": ([P, P, P, P, P, P, P, LL, P, P, P, P, P, P, SZ, P, P], I),
+            "ps_adam_step": ([P, P, P, P, LL, F, F, F, F, I, F, P], I),
+            "ps_count_pairs": ([P, P, P, P, P, P, LL, P, P], I),
+            "ps_status_string": ([I], ctypes.c_char_p),
+            "ps_version": ([], I),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(code: int, what: str):
+    if code != PS_OK:
+        msg = load().ps_status_string(code).decode()
+        raise PsError("%s failed: %s (%d)" % (what, msg, code))
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# Host planning.
+
+def ps_plan_views(H, W, scene_of_view, plane_ptr, w2c, intr, tile_w, tile_h):
+    """Plans a batch of views.  Returns (PsView array (host), PsFrame with views=NULL)."""
+    lib = load()
+    V = len(H)
+    Ha = np.ascontiguousarray(H, dtype=np.int32)
+    Wa = np.ascontiguousarray(W, dtype=np.int32)
+    sc = np.ascontiguousarray(scene_of_view, dtype=np.int32)
+    pp = np.ascontiguousarray(plane_ptr, dtype=np.int32)
+    w2 = np.ascontiguousarray(np.asarray(w2c, dtype=np.float32).reshape(V, 12))
+    it = np.ascontiguousarray(np.asarray(intr, dtype=np.float32).reshape(V, 4))
+    views = (PsView * V)()
+    frame = PsFrame()
+    code = lib.ps_plan_views(V, Ha.ctypes.data, Wa.ctypes.data, sc.ctypes.data, len(pp) - 1,
+                             pp.ctypes.data, w2.ctypes.data, it.ctypes.data, int(tile_w),
+                             int(tile_h), ctypes.byref(views), ctypes.byref(frame))
+    _check(code, "ps_plan_views")
+    return views, frame
+
+
+def make_settings(lam, delta, M=30, tile_w=16, tile_h=16, flags=0, w_min=1e-4, z_near=0.01,
+                  z_far=100.0, a_cos=5.0, a_l1n=5.0, a_depth=1.0) -> PsSettings:
+    s = PsSettings()
+    s.lambda_ = float(lam)
+    s.w_min = float(w_min)
+    s.z_near = float(z_near)
+    s.z_far = float(z_far)
+    s.delta = float(delta)
+    s.M = int(M)
+    s.tile_w, s.tile_h = int(tile_w), int(tile_h)
+    s.flags = int(flags)
+    s.a_cos, s.a_l1n, s.a_depth = float(a_cos), float(a_l1n), float(a_depth)
+    return s
+
+
+def filter_margin(lam: float, w_min: float = 1e-4) -> float:
+    """delta with 2 sigmoid(-5 lam delta) = w_min (Eq. 7-8 and the Sec. 3.2 filter)."""
+    h = 0.5 * w_min
+    return math.log((1.0 - h) / h) / (5.0 * lam)
+
+
+def lambda_schedule(ite: int) -> float:
+    """Eq. 10: lambda = min(20 e^{-(1 - 0.001 ite)}, 300)."""
+    return min(20.0 * math.exp(-(1.0 - 0.001 * ite)), 300.0)
+
+
+# ---------------------------------------------------------------------------
+# Device calls.
+
+def ps_project_cull(planes: PsPlanes, frame: PsFrame, settings: PsSettings, rec, rect, key,
+                    status, stream=None):
+    _check(load().ps_project_cull(ctypes.byref(planes), ctypes.byref(frame), ctypes.byref(settings),
+                                  _ptr(rec), _ptr(rect), _ptr(key), _ptr(status), _stream(stream)),
+           "ps_project_cull")
+
+
+def ps_bin_workspace_bytes(frame: PsFrame, capacity: int) -> int:
+    return int(load().ps_bin_workspace_bytes(ctypes.byref(frame), int(capacity)))
+
+
+def ps_bin_tiles(frame, settings, rect, key, tile_ptr, tile_ent, capacity, required, ws, status,
+                 stream=None):
+    nbytes = ws.numel() * ws.element_size()
+    _check(load().ps_bin_tiles(ctypes.byref(frame), ctypes.byref(settings), _ptr(rect), _ptr(key),
+                               _ptr(tile_ptr), _ptr(tile_ent), int(capacity), _ptr(required),
+                               _ptr(ws), nbytes, _ptr(status), _stream(stream)), "ps_bin_tiles")
+
+
+def ps_splat_fwd(frame, settings, rec, key, tile_ptr, tile_ent, capacity, depth, normal, alpha,
+                 status, stream=None):
+    _check(load().ps_splat_fwd(ctypes.byref(frame), ctypes.byref(settings), _ptr(rec), _ptr(key),
+                               _ptr(tile_ptr), _ptr(tile_ent), int(capacity), _ptr(depth),
+                               _ptr(normal), _ptr(alpha), _ptr(status), _stream(stream)),
+           "ps_splat_fwd")
+
+
+def ps_loss(frame, settings, depth, normal, gt_depth, gt_normal, dLdD, dLdN, view_sums, stream=None):
+    _check(load().ps_loss(ctypes.byref(frame), ctypes.byref(settings), _ptr(depth), _ptr(normal),
+                          _ptr(gt_depth), _ptr(gt_normal), _ptr(dLdD), _ptr(dLdN),
+                          _ptr(view_sums), _stream(stream)), "ps_loss")
+
+
+def ps_bwd_workspace_bytes(frame: PsFrame) -> int:
+    return int(load().ps_bwd_workspace_bytes(ctypes.byref(frame)))
+
+
+def ps_splat_bwd(planes, frame, settings, rec, key, tile_ptr, tile_ent, capacity, dLdD, dLdN,
+                 g_center, g_quat, g_radii, ws, status, stream=None):
+    nbytes = ws.numel() * ws.element_size()
+    _check(load().ps_splat_bwd(ctypes.byref(planes), ctypes.byref(frame), ctypes.byref(settings),
+                               _ptr(rec), _ptr(key), _ptr(tile_ptr), _ptr(tile_ent), int(capacity),
+                               _ptr(dLdD), _ptr(dLdN), _ptr(g_center), _ptr(g_quat),
+                               _ptr(g_radii), _ptr(ws), nbytes, _ptr(status), _stream(stream)),
+           "ps_splat_bwd")
+
+
+def ps_adam_step(param, grad, m, v, lr, b1, b2, eps, step, clamp_min=float("nan"), stream=None):
+    _check(load().ps_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
+                               float(lr), float(b1), float(b2), float(eps), int(step),
+                               float(clamp_min), _stream(stream)), "ps_adam_step")
+
+
+def ps_count_pairs(frame, settings, rec, key, tile_ptr, tile_ent, capacity, counts, stream=None):
+    _check(load().ps_count_pairs(ctypes.byref(frame), ctypes.byref(settings), _ptr(rec), _ptr(key),
+                                 _ptr(tile_ptr), _ptr(tile_ent), int(capacity), _ptr(counts),
+                                 _stream(stream)), "ps_count_pairs")
+
+
+def ps_status_string(code: int) -> str:
+    return load().ps_status_string(int(code)).decode()
+
+
+def ps_version() -> int:
+    return int(load().ps_version())
+
+
+def decode_status(word: int) -> list:
+    """Names of the device status bits set in a status word."""
+    return [ps_status_string(c) for c in range(1, 6) if word & (1 << c)]

@@ -1,0 +1,114 @@
+// ps_internal.cuh -- device helpers shared by the libps translation units.
+// Every TU of the library is compiled with -fmad=false: multiply-adds are
+// written as explicit fmaf() so that the forward and the backward kernels,
+// which recompute the same per-pixel candidate list, evaluate bit-identical
+// arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "ps.h"
+
+#define PS_CUDA_CHECK(expr)                                   \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return PS_ERR_CUDA;            \
+    } while (0)
+
+#define PS_LAUNCH_CHECK()                                     \
+    do {                                                      \
+        cudaError_t e_ = cudaGetLastError();                  \
+        if (e_ != cudaSuccess) return PS_ERR_CUDA;            \
+    } while (0)
+
+namespace ps {
+
+constexpr int kRecFloats = 16;   // floats per record
+
+__device__ __forceinline__ void set_status(int* st, ps_status code)
+{
+    if (st) atomicOr(st, 1 << (int)code);
+}
+
+// Global tile -> view by binary search over tile_off (views sorted by tile_off).
+__device__ __forceinline__ int view_of_tile(const ps_view* views, int V, int tile)
+{
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&views[mid].tile_off) <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One plane in camera coordinates, as stored in a record.
+struct Rec {
+    float4 n;    // n_c, s = n_c . p_c
+    float4 vx;   // v^x_c, a_x = v^x_c . p_c
+    float4 vy;   // v^y_c, a_y = v^y_c . p_c
+    float4 r;    // r^x+, r^x-, r^y+, r^y-
+};
+
+// Evaluation of one (pixel ray, plane) pair: Eq. 4, 6-9 and the filter of
+// Sec. 3.2.  d = (dx, dy, 1).  Returns true if the pair is a candidate.
+struct PairEval {
+    float t, w;        // depth, weight
+    float m;           // margin of the active side
+    float P;           // P_X or P_Y of the active side
+    float den;         // d . n_c
+    float dv;          // d . v_c of the active side
+    bool sideX;        // active side is X (m_X < m_Y); ties go to Y
+    bool pos;          // P > 0 on the active side (selects r^+)
+};
+
+struct SplatConst {
+    float lam5;        // 5 lambda
+    float w_min;
+    float z_near, z_far;
+    float reject;      // quick reject: margins below -reject cannot reach w_min
+    int hard;          // PS_HARD
+};
+
+__device__ __forceinline__ bool eval_pair(const float4& n, const float4& vx, const float4& vy,
+                                          const float4& r, float dx, float dy,
+                                          const SplatConst& c, PairEval& o)
+{
+    float den = fmaf(dx, n.x, fmaf(dy, n.y, n.z));
+    if (!(fabsf(den) > 1e-6f)) return false;
+    float t = __fdividef(n.w, den);
+    if (!(t > c.z_near && t < c.z_far)) return false;
+    float dvx = fmaf(dx, vx.x, fmaf(dy, vx.y, vx.z));
+    float dvy = fmaf(dx, vy.x, fmaf(dy, vy.y, vy.z));
+    float X = fmaf(t, dvx, -vx.w);
+    float Y = fmaf(t, dvy, -vy.w);
+    float mX = (X > 0.f ? r.x : r.y) - fabsf(X);
+    float mY = (Y > 0.f ? r.z : r.w) - fabsf(Y);
+    bool sx = mX < mY;
+    float m = sx ? mX : mY;
+    if (m < -c.reject) return false;
+    float w;
+    if (m >= 0.f) {
+        w = 1.f;
+    } else if (c.hard) {
+        return false;
+    } else {
+        // 2 sigmoid(x) = 2 e^x / (1 + e^x) for x = 5 lambda m < 0
+        float e = __expf(c.lam5 * m);
+        w = __fdividef(2.f * e, 1.f + e);
+    }
+    if (!(w >= c.w_min)) return false;
+    o.t = t; o.w = w; o.m = m; o.den = den;
+    o.sideX = sx;
+    o.P = sx ? X : Y;
+    o.dv = sx ? dvx : dvy;
+    o.pos = o.P > 0.f;
+    return true;
+}
+
+// (t, id) lexicographic order of candidates.
+__device__ __forceinline__ bool cand_less(float ta, int ia, float tb, int ib)
+{
+    return ta < tb || (ta == tb && ia < ib);
+}
+
+}  // namespace ps

@@ -1,0 +1,779 @@
+// ps_splat.cu -- forward and backward splatting, render loss.
+//
+// Forward (Sec. 3.2, Eq. 4, 6-9, 11-13).  One CTA renders one tile of
+// tile_w x tile_h pixels, one thread per pixel.  The tile's record list
+// (sorted by depth key, ps_bin.cu) is staged through shared memory in batches;
+// every thread intersects its ray with each staged plane and keeps the pairs
+// that survive the w >= w_min filter.  The M nearest pairs by (t, record id)
+// are composited front to back in exact order with a small sorted register
+// buffer: a pending pair is composited as soon as its depth is below the key
+// of the next list entry (keys bound every later depth from below).  If the
+// buffer overflows, the largest pair is dropped and remembered; compositing
+// stops at the smallest dropped pair and the pixel walks the list again from
+// the last composited pair (each such pass composites at least one pair, so
+// there are at most M + 1 passes).  A pixel stops when T reaches 0 (a plane
+// with w = 1 in front, exact in FP32) or M pairs are composited; a CTA stops
+// when all its pixels have.
+//
+// Backward.  The same walk (bit-identical arithmetic) rebuilds each pixel's
+// composited list and pushes (record, T_j) on a per-pixel stack in shared
+// memory; the adjoint of Eq. 11-13 is then taken back to front:
+//   A_j = w_j t_j + (1 - w_j) A_{j+1},  dD/dw_j = T_j (t_j - A_{j+1}),
+//   dD/dt_j = T_j w_j,  dN/dn_j = T_j w_j,  and the same for N with n_j,
+// so nothing is divided by 1 - w_j.  Each pair's gradient is chained through
+// Eq. 9, 7-8, 6 and 4 into the 16 record floats, summed over the lanes of a
+// warp that hold the same record, and added to a per-record accumulator; a
+// second kernel chains the records through the camera transform and Eq. 2-3
+// into the world parameters.
+#include "ps_internal.cuh"
+
+using namespace ps;
+
+namespace {
+
+constexpr int kPend = 8;                  // pending-pair buffer per pixel
+constexpr unsigned kFull = 0xffffffffu;
+
+struct SplatArgs {
+    const ps_view* views;
+    int n_views;
+    const float4* rec;        // [R][4]
+    const float* key;         // [R]
+    const int* tile_ptr;
+    const int* tile_ent;
+    long long capacity;
+    SplatConst c;
+    int M;
+    // forward outputs
+    float* depth;
+    float* normal;
+    float* alpha;
+    // backward inputs / outputs
+    const float* dLdD;
+    const float* dLdN;
+    float4* g_rec;            // [R][4]
+    int* status;
+};
+
+template <int NT>
+struct Smem {
+    static constexpr int kBatch = NT < 128 ? NT : 128;
+    float4 rec[kBatch][4];
+    int id[kBatch];
+    float key[kBatch + 1];
+    int view, beg, end;
+    int any;
+};
+
+// Per-pixel walk state.
+struct Walk {
+    float T;
+    int cnt;
+    bool done;
+    int nb;
+    float bt[kPend], bw[kPend];
+    int bid[kPend];
+    bool have_floor;
+    float ft;
+    int fid;
+    bool ovf;
+    float ot;
+    int oid;
+};
+
+__device__ __forceinline__ void drop_note(Walk& s, float t, int id)
+{
+    if (!s.ovf || cand_less(t, id, s.ot, s.oid)) { s.ot = t; s.oid = id; }
+    s.ovf = true;
+}
+
+__device__ __forceinline__ void pend_insert(Walk& s, float t, float w, int id)
+{
+    if (s.nb == kPend) {
+        if (!cand_less(t, id, s.bt[kPend - 1], s.bid[kPend - 1])) { drop_note(s, t, id); return; }
+        drop_note(s, s.bt[kPend - 1], s.bid[kPend - 1]);
+        s.nb = kPend - 1;
+    }
+    bool placed = false;
+#pragma unroll
+    for (int i = kPend - 1; i >= 1; --i) {
+        if (i <= s.nb) {
+            if (cand_less(t, id, s.bt[i - 1], s.bid[i - 1])) {
+                s.bt[i] = s.bt[i - 1]; s.bw[i] = s.bw[i - 1]; s.bid[i] = s.bid[i - 1];
+            } else if (!placed) {
+                s.bt[i] = t; s.bw[i] = w; s.bid[i] = id; placed = true;
+            }
+        }
+    }
+    if (!placed) { s.bt[0] = t; s.bw[0] = w; s.bid[0] = id; }
+    ++s.nb;
+}
+
+__device__ __forceinline__ void pend_pop(Walk& s)
+{
+#pragma unroll
+    for (int i = 0; i < kPend - 1; ++i) {
+        s.bt[i] = s.bt[i + 1]; s.bw[i] = s.bw[i + 1]; s.bid[i] = s.bid[i + 1];
+    }
+    --s.nb;
+}
+
+// Forward accumulators.
+struct Accum {
+    float D, N0, N1, N2, A;
+};
+
+template <bool BWD>
+struct Sink {
+    // forward: composite into Accum; backward: push (record, T) on the stack
+    Accum acc;
+    int2* stk;        // [M][NT] (backward)
+    int stride;       // NT
+};
+
+template <bool BWD>
+__device__ __forceinline__ void composite(Walk& s, Sink<BWD>& k, const float4* __restrict__ rec,
+                                          float t, float w, int id, int M)
+{
+    if constexpr (BWD) {
+        k.stk[s.cnt * k.stride] = make_int2(id, __float_as_int(s.T));
+    } else {
+        const float4 n = __ldg(&rec[(size_t)id * 4]);
+        const float tw = s.T * w;
+        k.acc.D = fmaf(tw, t, k.acc.D);
+        k.acc.N0 = fmaf(tw, n.x, k.acc.N0);
+        k.acc.N1 = fmaf(tw, n.y, k.acc.N1);
+        k.acc.N2 = fmaf(tw, n.z, k.acc.N2);
+        k.acc.A = k.acc.A + tw;
+    }
+    s.T = s.T * (1.f - w);
+    ++s.cnt;
+    s.have_floor = true;
+    s.ft = t;
+    s.fid = id;
+    if (s.cnt >= M || s.T == 0.f) s.done = true;
+}
+
+template <bool BWD>
+__device__ __forceinline__ void flush(Walk& s, Sink<BWD>& k, const float4* __restrict__ rec,
+                                      float bound, int M)
+{
+    while (s.nb > 0 && !s.done) {
+        if (!(s.bt[0] < bound)) break;
+        if (s.ovf && !cand_less(s.bt[0], s.bid[0], s.ot, s.oid)) break;
+        const float t = s.bt[0], w = s.bw[0];
+        const int id = s.bid[0];
+        pend_pop(s);
+        composite<BWD>(s, k, rec, t, w, id, M);
+    }
+}
+
+// Walks the tile list for one pixel (all threads of the CTA call it together).
+template <int NT, bool BWD>
+__device__ __forceinline__ void walk_tile(const SplatArgs& a, Smem<NT>& sm, Walk& s, Sink<BWD>& k,
+                                          float dx, float dy)
+{
+    constexpr int B = Smem<NT>::kBatch;
+    const int tid = threadIdx.x;
+    const int beg = sm.beg, end = sm.end;
+    const float kMargin = 1.f - 1.f / 4096.f;
+    for (int pass = 0; pass <= a.M + 1; ++pass) {
+        for (int base = beg; base < end; base += B) {
+            __syncthreads();
+            if (tid < B) {
+                const int i = base + tid;
+                if (i < end) {
+                    const int id = __ldg(&a.tile_ent[i]);
+                    sm.id[tid] = id;
+                    sm.key[tid] = __ldg(&a.key[id]);
+                    const float4* r = a.rec + (size_t)id * 4;
+                    sm.rec[tid][0] = __ldg(r + 0);
+                    sm.rec[tid][1] = __ldg(r + 1);
+                    sm.rec[tid][2] = __ldg(r + 2);
+                    sm.rec[tid][3] = __ldg(r + 3);
+                }
+            }
+            if (tid == 0)
+                sm.key[B] = (base + B < end) ? __ldg(&a.key[__ldg(&a.tile_ent[base + B])]) : INFINITY;
+            __syncthreads();
+            const int nbat = min(B, end - base);
+            if (!s.done) {
+                for (int e = 0; e < nbat; ++e) {
+                    PairEval pe;
+                    const int id = sm.id[e];
+                    if (eval_pair(sm.rec[e][0], sm.rec[e][1], sm.rec[e][2], sm.rec[e][3], dx, dy,
+                                  a.c, pe)) {
+                        if (!s.have_floor || cand_less(s.ft, s.fid, pe.t, id))
+                            pend_insert(s, pe.t, pe.w, id);
+                    }
+                    const float nk = (e + 1 < nbat) ? sm.key[e + 1] : sm.key[B];
+                    if (s.nb > 0) flush<BWD>(s, k, a.rec, nk * kMargin, a.M);
+                    if (s.done) break;
+                }
+            }
+            if (__syncthreads_and(s.done)) break;
+        }
+        // end of list: everything pending below the smallest dropped pair is final
+        flush<BWD>(s, k, a.rec, INFINITY, a.M);
+        const bool again = !s.done && s.ovf;
+        if (!again) s.done = true;
+        if (!__syncthreads_or(again)) break;
+        if (again) { s.ovf = false; s.nb = 0; }
+    }
+}
+
+template <int TW, int TH, bool BWD>
+__global__ void __launch_bounds__(TW * TH) k_splat(SplatArgs a)
+{
+    constexpr int NT = TW * TH;
+    __shared__ Smem<NT> sm;
+    extern __shared__ int2 dyn_stk[];   // backward: [M][NT]
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    if (tid == 0) {
+        const int v = view_of_tile(a.views, a.n_views, tile);
+        sm.view = v;
+        const long long b = __ldg(&a.tile_ptr[tile]), e = __ldg(&a.tile_ptr[tile + 1]);
+        sm.beg = (int)min(b, a.capacity);
+        sm.end = (int)min(e, a.capacity);
+    }
+    __syncthreads();
+    const ps_view* vw = a.views + sm.view;
+    const int W = __ldg(&vw->W), H = __ldg(&vw->H);
+    const int tx_n = __ldg(&vw->tiles_x);
+    const int lt = tile - __ldg(&vw->tile_off);
+    const int px = (lt % tx_n) * TW + tid % TW;
+    const int py = (lt / tx_n) * TH + tid / TW;
+    const bool inside = px < W && py < H;
+    const float fx = __ldg(&vw->fx), fy = __ldg(&vw->fy);
+    const float cx = __ldg(&vw->cx), cy = __ldg(&vw->cy);
+    const float dx = __fdiv_rn((float)px + 0.5f - cx, fx);
+    const float dy = __fdiv_rn((float)py + 0.5f - cy, fy);
+    const long long pix = __ldg(&vw->pix_off) + (long long)py * W + px;
+
+    Walk s;
+    s.T = 1.f; s.cnt = 0; s.nb = 0; s.have_floor = false; s.ft = 0.f; s.fid = 0;
+    s.ovf = false; s.ot = 0.f; s.oid = 0;
+    s.done = !inside;
+    Sink<BWD> k;
+    k.acc = Accum{0.f, 0.f, 0.f, 0.f, 0.f};
+    k.stk = dyn_stk + tid;
+    k.stride = NT;
+    float gD = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
+    if constexpr (BWD) {
+        if (inside) {
+            gD = __ldg(&a.dLdD[pix]);
+            gN0 = __ldg(&a.dLdN[3 * pix + 0]);
+            gN1 = __ldg(&a.dLdN[3 * pix + 1]);
+            gN2 = __ldg(&a.dLdN[3 * pix + 2]);
+            if (gD == 0.f && gN0 == 0.f && gN1 == 0.f && gN2 == 0.f) s.done = true;
+        }
+    }
+    walk_tile<NT, BWD>(a, sm, s, k, dx, dy);
+
+    if constexpr (!BWD) {
+        if (inside) {
+            a.depth[pix] = k.acc.D;
+            a.normal[3 * pix + 0] = k.acc.N0;
+            a.normal[3 * pix + 1] = k.acc.N1;
+            a.normal[3 * pix + 2] = k.acc.N2;
+            if (a.alpha) a.alpha[pix] = k.acc.A;
+        }
+    } else {
+        // back to front over the stack
+        const int lane = tid & 31;
+        const int cnt = inside ? s.cnt : 0;
+        int wmax = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, o));
+        float A = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
+        const float lam5 = a.c.lam5;
+        for (int j = wmax - 1; j >= 0; --j) {
+            const bool act = j < cnt;
+            float g[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) g[q] = 0.f;
+            int id = -1;
+            if (act) {
+                const int2 e = dyn_stk[j * NT + tid];
+                id = e.x;
+                const float Tj = __int_as_float(e.y);
+                const float4* r = a.rec + (size_t)id * 4;
+                const float4 n = __ldg(r + 0), vx = __ldg(r + 1), vy = __ldg(r + 2), rr = __ldg(r + 3);
+                PairEval pe;
+                eval_pair(n, vx, vy, rr, dx, dy, a.c, pe);   // same arithmetic as the walk
+                const float t = pe.t, w = pe.w;
+                const float gw = Tj * (gD * (t - A) + gN0 * (n.x - B0) + gN1 * (n.y - B1) +
+                                       gN2 * (n.z - B2));
+                const float Tw = Tj * w;
+                float gt = Tw * gD;
+                float gnx = Tw * gN0, gny = Tw * gN1, gnz = Tw * gN2;
+                A = fmaf(w, t, (1.f - w) * A);
+                B0 = fmaf(w, n.x, (1.f - w) * B0);
+                B1 = fmaf(w, n.y, (1.f - w) * B1);
+                B2 = fmaf(w, n.z, (1.f - w) * B2);
+                // Eq. 7-9: w = 2 sigmoid(5 lambda m) below the clamp, dw/dm = 5 lambda w (1 - w/2)
+                const float gm = (pe.m < 0.f) ? gw * lam5 * w * (1.f - 0.5f * w) : 0.f;
+                // m = r_side - |P|: radius gets gm, P gets -gm sgn(P)
+                const int ridx = (pe.sideX ? 0 : 2) + (pe.pos ? 0 : 1);
+                const float gP = (pe.P > 0.f) ? -gm : ((pe.P < 0.f) ? gm : 0.f);
+                // Eq. 6 in record form: P = t (d . v_c) - a
+                gt = fmaf(gP, pe.dv, gt);
+                const float gv = gP * t;
+                // Eq. 4: t = s / (d . n_c)
+                const float gs = gt / pe.den;
+                const float gden = -gs * t;
+                gnx = fmaf(gden, dx, gnx);
+                gny = fmaf(gden, dy, gny);
+                gnz = gnz + gden;
+                g[0] = gnx; g[1] = gny; g[2] = gnz; g[3] = gs;
+                const int vo = pe.sideX ? 4 : 8;
+#pragma unroll
+                for (int q = 4; q < 12; q += 4) {
+                    if (q == vo) {
+                        g[q + 0] = gv * dx;
+                        g[q + 1] = gv * dy;
+                        g[q + 2] = gv;
+                        g[q + 3] = -gP;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) g[12 + q] = (q == ridx) ? gm : 0.f;
+            }
+            // warp aggregation: one atomic set per distinct record
+            const unsigned actm = __ballot_sync(kFull, act);
+            if (actm == 0) continue;
+            const unsigned peers = __match_any_sync(kFull, id);
+            const bool uni = __all_sync(kFull, !act || peers == actm);
+            if (uni) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    float x = g[q];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+                    g[q] = x;
+                }
+                const int leader = __ffs(actm) - 1;
+                id = __shfl_sync(kFull, id, leader);
+                if (lane == leader) {
+                    float4* dst = a.g_rec + (size_t)id * 4;
+                    atomicAdd(dst + 0, make_float4(g[0], g[1], g[2], g[3]));
+                    atomicAdd(dst + 1, make_float4(g[4], g[5], g[6], g[7]));
+                    atomicAdd(dst + 2, make_float4(g[8], g[9], g[10], g[11]));
+                    atomicAdd(dst + 3, make_float4(g[12], g[13], g[14], g[15]));
+                }
+            } else if (act) {
+                float4* dst = a.g_rec + (size_t)id * 4;
+                atomicAdd(dst + 0, make_float4(g[0], g[1], g[2], g[3]));
+                atomicAdd(dst + 1, make_float4(g[4], g[5], g[6], g[7]));
+                atomicAdd(dst + 2, make_float4(g[8], g[9], g[10], g[11]));
+                atomicAdd(dst + 3, make_float4(g[12], g[13], g[14], g[15]));
+            }
+        }
+    }
+}
+
+// Work counts (diagnostic): full walk of every tile list, no early exit.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) k_count_pairs(SplatArgs a, unsigned long long* counts)
+{
+    constexpr int NT = TW * TH;
+    __shared__ Smem<NT> sm;
+    __shared__ unsigned long long red[3];
+    constexpr int B = Smem<NT>::kBatch;
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    if (tid == 0) {
+        sm.view = view_of_tile(a.views, a.n_views, tile);
+        const long long b = __ldg(&a.tile_ptr[tile]), e = __ldg(&a.tile_ptr[tile + 1]);
+        sm.beg = (int)min(b, a.capacity);
+        sm.end = (int)min(e, a.capacity);
+        red[0] = red[1] = red[2] = 0ull;
+    }
+    __syncthreads();
+    const ps_view* vw = a.views + sm.view;
+    const int W = __ldg(&vw->W), H = __ldg(&vw->H);
+    const int tx_n = __ldg(&vw->tiles_x);
+    const int lt = tile - __ldg(&vw->tile_off);
+    const int px = (lt % tx_n) * TW + tid % TW;
+    const int py = (lt / tx_n) * TH + tid / TW;
+    const bool inside = px < W && py < H;
+    const float dx = __fdiv_rn((float)px + 0.5f - __ldg(&vw->cx), __ldg(&vw->fx));
+    const float dy = __fdiv_rn((float)py + 0.5f - __ldg(&vw->cy), __ldg(&vw->fy));
+    unsigned long long n_cand = 0, n_front = 0;
+    bool have_op = false;
+    float op_t = 0.f;
+    int op_id = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int base = sm.beg; base < sm.end; base += B) {
+            __syncthreads();
+            if (tid < B && base + tid < sm.end) {
+                const int id = __ldg(&a.tile_ent[base + tid]);
+                sm.id[tid] = id;
+                const float4* r = a.rec + (size_t)id * 4;
+                sm.rec[tid][0] = __ldg(r + 0); sm.rec[tid][1] = __ldg(r + 1);
+                sm.rec[tid][2] = __ldg(r + 2); sm.rec[tid][3] = __ldg(r + 3);
+            }
+            __syncthreads();
+            const int nbat = min(B, sm.end - base);
+            if (inside) {
+                for (int e = 0; e < nbat; ++e) {
+                    PairEval pe;
+                    const int id = sm.id[e];
+                    if (!eval_pair(sm.rec[e][0], sm.rec[e][1], sm.rec[e][2], sm.rec[e][3], dx, dy,
+                                   a.c, pe))
+                        continue;
+                    if (pass == 0) {
+                        ++n_cand;
+                        if (pe.w == 1.f && (!have_op || cand_less(pe.t, id, op_t, op_id))) {
+                            have_op = true; op_t = pe.t; op_id = id;
+                        }
+                    } else if (!have_op || !cand_less(op_t, op_id, pe.t, id)) {
+                        ++n_front;
+                    }
+                }
+            }
+        }
+    }
+    const unsigned long long tested = inside ? (unsigned long long)(sm.end - sm.beg) : 0ull;
+    const unsigned long long comp = n_front < (unsigned long long)a.M ? n_front : (unsigned long long)a.M;
+    atomicAdd(&red[0], tested);
+    atomicAdd(&red[1], n_cand);
+    atomicAdd(&red[2], comp);
+    __syncthreads();
+    if (tid < 3) atomicAdd(&counts[tid], red[tid]);
+}
+
+// Per-record gradient -> world parameters (camera transform, Eq. 2-3 and the
+// quaternion normalisation).
+struct ChainArgs {
+    const ps_view* views;
+    const float* center;
+    const float* quat;
+    const float* radii;
+    const float4* g_rec;
+    float* g_center;
+    float* g_quat;
+    float* g_radii;
+    int single_radii;
+};
+
+__global__ void __launch_bounds__(128) k_chain(ChainArgs a)
+{
+    const int v = blockIdx.y;
+    const ps_view* vw = a.views + v;
+    const int K = __ldg(&vw->K);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const size_t r = (size_t)__ldg(&vw->rec_off) + k;
+    const float4 g0 = a.g_rec[4 * r + 0], g1 = a.g_rec[4 * r + 1];
+    const float4 g2 = a.g_rec[4 * r + 2], g3 = a.g_rec[4 * r + 3];
+    if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
+        g1.z == 0.f && g1.w == 0.f && g2.x == 0.f && g2.y == 0.f && g2.z == 0.f && g2.w == 0.f &&
+        g3.x == 0.f && g3.y == 0.f && g3.z == 0.f && g3.w == 0.f)
+        return;
+    const int p = __ldg(&vw->plane_off) + k;
+    float R[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) R[i] = __ldg(&vw->w2c[i]);
+    const float q0 = __ldg(&a.quat[4 * p + 0]), q1 = __ldg(&a.quat[4 * p + 1]);
+    const float q2 = __ldg(&a.quat[4 * p + 2]), q3 = __ldg(&a.quat[4 * p + 3]);
+    const float qs = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    if (!(qs > 0.f) || !isfinite(qs)) return;
+    const float w = q0 / qs, x = q1 / qs, y = q2 / qs, z = q3 / qs;
+    // world axes: columns of the Hamilton matrix (Eq. 2-3)
+    const float vx[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y)};
+    const float vy[3] = {2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x)};
+    const float nn[3] = {2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y)};
+    const float pw[3] = {__ldg(&a.center[3 * p + 0]), __ldg(&a.center[3 * p + 1]),
+                         __ldg(&a.center[3 * p + 2])};
+    float pc[3], vxc[3], vyc[3], nc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        pc[i] = R[4 * i] * pw[0] + R[4 * i + 1] * pw[1] + R[4 * i + 2] * pw[2] + R[4 * i + 3];
+        vxc[i] = R[4 * i] * vx[0] + R[4 * i + 1] * vx[1] + R[4 * i + 2] * vx[2];
+        vyc[i] = R[4 * i] * vy[0] + R[4 * i + 1] * vy[1] + R[4 * i + 2] * vy[2];
+        nc[i] = R[4 * i] * nn[0] + R[4 * i + 1] * nn[1] + R[4 * i + 2] * nn[2];
+    }
+    // record = {n_c, n_c.p_c, v^x_c, v^x_c.p_c, v^y_c, v^y_c.p_c, r}
+    const float gs = g0.w, gax = g1.w, gay = g2.w;
+    const float gnc[3] = {g0.x + gs * pc[0], g0.y + gs * pc[1], g0.z + gs * pc[2]};
+    const float gvxc[3] = {g1.x + gax * pc[0], g1.y + gax * pc[1], g1.z + gax * pc[2]};
+    const float gvyc[3] = {g2.x + gay * pc[0], g2.y + gay * pc[1], g2.z + gay * pc[2]};
+    float gpc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gpc[i] = gs * nc[i] + gax * vxc[i] + gay * vyc[i];
+    // camera -> world: multiply by R^T
+    float gp[3], gvx[3], gvy[3], gn[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gp[i] = R[i] * gpc[0] + R[4 + i] * gpc[1] + R[8 + i] * gpc[2];
+        gvx[i] = R[i] * gvxc[0] + R[4 + i] * gvxc[1] + R[8 + i] * gvxc[2];
+        gvy[i] = R[i] * gvyc[0] + R[4 + i] * gvyc[1] + R[8 + i] * gvyc[2];
+        gn[i] = R[i] * gnc[0] + R[4 + i] * gnc[1] + R[8 + i] * gnc[2];
+    }
+    // G[i][c] = dL/dR_ic with columns (v^x, v^y, n)
+    const float G00 = gvx[0], G10 = gvx[1], G20 = gvx[2];
+    const float G01 = gvy[0], G11 = gvy[1], G21 = gvy[2];
+    const float G02 = gn[0], G12 = gn[1], G22 = gn[2];
+    const float gw = 2.f * (-z * G01 + y * G02 + z * G10 - x * G12 - y * G20 + x * G21);
+    const float gx = 2.f * (y * G01 + z * G02 + y * G10 - 2.f * x * G11 - w * G12 + z * G20 +
+                            w * G21 - 2.f * x * G22);
+    const float gy = 2.f * (-2.f * y * G00 + x * G01 + w * G02 + x * G10 + z * G12 - w * G20 +
+                            z * G21 - 2.f * y * G22);
+    const float gz = 2.f * (-2.f * z * G00 - w * G01 + x * G02 + w * G10 - 2.f * z * G11 +
+                            y * G12 + x * G20 + y * G21);
+    const float proj = gw * w + gx * x + gy * y + gz * z;
+    atomicAdd(&a.g_center[3 * p + 0], gp[0]);
+    atomicAdd(&a.g_center[3 * p + 1], gp[1]);
+    atomicAdd(&a.g_center[3 * p + 2], gp[2]);
+    atomicAdd(&a.g_quat[4 * p + 0], (gw - w * proj) / qs);
+    atomicAdd(&a.g_quat[4 * p + 1], (gx - x * proj) / qs);
+    atomicAdd(&a.g_quat[4 * p + 2], (gy - y * proj) / qs);
+    atomicAdd(&a.g_quat[4 * p + 3], (gz - z * proj) / qs);
+    float gr0 = g3.x, gr1 = g3.y, gr2 = g3.z, gr3 = g3.w;
+    if (a.single_radii) { gr0 += gr1; gr1 = 0.f; gr2 += gr3; gr3 = 0.f; }
+    atomicAdd(&a.g_radii[4 * p + 0], gr0);
+    atomicAdd(&a.g_radii[4 * p + 1], gr1);
+    atomicAdd(&a.g_radii[4 * p + 2], gr2);
+    atomicAdd(&a.g_radii[4 * p + 3], gr3);
+}
+
+// Render loss, Eq. 14.
+struct LossArgs {
+    const ps_view* views;
+    const float* depth;
+    const float* normal;
+    const float* gt_depth;
+    const float* gt_normal;
+    float* dLdD;
+    float* dLdN;
+    double* view_sums;
+    float a_cos, a_l1n, a_depth;
+};
+
+__device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
+
+__global__ void __launch_bounds__(256) k_loss(LossArgs a)
+{
+    const int v = blockIdx.y;
+    const ps_view* vw = a.views + v;
+    const long long HW = (long long)__ldg(&vw->H) * __ldg(&vw->W);
+    const long long off = __ldg(&vw->pix_off);
+    float sc = 0.f, sl = 0.f, sd = 0.f, cnt = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < HW;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long p = off + i;
+        const float Dg = __ldg(&a.gt_depth[p]);
+        if (!(Dg > 0.f)) {
+            a.dLdD[p] = 0.f;
+            a.dLdN[3 * p + 0] = 0.f; a.dLdN[3 * p + 1] = 0.f; a.dLdN[3 * p + 2] = 0.f;
+            continue;
+        }
+        const float D = __ldg(&a.depth[p]);
+        const float N0 = __ldg(&a.normal[3 * p]), N1 = __ldg(&a.normal[3 * p + 1]),
+                    N2 = __ldg(&a.normal[3 * p + 2]);
+        const float G0 = __ldg(&a.gt_normal[3 * p]), G1 = __ldg(&a.gt_normal[3 * p + 1]),
+                    G2 = __ldg(&a.gt_normal[3 * p + 2]);
+        const float c = 1.f - (N0 * G0 + N1 * G1 + N2 * G2);
+        const float e0 = N0 - G0, e1 = N1 - G1, e2 = N2 - G2;
+        const float dd = D - Dg;
+        sc += fabsf(c);
+        sl += fabsf(e0) + fabsf(e1) + fabsf(e2);
+        sd += fabsf(dd);
+        cnt += 1.f;
+        a.dLdD[p] = a.a_depth * sgnf(dd);
+        const float sc_ = -a.a_cos * sgnf(c);
+        a.dLdN[3 * p + 0] = sc_ * G0 + a.a_l1n * sgnf(e0);
+        a.dLdN[3 * p + 1] = sc_ * G1 + a.a_l1n * sgnf(e1);
+        a.dLdN[3 * p + 2] = sc_ * G2 + a.a_l1n * sgnf(e2);
+    }
+    // block reduction in double
+    __shared__ double red[4][8];
+    double x[4] = {sc, sl, sd, cnt};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_xor_sync(kFull, x[q], o);
+        if (lane == 0) red[q][wid] = x[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[threadIdx.x][i];
+        atomicAdd(&a.view_sums[4 * v + threadIdx.x], s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+template <int TW, int TH>
+cudaError_t launch_splat(const SplatArgs& a, int n_tiles, bool bwd, int M, cudaStream_t st)
+{
+    constexpr int NT = TW * TH;
+    if (!bwd) {
+        k_splat<TW, TH, false><<<n_tiles, NT, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    const size_t dyn = sizeof(int2) * (size_t)M * NT;
+    static int configured_max[64] = {0};   // per device: largest dynamic smem set so far
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && configured_max[dev] < (int)dyn) {
+        cudaError_t e = cudaFuncSetAttribute(k_splat<TW, TH, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        configured_max[dev] = (int)dyn;
+    }
+    k_splat<TW, TH, true><<<n_tiles, NT, dyn, st>>>(a);
+    return cudaGetLastError();
+}
+
+ps_status check_common(const ps_frame* f, const ps_settings* s, const float* rec, const float* key,
+                       const int* tile_ptr, const int* tile_ent, long long capacity)
+{
+    if (!f || !s || !rec || !key || !tile_ptr || !f->views) return PS_ERR_ARG;
+    if (capacity < 0 || (capacity > 0 && !tile_ent)) return PS_ERR_ARG;
+    if (f->n_tiles <= 0 || f->n_views <= 0) return PS_ERR_ARG;
+    if (s->M < 1 || s->M > PS_MAX_M) return PS_ERR_ARG;
+    if (!(s->lambda > 0.f) || !(s->w_min > 0.f) || !(s->w_min < 1.f)) return PS_ERR_ARG;
+    if (!(s->z_near > 0.f) || !(s->z_far > s->z_near) || !(s->delta >= 0.0)) return PS_ERR_ARG;
+    const int tw = s->tile_w, th = s->tile_h;
+    if (!((tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8))) return PS_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(rec) & 15) return PS_ERR_ARG;
+    return PS_OK;
+}
+
+SplatConst make_const(const ps_settings* s)
+{
+    SplatConst c;
+    c.lam5 = 5.f * s->lambda;
+    c.w_min = s->w_min;
+    c.z_near = s->z_near;
+    c.z_far = s->z_far;
+    c.hard = (s->flags & PS_HARD) ? 1 : 0;
+    c.reject = c.hard ? 0.f : (float)(s->delta * 1.02 + 1e-6);
+    return c;
+}
+
+cudaError_t dispatch(const SplatArgs& a, const ps_settings* s, int n_tiles, bool bwd, cudaStream_t st)
+{
+    if (s->tile_w == 16) return launch_splat<16, 16>(a, n_tiles, bwd, s->M, st);
+    if (s->tile_w == 8) return launch_splat<8, 8>(a, n_tiles, bwd, s->M, st);
+    return launch_splat<32, 8>(a, n_tiles, bwd, s->M, st);
+}
+
+template <int TW, int TH>
+cudaError_t launch_count(const SplatArgs& a, int n_tiles, unsigned long long* counts, cudaStream_t st)
+{
+    k_count_pairs<TW, TH><<<n_tiles, TW * TH, 0, st>>>(a, counts);
+    return cudaGetLastError();
+}
+
+inline size_t bwd_ws(const ps_frame* f) { return sizeof(float4) * 4 * (size_t)f->n_records; }
+
+}  // namespace
+
+extern "C" ps_status ps_splat_fwd(const ps_frame* f, const ps_settings* s, const float* rec,
+                                  const float* key, const int* tile_ptr, const int* tile_ent,
+                                  long long capacity, float* depth, float* normal, float* alpha,
+                                  int* d_status, ps_stream stream)
+{
+    ps_status e = check_common(f, s, rec, key, tile_ptr, tile_ent, capacity);
+    if (e != PS_OK) return e;
+    if (!depth || !normal) return PS_ERR_ARG;
+    SplatArgs a{};
+    a.views = f->views; a.n_views = f->n_views;
+    a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
+    a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
+    a.c = make_const(s); a.M = s->M;
+    a.depth = depth; a.normal = normal; a.alpha = alpha; a.status = d_status;
+    if (dispatch(a, s, f->n_tiles, false, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return PS_ERR_CUDA;
+    return PS_OK;
+}
+
+extern "C" size_t ps_bwd_workspace_bytes(const ps_frame* f)
+{
+    if (!f || f->n_records < 0) return 0;
+    return bwd_ws(f);
+}
+
+extern "C" ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* f, const ps_settings* s,
+                                  const float* rec, const float* key, const int* tile_ptr,
+                                  const int* tile_ent, long long capacity, const float* dLdD,
+                                  const float* dLdN, float* g_center, float* g_quat, float* g_radii,
+                                  void* ws, size_t ws_bytes, int* d_status, ps_stream stream)
+{
+    ps_status e = check_common(f, s, rec, key, tile_ptr, tile_ent, capacity);
+    if (e != PS_OK) return e;
+    if (!planes || !planes->center || !planes->quat || !planes->radii) return PS_ERR_ARG;
+    if (!dLdD || !dLdN || !g_center || !g_quat || !g_radii || !ws) return PS_ERR_ARG;
+    if (s->flags & PS_HARD) return PS_ERR_ARG;
+    if (ws_bytes < bwd_ws(f) || (reinterpret_cast<uintptr_t>(ws) & 15)) return PS_ERR_ARG;
+    if (f->n_records == 0) return PS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, bwd_ws(f), st));
+    SplatArgs a{};
+    a.views = f->views; a.n_views = f->n_views;
+    a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
+    a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
+    a.c = make_const(s); a.M = s->M;
+    a.dLdD = dLdD; a.dLdN = dLdN; a.g_rec = reinterpret_cast<float4*>(ws); a.status = d_status;
+    if (dispatch(a, s, f->n_tiles, true, st) != cudaSuccess) return PS_ERR_CUDA;
+    ChainArgs c;
+    c.views = f->views; c.center = planes->center; c.quat = planes->quat; c.radii = planes->radii;
+    c.g_rec = a.g_rec; c.g_center = g_center; c.g_quat = g_quat; c.g_radii = g_radii;
+    c.single_radii = (s->flags & PS_SINGLE_RADII) ? 1 : 0;
+    dim3 grid((f->max_K + 127) / 128, f->n_views);
+    k_chain<<<grid, 128, 0, st>>>(c);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
+
+extern "C" ps_status ps_loss(const ps_frame* f, const ps_settings* s, const float* depth,
+                             const float* normal, const float* gt_depth, const float* gt_normal,
+                             float* dLdD, float* dLdN, double* view_sums, ps_stream stream)
+{
+    if (!f || !s || !f->views || !depth || !normal || !gt_depth || !gt_normal || !dLdD || !dLdN ||
+        !view_sums)
+        return PS_ERR_ARG;
+    if (f->n_views <= 0) return PS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PS_CUDA_CHECK(cudaMemsetAsync(view_sums, 0, sizeof(double) * 4 * (size_t)f->n_views, st));
+    LossArgs a;
+    a.views = f->views; a.depth = depth; a.normal = normal; a.gt_depth = gt_depth;
+    a.gt_normal = gt_normal; a.dLdD = dLdD; a.dLdN = dLdN; a.view_sums = view_sums;
+    a.a_cos = s->a_cos; a.a_l1n = s->a_l1n; a.a_depth = s->a_depth;
+    const long long per_view = (f->n_pixels + f->n_views - 1) / f->n_views;
+    int bx = (int)((per_view + 256 * 8 - 1) / (256 * 8));
+    if (bx < 1) bx = 1;
+    if (bx > 1024) bx = 1024;
+    k_loss<<<dim3(bx, f->n_views), 256, 0, st>>>(a);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
+
+extern "C" ps_status ps_count_pairs(const ps_frame* f, const ps_settings* s, const float* rec,
+                                    const float* key, const int* tile_ptr, const int* tile_ent,
+                                    long long capacity, long long* d_counts, ps_stream stream)
+{
+    ps_status e = check_common(f, s, rec, key, tile_ptr, tile_ent, capacity);
+    if (e != PS_OK) return e;
+    if (!d_counts) return PS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PS_CUDA_CHECK(cudaMemsetAsync(d_counts, 0, 3 * sizeof(long long), st));
+    SplatArgs a{};
+    a.views = f->views; a.n_views = f->n_views;
+    a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
+    a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
+    a.c = make_const(s); a.M = s->M;
+    unsigned long long* c = reinterpret_cast<unsigned long long*>(d_counts);
+    cudaError_t err;
+    if (s->tile_w == 16) err = launch_count<16, 16>(a, f->n_tiles, c, st);
+    else if (s->tile_w == 8) err = launch_count<8, 8>(a, f->n_tiles, c, st);
+    else err = launch_count<32, 8>(a, f->n_tiles, c, st);
+    return err == cudaSuccess ? PS_OK : PS_ERR_CUDA;
+}

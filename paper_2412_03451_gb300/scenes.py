@@ -63,6 +63,7 @@ class Room:
     cams: Cameras
     size: tuple
     boxes: list = field(default_factory=list)
+    axes: tuple = None     # (v^x [K,3], v^y [K,3]) of the ground-truth rectangles, float64
 
 
 # --------------------------------------------------------------------------
@@ -153,6 +154,10 @@ class _RectList:
                           np.asarray(self.hy), np.asarray(self.hy)], axis=1) if K else np.zeros((0, 4))
         return Planes(center.astype(np.float32), quat.astype(np.float32), radii.astype(np.float32))
 
+    def axes(self):
+        K = len(self.c)
+        return (np.stack(self.vx) if K else np.zeros((0, 3)), np.stack(self.vy) if K else np.zeros((0, 3)))
+
 
 def _room_faces(sx, sy, sz):
     """The 6 inner faces of the box [0,sx]x[0,sy]x[0,sz] as (corner, u, v, su, sv)
@@ -230,7 +235,7 @@ def tiny_room(seed: int = 0, H: int = 96, W: int = 128, f: float = 100.0, n_view
         w2c.append(look_at(eye, target))
         intr.append([f, f, W / 2.0, H / 2.0])
     cams = Cameras(np.asarray(w2c, np.float32), np.asarray(intr, np.float32), H, W)
-    return Room(gt, cams, (sx, sy, sz), boxes)
+    return Room(gt, cams, (sx, sy, sz), boxes, rl.axes())
 
 
 def perturb_planes(gt: Planes, seed: int, center_sigma=0.1, angle_sigma_deg=10.0,
@@ -254,9 +259,11 @@ def perturb_planes(gt: Planes, seed: int, center_sigma=0.1, angle_sigma_deg=10.0
 
 def _split_faces(faces, n_target, rng, min_half=0.1, max_half=2.0):
     """Random guillotine splits of the given faces until n_target rectangles.
-    A rectangle is chosen with probability proportional to area * U^2 and cut
-    across its longer side at a random fraction, which spreads the sizes over
-    a wide, roughly log-uniform range."""
+    A splittable rectangle is chosen uniformly at random (regardless of size)
+    and cut across its longer side at a random fraction, which spreads the
+    half-extents over a wide range from min_half upwards (about 0.1-1 m for
+    2,000 rectangles in an 8x10x3 m room: that many rectangles cannot tile the
+    room with sizes log-uniform up to 2 m)."""
     rects = [list(f) for f in faces]   # corner, u, v, su, sv
     # first make every rectangle at most 2*max_half long
     i = 0
@@ -274,12 +281,11 @@ def _split_faces(faces, n_target, rng, min_half=0.1, max_half=2.0):
     guard = 0
     while len(rects) < n_target and guard < 100000:
         guard += 1
-        areas = np.array([r[3] * r[4] for r in rects])
         longest = np.array([max(r[3], r[4]) for r in rects])
         ok = longest >= 4 * min_half
         if not ok.any():
             break
-        wgt = np.where(ok, areas * rng.uniform(size=len(rects)) ** 2, 0.0)
+        wgt = np.where(ok, rng.uniform(size=len(rects)), 0.0)
         j = int(np.argmax(wgt))
         corner, u, v, su, sv = rects[j]
         frac = rng.uniform(0.25, 0.75)
@@ -337,7 +343,7 @@ def large_room(seed: int = 1000, n_rect: int = 2000, size=(8.0, 10.0, 3.0), n_vi
         rl.add(corner + 0.5 * su * u + 0.5 * sv * v, u, v, 0.5 * su, 0.5 * sv)
     gt = rl.planes()
     cams = trajectory_cameras(rng, (sx, sy, sz), boxes, n_views, H, W, f)
-    return Room(gt, cams, (sx, sy, sz), boxes)
+    return Room(gt, cams, (sx, sy, sz), boxes, rl.axes())
 
 
 def trajectory_cameras(rng, size, boxes, n_views, H, W, f, n_ctrl=8, margin=0.8) -> Cameras:
@@ -383,6 +389,25 @@ def backprojected_init(depth: np.ndarray, cams: Cameras, n: int, seed: int,
         pc = np.array([(i + 0.5 - cx) / fx * z, (j + 0.5 - cy) / fy * z, z])
         Rt = cams.w2c[v].astype(np.float64)
         centers[idx] = Rt[:, :3].T @ (pc - Rt[:, 3])
+    quat = random_quats(rng, n)
+    radii = np.full((n, 4), radius)
+    return Planes(centers.astype(np.float32), quat.astype(np.float32), radii.astype(np.float32))
+
+
+def surface_init(room: Room, n: int, seed: int, radius: float = 0.2) -> Planes:
+    """n planes centred at points drawn uniformly (by area) on the ground-truth
+    rectangles of the room, with uniformly random orientation and all radii =
+    radius.  With exact synthetic depth, back-projected depth pixels lie on these
+    rectangles, so this stands in for the "random depth-backprojected points"
+    initialisation without rendering anything."""
+    rng = np.random.default_rng(seed)
+    gt = room.gt
+    vx_all, vy_all = room.axes
+    area = (gt.radii[:, 0] + gt.radii[:, 1]).astype(np.float64) * (gt.radii[:, 2] + gt.radii[:, 3])
+    k = rng.choice(gt.K, size=n, p=area / area.sum())
+    u = rng.uniform(-gt.radii[k, 1], gt.radii[k, 0])
+    v = rng.uniform(-gt.radii[k, 3], gt.radii[k, 2])
+    centers = gt.center[k].astype(np.float64) + u[:, None] * vx_all[k] + v[:, None] * vy_all[k]
     quat = random_quats(rng, n)
     radii = np.full((n, 4), radius)
     return Planes(centers.astype(np.float32), quat.astype(np.float32), radii.astype(np.float32))

@@ -1,0 +1,245 @@
+"""PyTorch driver of libps: buffers, one optimisation step, autograd wrapper.
+
+PyTorch provides device memory and streams; every step of the rendering path
+(projection, binning, forward splat, loss, backward splat, Adam) is a call into
+libps through ``binding``.  The plane parameters of all scenes live in one flat
+float32 buffer laid out as [center P*3 | quat P*4 | radii P*4], so that Adam
+runs as two launches (the radii group is clamped to stay positive, Eq. 1).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+R_MIN = 1e-3          # radii are clamped to >= 1 mm after each Adam step (Eq. 1: r in R^4_+)
+
+
+def planes_to_flat(center, quat, radii, device) -> torch.Tensor:
+    P = int(np.asarray(center).shape[0])
+    flat = np.concatenate([np.asarray(center, np.float32).reshape(-1),
+                           np.asarray(quat, np.float32).reshape(-1),
+                           np.asarray(radii, np.float32).reshape(-1)])
+    assert flat.size == 11 * P
+    return torch.from_numpy(flat).to(device)
+
+
+def flat_views(flat: torch.Tensor, P: int):
+    return flat[:3 * P].view(P, 3), flat[3 * P:7 * P].view(P, 4), flat[7 * P:].view(P, 4)
+
+
+@dataclass
+class StepStats:
+    view_sums: torch.Tensor      # [V,4] f64 (device)
+    required: torch.Tensor       # [1] i64 (device)
+    status: torch.Tensor         # [1] i32 (device)
+
+
+class Renderer:
+    """Owns every buffer of one batch shape (a fixed set of view sizes and
+    scene plane counts) and runs the libps calls on the current stream."""
+
+    def __init__(self, H, W, scene_of_view, plane_ptr, tile=(16, 16), M=30, capacity=None,
+                 device="cuda", flags=0):
+        self.device = torch.device(device)
+        self.H = np.asarray(H, np.int32).reshape(-1)
+        self.W = np.asarray(W, np.int32).reshape(-1)
+        self.V = int(self.H.size)
+        self.scene_of_view = np.asarray(scene_of_view, np.int32).reshape(-1)
+        self.plane_ptr = np.asarray(plane_ptr, np.int32).reshape(-1)
+        self.P = int(self.plane_ptr[-1])
+        self.tile = (int(tile[0]), int(tile[1]))
+        self.M = int(M)
+        self.flags = int(flags)
+        # plan once with identity cameras to learn the totals
+        eye = np.tile(np.concatenate([np.eye(3), np.zeros((3, 1))], 1).astype(np.float32),
+                      (self.V, 1, 1))
+        intr = np.tile(np.array([1, 1, 0, 0], np.float32), (self.V, 1))
+        self._views_host, self.frame = B.ps_plan_views(self.H, self.W, self.scene_of_view,
+                                                       self.plane_ptr, eye, intr, *self.tile)
+        f = self.frame
+        dev = self.device
+        self.views_dev = torch.zeros(self.V * 128, dtype=torch.uint8, device=dev)
+        self.frame.views = self.views_dev.data_ptr()
+        R = f.n_records
+        self.rec = torch.zeros((max(R, 1), 16), dtype=torch.float32, device=dev)
+        self.rect = torch.zeros((max(R, 1), 4), dtype=torch.int32, device=dev)
+        self.key = torch.zeros(max(R, 1), dtype=torch.float32, device=dev)
+        self.tile_ptr = torch.zeros(f.n_tiles + 1, dtype=torch.int32, device=dev)
+        if capacity is None:
+            capacity = max(1 << 16, 64 * f.n_tiles)
+        self._alloc_lists(int(capacity))
+        self.required = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        npix = int(f.n_pixels)
+        self.depth = torch.zeros(npix, dtype=torch.float32, device=dev)
+        self.normal = torch.zeros((npix, 3), dtype=torch.float32, device=dev)
+        self.alpha = torch.zeros(npix, dtype=torch.float32, device=dev)
+        self.dLdD = torch.zeros(npix, dtype=torch.float32, device=dev)
+        self.dLdN = torch.zeros((npix, 3), dtype=torch.float32, device=dev)
+        self.view_sums = torch.zeros((self.V, 4), dtype=torch.float64, device=dev)
+        self.bwd_ws = torch.zeros((B.ps_bwd_workspace_bytes(f) + 255) // 256 * 64,
+                                  dtype=torch.float32, device=dev)
+        self._batches = None
+        self.settings = None
+
+    # -- buffers ---------------------------------------------------------------
+    def _alloc_lists(self, capacity: int):
+        self.capacity = int(capacity)
+        self.tile_ent = torch.zeros(max(self.capacity, 1), dtype=torch.int32, device=self.device)
+        nbytes = B.ps_bin_workspace_bytes(self.frame, self.capacity)
+        self.bin_ws = torch.zeros((nbytes + 255) // 256 * 64, dtype=torch.float32,
+                                  device=self.device)
+
+    def set_cameras(self, w2c, intr):
+        """Re-plans the views with new poses/intrinsics (host) and uploads the
+        128-byte descriptors (synchronous copy of V * 128 bytes)."""
+        self._views_host, fr = B.ps_plan_views(self.H, self.W, self.scene_of_view, self.plane_ptr,
+                                               w2c, intr, *self.tile)
+        raw = np.frombuffer(bytes(self._views_host), dtype=np.uint8).copy()
+        self.views_dev.copy_(torch.from_numpy(raw))
+        self.frame.views = self.views_dev.data_ptr()
+
+    def preplan(self, w2c_batches, intr_batches):
+        """Plans several camera batches of this renderer's shape once and keeps
+        their descriptors on the device; select(i) then switches batches with no
+        host-to-device traffic (and so can run inside a captured graph)."""
+        raws = []
+        for w2c, intr in zip(w2c_batches, intr_batches):
+            vh, _ = B.ps_plan_views(self.H, self.W, self.scene_of_view, self.plane_ptr, w2c, intr,
+                                    *self.tile)
+            raws.append(np.frombuffer(bytes(vh), dtype=np.uint8))
+        self._batches = torch.from_numpy(np.stack(raws)).to(self.device)
+        self.select(0)
+
+    def select(self, i: int):
+        self.frame.views = self._batches[i].data_ptr()
+
+    def make_settings(self, lam, flags=None):
+        fl = self.flags if flags is None else flags
+        delta = 0.0 if (fl & B.PS_HARD) else B.filter_margin(float(np.float32(lam)))
+        self.settings = B.make_settings(lam, delta, M=self.M, tile_w=self.tile[0],
+                                        tile_h=self.tile[1], flags=fl)
+        return self.settings
+
+    def planes_struct(self, flat: torch.Tensor) -> B.PsPlanes:
+        c, q, r = flat_views(flat, self.P)
+        p = B.PsPlanes()
+        p.n_planes = self.P
+        p.center, p.quat, p.radii = c.data_ptr(), q.data_ptr(), r.data_ptr()
+        return p
+
+    # -- the path ----------------------------------------------------------------
+    def project_bin(self, flat: torch.Tensor, lam: float, flags=None):
+        s = self.make_settings(lam, flags)
+        pl = self.planes_struct(flat)
+        B.ps_project_cull(pl, self.frame, s, self.rec, self.rect, self.key, self.status)
+        B.ps_bin_tiles(self.frame, s, self.rect, self.key, self.tile_ptr, self.tile_ent,
+                       self.capacity, self.required, self.bin_ws, self.status)
+
+    def ensure_capacity(self, flat, lam, flags=None, headroom=1.5) -> bool:
+        """Runs projection + binning once and grows the tile-list capacity if it
+        was too small (synchronises).  Returns True if it grew."""
+        self.project_bin(flat, lam, flags)
+        need = int(self.required.item())
+        if need > self.capacity:
+            self._alloc_lists(int(need * headroom) + 1024)
+            self.status.zero_()
+            return True
+        return False
+
+    def splat_forward(self, alpha=True):
+        B.ps_splat_fwd(self.frame, self.settings, self.rec, self.key, self.tile_ptr, self.tile_ent,
+                       self.capacity, self.depth, self.normal, self.alpha if alpha else None,
+                       self.status)
+        return self.depth, self.normal
+
+    def forward(self, flat: torch.Tensor, lam: float, flags=None, alpha=True):
+        self.project_bin(flat, lam, flags)
+        return self.splat_forward(alpha)
+
+    def count_pairs(self, counts: torch.Tensor):
+        """Work counts of the current tile lists (tested, candidate, composited pairs)."""
+        B.ps_count_pairs(self.frame, self.settings, self.rec, self.key, self.tile_ptr,
+                         self.tile_ent, self.capacity, counts)
+
+    def loss(self, gt_depth, gt_normal):
+        B.ps_loss(self.frame, self.settings, self.depth, self.normal, gt_depth, gt_normal,
+                  self.dLdD, self.dLdN, self.view_sums)
+        return self.view_sums
+
+    def backward(self, flat: torch.Tensor, grad_flat: torch.Tensor, dLdD=None, dLdN=None):
+        """Accumulates d(sum dLdD*D + dLdN.N)/dparams into grad_flat (same layout)."""
+        pl = self.planes_struct(flat)
+        gc, gq, gr = flat_views(grad_flat, self.P)
+        B.ps_splat_bwd(pl, self.frame, self.settings, self.rec, self.key, self.tile_ptr,
+                       self.tile_ent, self.capacity, self.dLdD if dLdD is None else dLdD,
+                       self.dLdN if dLdN is None else dLdN, gc, gq, gr, self.bwd_ws, self.status)
+
+
+class PlaneSplatFunction(torch.autograd.Function):
+    """(center, quat, radii) -> (depth, normal) through libps; the backward is
+    the hand-written adjoint kernel ps_splat_bwd."""
+
+    @staticmethod
+    def forward(ctx, flat, renderer: Renderer, lam: float):
+        depth, normal = renderer.forward(flat, lam)
+        ctx.renderer = renderer
+        ctx.save_for_backward(flat)
+        return depth.clone(), normal.clone()
+
+    @staticmethod
+    def backward(ctx, gD, gN):
+        (flat,) = ctx.saved_tensors
+        r = ctx.renderer
+        g = torch.zeros_like(flat)
+        r.backward(flat, g, gD.contiguous(), gN.contiguous())
+        return g, None, None
+
+
+class Fitter:
+    """Adam fit of the planes of a batch (Sec. 3.3): per step, lambda from
+    Eq. 10, render, Eq. 14 loss, backward, Adam with lr 1e-3 for every group."""
+
+    def __init__(self, renderer: Renderer, flat: torch.Tensor, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.r = renderer
+        self.flat = flat
+        self.grad = torch.zeros_like(flat)
+        self.m = torch.zeros_like(flat)
+        self.v = torch.zeros_like(flat)
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+        self.ite = 0
+
+    def step(self, gt_depth, gt_normal, lam=None, marks=None):
+        """One iteration.  If marks is a list, CUDA events are recorded on the
+        current stream after each stage as (name, event) pairs."""
+        def mark(tag):
+            if marks is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                marks.append((tag, e))
+
+        lam = B.lambda_schedule(self.ite) if lam is None else lam
+        r = self.r
+        mark("start")
+        r.project_bin(self.flat, lam)
+        mark("project_bin")
+        r.splat_forward(alpha=False)
+        mark("splat_fwd")
+        r.loss(gt_depth, gt_normal)
+        self.grad.zero_()
+        mark("loss")
+        r.backward(self.flat, self.grad)
+        mark("splat_bwd")
+        P = r.P
+        t = self.ite + 1
+        B.ps_adam_step(self.flat[:7 * P], self.grad[:7 * P], self.m[:7 * P], self.v[:7 * P],
+                       self.lr, self.b1, self.b2, self.eps, t)
+        B.ps_adam_step(self.flat[7 * P:], self.grad[7 * P:], self.m[7 * P:], self.v[7 * P:],
+                       self.lr, self.b1, self.b2, self.eps, t, clamp_min=R_MIN)
+        mark("adam")
+        self.ite += 1
+        return r.view_sums

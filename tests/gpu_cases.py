@@ -1,0 +1,93 @@
+"""Shared helpers of the GPU parity tests: run the libps path and the oracle on
+the same seeded inputs and collect comparable numpy arrays."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import oracle as O
+from paper_2412_03451_gb300 import scenes as S
+
+Z_NEAR32 = float(np.float32(0.01))     # the library takes z_near as f32; the oracle gets the same value
+Z_FAR32 = 100.0
+
+
+def f32(x: float) -> float:
+    return float(np.float32(x))
+
+
+def gpu_run(planes: S.Planes, cams: S.Cameras, lam: float, tile=(16, 16), M=30, flags=0,
+            capacity=None, dLdD=None, dLdN=None, backward=False):
+    """Runs project -> bin -> fwd (-> bwd) on cuda:0 for one scene.  Returns numpy arrays."""
+    import torch
+    from paper_2412_03451_gb300 import splat as SP
+    V = cams.V
+    r = SP.Renderer([cams.H] * V, [cams.W] * V, [0] * V, [0, planes.K], tile=tile, M=M,
+                    capacity=capacity, flags=flags)
+    r.set_cameras(cams.w2c, cams.intr)
+    flat = SP.planes_to_flat(planes.center, planes.quat, planes.radii, "cuda")
+    if capacity is None:
+        r.ensure_capacity(flat, lam)
+    r.status.zero_()
+    r.forward(flat, lam)
+    out = {}
+    if backward:
+        g = torch.zeros_like(flat)
+        gD = torch.from_numpy(np.asarray(dLdD, np.float32).reshape(-1)).cuda()
+        gN = torch.from_numpy(np.asarray(dLdN, np.float32).reshape(-1, 3)).cuda()
+        r.backward(flat, g, gD, gN)
+        gc, gq, gr = SP.flat_views(g, planes.K)
+        out.update(g_center=gc.cpu().numpy(), g_quat=gq.cpu().numpy(), g_radii=gr.cpu().numpy())
+    torch.cuda.synchronize()
+    H, W = cams.H, cams.W
+    out.update(
+        rect=r.rect.cpu().numpy().reshape(V, planes.K, 4),
+        key=r.key.cpu().numpy().reshape(V, planes.K),
+        tile_ptr=r.tile_ptr.cpu().numpy(),
+        tile_ent=r.tile_ent.cpu().numpy()[: int(r.tile_ptr[-1].item())],
+        required=int(r.required.item()),
+        status=int(r.status.item()),
+        depth=r.depth.cpu().numpy().reshape(V, H, W),
+        normal=r.normal.cpu().numpy().reshape(V, H, W, 3),
+        alpha=r.alpha.cpu().numpy().reshape(V, H, W),
+        delta=r.settings.delta,
+    )
+    return out
+
+
+def oracle_bins(planes, cams, delta, tile):
+    rect, key, key32 = O.bin_records(planes.center, planes.quat, planes.radii, cams.w2c, cams.intr,
+                                     cams.H, cams.W, tile[0], tile[1], delta, z_near=Z_NEAR32,
+                                     z_far=Z_FAR32)
+    ptr, ent = O.tile_lists(rect, key32, cams.H, cams.W, tile[0], tile[1])
+    return rect, key32, ptr, ent
+
+
+def oracle_render(planes, cams, lam, M=30, rows=None):
+    return O.render(planes.center, planes.quat, planes.radii, cams.w2c, cams.intr, cams.H, cams.W,
+                    f32(lam), M=M, z_near=Z_NEAR32, z_far=Z_FAR32, rows=rows)
+
+
+def compare_maps(g, o, rows=None, tol_d=1e-4, tol_n=1e-5):
+    """Max depth / normal error over well-conditioned pixels (oracle ill bit 0
+    clear) and the count of ill-conditioned pixels."""
+    sl = slice(None) if rows is None else slice(rows[0], rows[1])
+    well = (o["ill"][:, sl] & 1) == 0
+    dd = np.abs(g["depth"][:, sl].astype(np.float64) - o["depth"][:, sl])
+    dn = np.abs(g["normal"][:, sl].astype(np.float64) - o["normal"][:, sl]).max(axis=-1)
+    return dict(
+        n_pix=int(well.size), n_ill=int((~well).sum()),
+        max_dd_well=float(dd[well].max()) if well.any() else 0.0,
+        max_dn_well=float(dn[well].max()) if well.any() else 0.0,
+        max_dd_ill=float(dd[~well].max()) if (~well).any() else 0.0,
+        n_bad_d=int((dd[well] > tol_d).sum()), n_bad_n=int((dn[well] > tol_n).sum()),
+    )
+
+
+def grad_errors(g_gpu, g_or, rel=1e-3, floor=1e-6):
+    """Per-plane gradient check of one parameter group: ||g - g*|| <=
+    rel ||g*|| + floor max_planes ||g*||.  Returns (n_bad, worst ratio)."""
+    n_or = np.linalg.norm(g_or, axis=1)
+    err = np.linalg.norm(g_gpu.astype(np.float64) - g_or, axis=1)
+    bound = rel * n_or + floor * max(n_or.max(), 1e-30)
+    ratio = err / np.maximum(bound, 1e-300)
+    return int((err > bound).sum()), float(ratio.max())

@@ -1,0 +1,324 @@
+"""GPU parity of libps against the FP64 oracle (calls go through the C ABI).
+
+Bars (arxiv 2412.03451 fixes no precision; these are the build's targets):
+  * tile rectangles, depth keys and tile lists: bit-exact;
+  * depth within 1e-4 m and normal components within 1e-5 on well-conditioned
+    pixels (pixels whose result FP32 rounding of the margins cannot move by
+    more than half the tolerance, as flagged by the oracle);
+  * gradients per plane and group: ||g - g*|| <= 1e-3 ||g*|| + 1e-6 max ||g*||,
+    with the upstream gradient zeroed on pixels where a min/sign branch or the
+    filter is within FP32 noise of flipping (same input on both sides).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2412_03451_gb300 import scenes as S
+
+from gpu_cases import (compare_maps, f32, gpu_run, grad_errors, oracle_bins, oracle_render)
+
+pytestmark = pytest.mark.gpu
+
+REPORT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out",
+                      "parity_report.jsonl")
+
+
+def report(name, **kw):
+    try:
+        os.makedirs(os.path.dirname(REPORT), exist_ok=True)
+        with open(REPORT, "a") as f:
+            f.write(json.dumps(dict(test=name, **kw)) + "\n")
+    except OSError:
+        pass
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_03451_gb300 import binding
+    binding.load()
+
+
+def tiny_init(seed=1):
+    room = S.tiny_room(0)
+    return room, S.perturb_planes(room.gt, seed)
+
+
+# ---------------------------------------------------------------------------
+# Binning: bit-exact.
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+@pytest.mark.parametrize("lam", [20.0 / np.e, 20.0, 300.0])
+def test_bins_bit_exact_tiny_room(tile, lam):
+    room, init = tiny_init()
+    g = gpu_run(init, room.cams, lam, tile=tile)
+    rect, key32, ptr, ent = oracle_bins(init, room.cams, g["delta"], tile)
+    assert g["status"] == 0
+    assert np.array_equal(g["rect"], rect)
+    assert np.array_equal(g["key"].view(np.uint32), key32.view(np.uint32))
+    assert np.array_equal(g["tile_ptr"], ptr)
+    assert np.array_equal(g["tile_ent"], ent)
+    assert g["required"] == len(ent)
+    report("bins_tiny", tile=tile, lam=lam, entries=len(ent))
+
+
+def test_bins_bit_exact_ragged_and_clipped():
+    # image size not a multiple of the tile; planes crossing z = z_near and behind the camera
+    p = S.random_planes_in_view(21, 40, depth_range=(-0.5, 3.0), half=(0.1, 1.5))
+    cams = S.identity_cameras(3, 50, 70, 40.0, seed=2, jitter=0.2)
+    g = gpu_run(p, cams, 20.0, tile=(16, 16))
+    rect, key32, ptr, ent = oracle_bins(p, cams, g["delta"], (16, 16))
+    assert np.array_equal(g["rect"], rect)
+    assert np.array_equal(g["key"].view(np.uint32), key32.view(np.uint32))
+    assert np.array_equal(g["tile_ptr"], ptr) and np.array_equal(g["tile_ent"], ent)
+    culled = (rect[..., 2] < rect[..., 0]).sum()
+    report("bins_ragged", culled=int(culled), entries=len(ent))
+    assert culled > 0
+
+
+def test_capacity_overflow_reports_required():
+    room, init = tiny_init()
+    g = gpu_run(init, room.cams, 20.0, capacity=100)
+    rect, key32, ptr, ent = oracle_bins(init, room.cams, g["delta"], (16, 16))
+    assert g["status"] & (1 << 3)
+    assert g["required"] == len(ent)
+
+
+# ---------------------------------------------------------------------------
+# Forward.
+
+@pytest.mark.parametrize("lam", [20.0 / np.e, 20.0, 300.0])
+def test_forward_tiny_room(lam):
+    room, init = tiny_init()
+    g = gpu_run(init, room.cams, lam)
+    o = oracle_render(init, room.cams, lam)
+    c = compare_maps(g, o)
+    report("fwd_tiny", lam=lam, **c)
+    assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_ill"] < 0.5 * c["n_pix"]
+    well = (o["ill"] & 1) == 0
+    assert np.abs(g["alpha"][well] - o["alpha"][well]).max() < 1e-5
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (32, 8)])
+def test_forward_other_tiles(tile):
+    room, init = tiny_init(3)
+    g = gpu_run(init, room.cams, 20.0, tile=tile)
+    o = oracle_render(init, room.cams, 20.0)
+    c = compare_maps(g, o)
+    report("fwd_tiles", tile=tile, **c)
+    assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+
+
+def test_forward_dense_overlaps_top_m_and_restarts():
+    # many overlapping, partly transparent planes: exercises the pending-buffer
+    # overflow and restart path and the M cut
+    p = S.random_planes_in_view(7, 120, depth_range=(1.0, 3.0), half=(0.3, 1.2), fov=0.4)
+    cams = S.identity_cameras(2, 40, 56, 30.0, seed=3, jitter=0.05)
+    for M in (30, 4):
+        g = gpu_run(p, cams, 7.36, M=M)
+        o = oracle_render(p, cams, 7.36, M=M)
+        c = compare_maps(g, o)
+        report("fwd_dense", M=M, max_cand=int(o["n_cand"].max()), **c)
+        assert o["n_cand"].max() > 30
+        assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+
+
+def test_forward_stack_of_40_equal_weights():
+    # 40 fronto-parallel planes whose weight at one pixel is the same value < 1
+    lam, i0, j0 = 50.0, 100, 48
+    d = O.filter_margin(lam)
+    cs, qs, rs = [], [], []
+    for j in range(40):
+        Z = 1.0 + 0.05 * j
+        X0 = Z * (i0 + 0.5 - 64) / 100.0
+        cs.append([0, 0, Z]); qs.append([1, 0, 0, 0]); rs.append([X0 - 0.5 * d, 1.0, 0.5, 0.5])
+    p = S.Planes(np.asarray(cs, np.float32), np.asarray(qs, np.float32), np.asarray(rs, np.float32))
+    cams = S.identity_cameras(1, 96, 128, 100.0)
+    g = gpu_run(p, cams, lam)
+    o = oracle_render(p, cams, lam)
+    assert o["n_cand"][0, j0, i0] == 40 and o["n_sel"][0, j0, i0] == 30
+    assert abs(g["depth"][0, j0, i0] - o["depth"][0, j0, i0]) < 1e-4
+    assert abs(g["alpha"][0, j0, i0] - o["alpha"][0, j0, i0]) < 1e-5
+
+
+def test_hard_mode_matches_ray_caster():
+    room = S.tiny_room(0)
+    from paper_2412_03451_gb300 import binding as B
+    g = gpu_run(room.gt, room.cams, 300.0, flags=B.PS_HARD)
+    D, N, pid = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, room.cams.w2c,
+                          room.cams.intr, room.cams.H, room.cams.W, z_near=0.01)
+    close = np.abs(g["depth"] - D) < 1e-4
+    report("hard", frac_close=float(close.mean()))
+    assert close.mean() > 0.995
+
+
+def test_empty_scene_and_culled_planes():
+    p = S.Planes(np.array([[0, 0, -3.0]], np.float32), np.array([[1, 0, 0, 0]], np.float32),
+                 np.array([[0.5, 0.5, 0.5, 0.5]], np.float32))
+    cams = S.identity_cameras(1, 24, 40, 20.0)
+    g = gpu_run(p, cams, 20.0)
+    assert g["required"] == 0 and np.all(g["depth"] == 0) and np.all(g["alpha"] == 0)
+
+
+def test_nonfinite_parameters_flagged_and_culled():
+    room, init = tiny_init()
+    bad = init.copy()
+    bad.center[3, 0] = np.nan
+    bad.quat[5] = 0.0
+    g = gpu_run(bad, room.cams, 20.0)
+    assert g["status"] & (1 << 5)
+    assert np.all(g["rect"][:, 3, 2] < g["rect"][:, 3, 0])
+    assert np.all(g["rect"][:, 5, 2] < g["rect"][:, 5, 0])
+    assert np.isfinite(g["depth"]).all()
+
+
+# ---------------------------------------------------------------------------
+# Loss and Adam.
+
+def test_loss_parity():
+    import torch
+    from paper_2412_03451_gb300 import splat as SP
+    rng = np.random.default_rng(0)
+    V, H, W = 3, 20, 30
+    D = rng.uniform(1, 3, (V, H, W)).astype(np.float32)
+    N = rng.normal(size=(V, H, W, 3)).astype(np.float32)
+    Dg = rng.uniform(1, 3, (V, H, W)).astype(np.float32)
+    Dg[1, :5] = 0.0
+    Ng = rng.normal(size=(V, H, W, 3)).astype(np.float32)
+    tot, dD, dN, sums = O.loss(D, N, Dg, Ng)
+    r = SP.Renderer([H] * V, [W] * V, [0] * V, [0, 1])
+    r.set_cameras(np.tile(np.eye(3, 4, dtype=np.float32), (V, 1, 1)),
+                  np.tile(np.array([10, 10, 15, 10], np.float32), (V, 1)))
+    r.make_settings(20.0)
+    r.depth.copy_(torch.from_numpy(D.reshape(-1)))
+    r.normal.copy_(torch.from_numpy(N.reshape(-1, 3)))
+    r.loss(torch.from_numpy(Dg.reshape(-1)).cuda(), torch.from_numpy(Ng.reshape(-1, 3)).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(r.dLdD.cpu().numpy().reshape(V, H, W), dD.astype(np.float32))
+    assert np.abs(r.dLdN.cpu().numpy().reshape(V, H, W, 3) - dN).max() < 1e-5
+    assert np.allclose(r.view_sums.cpu().numpy(), sums, rtol=1e-5)
+
+
+def test_adam_parity():
+    import torch
+    from paper_2412_03451_gb300 import binding as B
+    rng = np.random.default_rng(1)
+    n = 1000
+    p0 = rng.normal(size=n).astype(np.float32)
+    p, m, v = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    pt = torch.from_numpy(p0.copy()).cuda()
+    mt, vt = torch.zeros_like(pt), torch.zeros_like(pt)
+    for step in range(1, 6):
+        g = rng.normal(size=n).astype(np.float32)
+        O.adam(p, g.astype(np.float64), m, v, step, clamp_min=0.0)
+        B.ps_adam_step(pt, torch.from_numpy(g).cuda(), mt, vt, 1e-3, 0.9, 0.999, 1e-8, step,
+                       clamp_min=0.0)
+    torch.cuda.synchronize()
+    assert np.abs(pt.cpu().numpy() - p).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Backward.
+
+def _upstream(o, gt_D, gt_N, mask_bits=2):
+    _, dD, dN, _ = O.loss(o["depth"], o["normal"], gt_D, gt_N)
+    ill = (o["ill"] & mask_bits) != 0
+    dD[ill] = 0.0
+    dN[ill] = 0.0
+    return dD.astype(np.float32), dN.astype(np.float32), float(ill.mean())
+
+
+@pytest.mark.parametrize("lam", [20.0 / np.e, 20.0, 100.0])
+def test_backward_tiny_room(lam):
+    room, init = tiny_init()
+    D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, room.cams.w2c, room.cams.intr,
+                        room.cams.H, room.cams.W)
+    o = oracle_render(init, room.cams, lam)
+    dD, dN, ill = _upstream(o, D, N)
+    g = gpu_run(init, room.cams, lam, dLdD=dD, dLdN=dN, backward=True)
+    gc, gq, gr = O.backward(init.center, init.quat, init.radii, room.cams.w2c, room.cams.intr,
+                            room.cams.H, room.cams.W, f32(lam), dD, dN, z_near=f32(0.01))
+    res = {k: grad_errors(g[k], ref) for k, ref in
+           (("g_center", gc), ("g_quat", gq), ("g_radii", gr))}
+    report("bwd_tiny", lam=lam, ill_frac=ill, **{k: v for k, v in res.items()})
+    for k, (nbad, worst) in res.items():
+        assert nbad == 0, (k, nbad, worst)
+
+
+def test_backward_dense_overlaps():
+    p = S.random_planes_in_view(9, 60, depth_range=(1.0, 3.0), half=(0.2, 0.8), fov=0.5)
+    cams = S.identity_cameras(2, 40, 56, 30.0, seed=5, jitter=0.05)
+    lam = 20.0
+    o = oracle_render(p, cams, lam)
+    rng = np.random.default_rng(3)
+    dD = rng.normal(size=o["depth"].shape)
+    dN = rng.normal(size=o["normal"].shape)
+    ill = (o["ill"] & 2) != 0
+    dD[ill] = 0
+    dN[ill] = 0
+    dD, dN = dD.astype(np.float32), dN.astype(np.float32)
+    g = gpu_run(p, cams, lam, dLdD=dD, dLdN=dN, backward=True)
+    gc, gq, gr = O.backward(p.center, p.quat, p.radii, cams.w2c, cams.intr, cams.H, cams.W,
+                            f32(lam), dD, dN, z_near=f32(0.01))
+    res = {k: grad_errors(g[k], ref) for k, ref in
+           (("g_center", gc), ("g_quat", gq), ("g_radii", gr))}
+    report("bwd_dense", ill_frac=float(ill.mean()), **res)
+    for k, (nbad, worst) in res.items():
+        assert nbad == 0, (k, nbad, worst)
+
+
+# ---------------------------------------------------------------------------
+# Paper-scale room (640x480, 3000 planes, 8 views): sampled rows.
+
+BIG_ROWS = (240, 242)
+
+
+@pytest.fixture(scope="module")
+def big_case():
+    room = S.large_room(1000, n_rect=2000, n_views=64)
+    cams = room.cams.subset(np.arange(0, 64, 8))
+    D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, cams.w2c, cams.intr,
+                        cams.H, cams.W, z_near=f32(0.01), rows=BIG_ROWS)
+    init = S.surface_init(room, 3000, seed=7)
+    return room, cams, D, N, init
+
+
+def test_paper_scale_forward_sampled_rows(big_case):
+    room, cams, D, N, init = big_case
+    lam = 20.0 / np.e
+    g = gpu_run(init, cams, lam)
+    rows = (200, 203)
+    o = oracle_render(init, cams, lam, rows=rows)
+    c = compare_maps(g, o, rows=rows)
+    report("fwd_big", **c)
+    assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    # bit-exact bins at full size
+    rect, key32, ptr, ent = oracle_bins(init, cams, g["delta"], (16, 16))
+    assert np.array_equal(g["rect"], rect)
+    assert np.array_equal(g["tile_ptr"], ptr) and np.array_equal(g["tile_ent"], ent)
+
+
+def test_paper_scale_backward_sampled_rows(big_case):
+    room, cams, D, N, init = big_case
+    lam = 20.0
+    rows = BIG_ROWS
+    o = oracle_render(init, cams, lam, rows=rows)
+    dD, dN, ill = _upstream(o, D, N)
+    keep = np.zeros_like(dD, dtype=bool)
+    keep[:, rows[0]:rows[1]] = True
+    dD[~keep] = 0
+    dN[~keep] = 0
+    g = gpu_run(init, cams, lam, dLdD=dD, dLdN=dN, backward=True)
+    gc, gq, gr = O.backward(init.center, init.quat, init.radii, cams.w2c, cams.intr, cams.H,
+                            cams.W, f32(lam), dD, dN, z_near=f32(0.01))
+    res = {k: grad_errors(g[k], ref) for k, ref in
+           (("g_center", gc), ("g_quat", gq), ("g_radii", gr))}
+    report("bwd_big", **res)
+    for k, (nbad, worst) in res.items():
+        assert nbad == 0, (k, nbad, worst)
