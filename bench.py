@@ -52,6 +52,10 @@ N_VIEWS, VIEWS_PER_STEP, N_GT, N_INIT = 64, 8, 2000, 3000
 #     + record accumulation 16                                         = 66
 FLOP_CAND, FLOP_COMP_FWD, FLOP_COMP_BWD = 27, 12, 66
 SM_COUNT, FP32_LANES = 152, 128
+# kernels of one step: project 1; bin 1 + 3 (record scan) + 1 + 3 (tile scan) + 1 + 1;
+# fused splat 1 + chain 1 (split: fwd 1, loss 1, bwd 1 + chain 1); Adam 2
+LAUNCHES_FUSED = 1 + 10 + 2 + 2
+LAUNCHES_SPLIT = 1 + 10 + 4 + 2
 
 # DRAM traffic per launch of ps_splat_bwd's main kernel, from the ncu capture
 # summarised in profiles/ (valid only for the kernel source it was taken on).
@@ -282,16 +286,21 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (ALU-bound: FP32 work of the formulas)
     tested, cand, comp = counts
-    fwd_ms = statistics.mean(stages["splat_fwd"])
-    bwd_ms = statistics.mean(stages["splat_bwd"])
     K = args.steps
-    flops_fwd = (cand * FLOP_CAND + comp * FLOP_COMP_FWD) / K
-    flops_bwd = (cand * FLOP_CAND + comp * FLOP_COMP_BWD) / K
     sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = SM_COUNT * FP32_LANES * 2 * sm_clock * 1e6 / 1e12
-    dom = "splat_bwd" if bwd_ms >= fwd_ms else "splat_fwd"
-    dom_ms = max(fwd_ms, bwd_ms)
-    achieved = (flops_bwd if dom == "splat_bwd" else flops_fwd) / (dom_ms / 1e3) / 1e12
+    if "splat_fused" in stages:
+        # one walk: candidates evaluated once, composited pairs forward + adjoint
+        dom, dom_ms = "splat_fused", statistics.mean(stages["splat_fused"])
+        flops = (cand * FLOP_CAND + comp * (FLOP_COMP_FWD + FLOP_COMP_BWD)) / K
+    else:
+        fwd_ms = statistics.mean(stages["splat_fwd"])
+        bwd_ms = statistics.mean(stages["splat_bwd"])
+        dom = "splat_bwd" if bwd_ms >= fwd_ms else "splat_fwd"
+        dom_ms = max(fwd_ms, bwd_ms)
+        flops = ((cand * FLOP_CAND + comp * FLOP_COMP_BWD) if dom == "splat_bwd"
+                 else (cand * FLOP_CAND + comp * FLOP_COMP_FWD)) / K
+    achieved = flops / (dom_ms / 1e3) / 1e12
     traffic = TRAFFIC.get(dom) if TRAFFIC.get("src_sha") == src_hash() else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -307,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
         "stage_ms": {k: round(statistics.mean(v), 4) for k, v in stages.items()},
         "wall_s_timed": round(wall, 4),
         "roofline": roofline, "clocks": clocks,
-        "gpu_launches": 11 * args.steps,
+        "gpu_launches": (LAUNCHES_FUSED if wl.fit.fused else LAUNCHES_SPLIT) * args.steps,
         "culling": {"tested_per_candidate": round(tested / max(cand, 1), 2)},
     }
 

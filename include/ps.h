@@ -160,6 +160,9 @@ ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* settings, const
                        long long* d_required, void* ws, size_t ws_bytes, int* d_status,
                        ps_stream stream);
 
+/* Bytes of scratch that ps_splat_fwd needs (its work counter). */
+size_t ps_fwd_workspace_bytes(const ps_frame* frame);
+
 /* Forward splatting (Sec. 3.2, Eq. 4, 6-9, 11-13).  For every pixel: intersect
    the ray with every plane of the pixel's tile list, weight it with
    w = min(1, 2 sigmoid(5 lambda min(m_X, m_Y))) (m = r - |P| on the side given
@@ -167,11 +170,12 @@ ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* settings, const
    the M nearest by (t, record id) and composite front to back:
    D = sum T_j w_j t_j, N = sum T_j w_j n_j, alpha = sum T_j w_j.
    depth [n_pixels], normal [n_pixels][3], alpha [n_pixels] (device, written;
-   alpha may be NULL). */
+   alpha may be NULL).  ws (device, 16-byte aligned, >= ps_fwd_workspace_bytes)
+   is scratch (a work counter reset by the call). */
 ps_status ps_splat_fwd(const ps_frame* frame, const ps_settings* settings, const float* rec,
                        const float* key, const int* tile_ptr, const int* tile_ent,
                        long long capacity, float* depth, float* normal, float* alpha,
-                       int* d_status, ps_stream stream);
+                       void* ws, size_t ws_bytes, int* d_status, ps_stream stream);
 
 /* Render loss (Eq. 14) and its gradient with respect to the rendered maps.
    Pixels with gt_depth <= 0 are not supervised (zero gradient).
@@ -183,7 +187,8 @@ ps_status ps_loss(const ps_frame* frame, const ps_settings* settings, const floa
                   const float* normal, const float* gt_depth, const float* gt_normal,
                   float* dL_dD, float* dL_dN, double* view_sums, ps_stream stream);
 
-/* Bytes of scratch that ps_splat_bwd needs (per-record gradient accumulators). */
+/* Bytes of scratch that ps_splat_bwd needs (per-record gradient accumulators
+   and a work counter). */
 size_t ps_bwd_workspace_bytes(const ps_frame* frame);
 
 /* Backward splatting: gradient of sum(dL_dD * D + dL_dN . N) with respect to
@@ -205,6 +210,25 @@ ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* frame,
                        const float* dL_dD, const float* dL_dN, float* g_center, float* g_quat,
                        float* g_radii, void* ws, size_t ws_bytes, int* d_status,
                        ps_stream stream);
+
+/* Forward splatting, render loss and backward splatting fused (Sec. 3.2,
+   Eq. 4, 6-14).  Because the loss of Eq. 14 is a sum of per-pixel terms, each
+   pixel's composited list, built once, serves both the forward and the
+   adjoint: the call renders D and N exactly as ps_splat_fwd, evaluates Eq. 14
+   against gt_depth / gt_normal (pixels with gt_depth <= 0 unsupervised) as
+   ps_loss, and accumulates the gradient of the loss into g_center, g_quat,
+   g_radii exactly as ps_splat_bwd would with the loss's dL/dD and dL/dN.
+   depth, normal, dL_dD, dL_dN (device, written) may each be NULL;
+   view_sums [V][4] f64 (device) is overwritten as in ps_loss; gradients are
+   accumulated (the caller zeroes them).  ws (device, 16-byte aligned,
+   >= ps_bwd_workspace_bytes) is scratch. */
+ps_status ps_splat_fused(const ps_planes* planes, const ps_frame* frame,
+                         const ps_settings* settings, const float* rec, const float* key,
+                         const int* tile_ptr, const int* tile_ent, long long capacity,
+                         const float* gt_depth, const float* gt_normal, float* depth,
+                         float* normal, float* dL_dD, float* dL_dN, double* view_sums,
+                         float* g_center, float* g_quat, float* g_radii, void* ws,
+                         size_t ws_bytes, int* d_status, ps_stream stream);
 
 /* Adam (Kingma & Ba; Sec. 3.3, lr = 1e-3 for every group, App. A.2),
    bias-corrected, on n floats in place: param, m, v (device, updated),

@@ -23,7 +23,8 @@ PS_HARD = 2
 PS_MAX_M = 64
 
 EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin_tiles",
-           "ps_splat_fwd", "ps_loss", "ps_bwd_workspace_bytes", "ps_splat_bwd", "ps_adam_step",
+           "ps_fwd_workspace_bytes", "ps_splat_fwd", "ps_loss", "ps_bwd_workspace_bytes", "ps_splat_bwd",
+           "ps_splat_fused", "ps_adam_step",
            "ps_count_pairs", "ps_status_string", "ps_version")
 
 
@@ -83,10 +84,12 @@ def load():
             "ps_project_cull": ([P, P, P, P, P, P, P, P], I),
             "ps_bin_workspace_bytes": ([P, LL], SZ),
             "ps_bin_tiles": ([P, P, P, P, P, P, LL, P, P, SZ, P, P], I),
-            "ps_splat_fwd": ([P, P, P, P, P, P, LL, P, P, P, P, P], I),
+            "ps_fwd_workspace_bytes": ([P], SZ),
+            "ps_splat_fwd": ([P, P, P, P, P, P, LL, P, P, P, P, SZ, P, P], I),
             "ps_loss": ([P, P, P, P, P, P, P, P, P, P], I),
             "ps_bwd_workspace_bytes": ([P], SZ),
             "ps_splat_bwd": ([P, P, P, P, P, P, P, LL, P, P, P, P, P, P, SZ, P, P], I),
+            "ps_splat_fused": ([P, P, P, P, P, P, P, LL, P, P, P, P, P, P, P, P, P, P, P, SZ, P, P], I),
             "ps_adam_step": ([P, P, P, P, LL, F, F, F, F, I, F, P], I),
             "ps_count_pairs": ([P, P, P, P, P, P, LL, P, P], I),
             "ps_status_string": ([I], ctypes.c_char_p),
@@ -188,11 +191,17 @@ def ps_bin_tiles(frame, settings, rect, key, tile_ptr, tile_ent, capacity, requi
                                _ptr(ws), nbytes, _ptr(status), _stream(stream)), "ps_bin_tiles")
 
 
+def ps_fwd_workspace_bytes(frame: PsFrame) -> int:
+    return int(load().ps_fwd_workspace_bytes(ctypes.byref(frame)))
+
+
 def ps_splat_fwd(frame, settings, rec, key, tile_ptr, tile_ent, capacity, depth, normal, alpha,
-                 status, stream=None):
+                 ws, status, stream=None):
+    nbytes = ws.numel() * ws.element_size()
     _check(load().ps_splat_fwd(ctypes.byref(frame), ctypes.byref(settings), _ptr(rec), _ptr(key),
                                _ptr(tile_ptr), _ptr(tile_ent), int(capacity), _ptr(depth),
-                               _ptr(normal), _ptr(alpha), _ptr(status), _stream(stream)),
+                               _ptr(normal), _ptr(alpha), _ptr(ws), nbytes, _ptr(status),
+                               _stream(stream)),
            "ps_splat_fwd")
 
 
@@ -214,6 +223,18 @@ def ps_splat_bwd(planes, frame, settings, rec, key, tile_ptr, tile_ent, capacity
                                _ptr(dLdD), _ptr(dLdN), _ptr(g_center), _ptr(g_quat),
                                _ptr(g_radii), _ptr(ws), nbytes, _ptr(status), _stream(stream)),
            "ps_splat_bwd")
+
+
+def ps_splat_fused(planes, frame, settings, rec, key, tile_ptr, tile_ent, capacity, gt_depth,
+                   gt_normal, depth, normal, dLdD, dLdN, view_sums, g_center, g_quat, g_radii, ws,
+                   status, stream=None):
+    nbytes = ws.numel() * ws.element_size()
+    _check(load().ps_splat_fused(ctypes.byref(planes), ctypes.byref(frame), ctypes.byref(settings),
+                                 _ptr(rec), _ptr(key), _ptr(tile_ptr), _ptr(tile_ent),
+                                 int(capacity), _ptr(gt_depth), _ptr(gt_normal), _ptr(depth),
+                                 _ptr(normal), _ptr(dLdD), _ptr(dLdN), _ptr(view_sums),
+                                 _ptr(g_center), _ptr(g_quat), _ptr(g_radii), _ptr(ws), nbytes,
+                                 _ptr(status), _stream(stream)), "ps_splat_fused")
 
 
 def ps_adam_step(param, grad, m, v, lr, b1, b2, eps, step, clamp_min=float("nan"), stream=None):

@@ -8,117 +8,69 @@
 // (key bits, record id), so the output does not depend on the order in which
 // the atomics below land.
 //
-//   1. count:   tile_cnt[t] += 1 for every tile of every record's rectangle
-//   2. scan:    tile_ptr = exclusive prefix sum of tile_cnt, total -> d_required
-//   3. scatter: record ids into their tiles' slots (unordered, via cursors)
-//   4. sort:    each tile's slots by (key, record id): shared-memory bitonic
-//               sort up to kSortCap entries, an O(n^2) rank sort beyond.
+//   1. record counts: tiles covered by each record's rectangle (+ the record's
+//      first global tile and rectangle width), then an exclusive scan over
+//      records numbers every (record, tile) pair;
+//   2. pair count: one thread per pair adds 1 to its tile's counter;
+//   3. tile scan: tile_ptr = exclusive prefix sum, total -> d_required;
+//   4. scatter: one thread per pair writes its record id into a slot of its
+//      tile (unordered, via per-tile cursors);
+//   5. sort: each tile's slots by (key, record id): shared-memory bitonic sort
+//      up to kSortCap entries, an O(n^2) rank sort beyond.
+// Every pair gets its own thread, so a plane covering a thousand tiles costs
+// no more latency than one covering a single tile.
 #include "ps_internal.cuh"
 
 using namespace ps;
 
 namespace {
 
-constexpr int kSortCap = 4096;    // entries sorted in shared memory (32 KB of u64)
+constexpr int kSortCap = 4096;     // entries sorted in shared memory (32 KB of u64)
 constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;      // elements per thread per scan tile
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kFlatBlocks = 152 * 8;
 
 struct BinWs {
+    int* rec_cnt;       // [R + 1] tiles per record -> exclusive prefix (pair numbering)
+    int4* rec_info;     // [R] first global tile, rectangle width in tiles, tiles_x, 0
     int* tile_cnt;      // [n_tiles]
     int* cursor;        // [n_tiles]
+    long long* part;    // [2 * max scan tiles] scan partial sums
     int* ent_tmp;       // [capacity] unordered entries
 };
 
-__host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-inline BinWs carve(void* ws, int n_tiles, long long capacity)
+inline int scan_tiles(long long n) { return (int)((n + kScanTile - 1) / kScanTile); }
+
+inline size_t ws_bytes(int R, int n_tiles, long long capacity)
+{
+    const int parts = 2 * (scan_tiles(R + 1) > scan_tiles(n_tiles) ? scan_tiles(R + 1) : scan_tiles(n_tiles)) + 2;
+    return align_up(sizeof(int) * (size_t)(R + 1)) + align_up(sizeof(int4) * (size_t)(R > 0 ? R : 1)) +
+           2 * align_up(sizeof(int) * (size_t)n_tiles) + align_up(sizeof(long long) * (size_t)parts) +
+           align_up(sizeof(int) * (size_t)(capacity > 0 ? capacity : 1));
+}
+
+inline BinWs carve(void* ws, int R, int n_tiles)
 {
     char* p = static_cast<char*>(ws);
     BinWs w;
+    w.rec_cnt = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * (size_t)(R + 1));
+    w.rec_info = reinterpret_cast<int4*>(p); p += align_up(sizeof(int4) * (size_t)(R > 0 ? R : 1));
     w.tile_cnt = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * (size_t)n_tiles);
     w.cursor = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * (size_t)n_tiles);
+    const int parts = 2 * (scan_tiles(R + 1) > scan_tiles(n_tiles) ? scan_tiles(R + 1) : scan_tiles(n_tiles)) + 2;
+    w.part = reinterpret_cast<long long*>(p); p += align_up(sizeof(long long) * (size_t)parts);
     w.ent_tmp = reinterpret_cast<int*>(p);
-    (void)capacity;
     return w;
 }
 
-inline size_t ws_bytes(int n_tiles, long long capacity)
-{
-    return 2 * align_up(sizeof(int) * (size_t)n_tiles) + align_up(sizeof(int) * (size_t)capacity);
-}
-
-// 1. count -------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_count(const int4* __restrict__ rect,
-                                                const ps_view* __restrict__ views,
-                                                int* __restrict__ tile_cnt)
-{
-    const int v = blockIdx.y;
-    const ps_view* vw = views + v;
-    const int K = __ldg(&vw->K);
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    const int4 rc = __ldg(&rect[(long long)__ldg(&vw->rec_off) + k]);
-    if (rc.z < rc.x || rc.w < rc.y) return;
-    const int tx = __ldg(&vw->tiles_x), off = __ldg(&vw->tile_off);
-    for (int y = rc.y; y <= rc.w; ++y)
-        for (int x = rc.x; x <= rc.z; ++x) atomicAdd(&tile_cnt[off + y * tx + x], 1);
-}
-
-// 2. scan (one CTA) -------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) k_scan(const int* __restrict__ tile_cnt, int n,
-                                                       int* __restrict__ tile_ptr,
-                                                       int* __restrict__ cursor,
-                                                       long long capacity,
-                                                       long long* __restrict__ d_required,
-                                                       int* status)
-{
-    __shared__ long long s_warp[kScanThreads / 32];
-    const int tid = threadIdx.x;
-    const int per = (n + kScanThreads - 1) / kScanThreads;
-    const int b = min(n, tid * per), e = min(n, b + per);
-    long long sum = 0;
-    for (int i = b; i < e; ++i) sum += tile_cnt[i];
-    // block exclusive scan of the per-thread sums
-    long long x = sum;
-    const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        long long w = (lane < kScanThreads / 32) ? s_warp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < kScanThreads / 32) s_warp[lane] = w;
-    }
-    __syncthreads();
-    long long excl = x - sum + (wid > 0 ? s_warp[wid - 1] : 0);
-    long long run = excl;
-    for (int i = b; i < e; ++i) {
-        const int c = tile_cnt[i];
-        const int vptr = (int)min(run, capacity);
-        tile_ptr[i] = vptr;
-        cursor[i] = vptr;
-        run += c;
-    }
-    if (tid == kScanThreads - 1) {
-        tile_ptr[n] = (int)min(run, capacity);
-        *d_required = run;
-        if (run > capacity) set_status(status, PS_ERR_CAPACITY);
-    }
-}
-
-// 3. scatter -------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_scatter(const int4* __restrict__ rect,
-                                                  const ps_view* __restrict__ views,
-                                                  const int* __restrict__ tile_ptr,
-                                                  int* __restrict__ cursor,
-                                                  int* __restrict__ ent_tmp)
+// 1. record counts ---------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_rec_count(const int4* __restrict__ rect,
+                                                    const ps_view* __restrict__ views,
+                                                    int* __restrict__ rec_cnt,
+                                                    int4* __restrict__ rec_info)
 {
     const int v = blockIdx.y;
     const ps_view* vw = views + v;
@@ -127,19 +79,187 @@ __global__ void __launch_bounds__(128) k_scatter(const int4* __restrict__ rect,
     if (k >= K) return;
     const int r = __ldg(&vw->rec_off) + k;
     const int4 rc = __ldg(&rect[r]);
-    if (rc.z < rc.x || rc.w < rc.y) return;
-    const int tx = __ldg(&vw->tiles_x), off = __ldg(&vw->tile_off);
-    for (int y = rc.y; y <= rc.w; ++y)
-        for (int x = rc.x; x <= rc.z; ++x) {
-            const int t = off + y * tx + x;
-            const int pos = atomicAdd(&cursor[t], 1);
-            // tile_ptr is clamped to capacity, so positions past it belong to
-            // lists that did not fit: drop them (status already set)
-            if (pos < __ldg(&tile_ptr[t + 1])) ent_tmp[pos] = r;
-        }
+    const int tx = __ldg(&vw->tiles_x);
+    int c = 0;
+    int4 info = make_int4(0, 1, tx, 0);
+    if (rc.z >= rc.x && rc.w >= rc.y) {
+        const int w = rc.z - rc.x + 1;
+        c = w * (rc.w - rc.y + 1);
+        info = make_int4(__ldg(&vw->tile_off) + rc.y * tx + rc.x, w, tx, 0);
+    }
+    rec_cnt[r] = c;
+    rec_info[r] = info;
 }
 
-// 4. sort ----------------------------------------------------------------------
+// Exclusive scan of int counts in three passes (tile sums, scan of the sums,
+// tile scan + offset).  The last pass can clamp the offsets to a capacity and
+// copy them to a cursor array (tile lists) and reports the total.
+__device__ __forceinline__ long long block_scan_excl(long long x, long long* s_warp, long long& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = (lane < (int)(blockDim.x >> 5)) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;   // inclusive warp totals
+    }
+    __syncthreads();
+    total = s_warp[(blockDim.x >> 5) - 1];
+    const long long r = incl - x + (wid > 0 ? s_warp[wid - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int* __restrict__ in, int n,
+                                                            long long* __restrict__ part)
+{
+    __shared__ long long s_warp[32];
+    const long long base = (long long)blockIdx.x * kScanTile;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const long long j = base + (long long)i * kScanThreads + threadIdx.x;
+        if (j < n) s += in[j];
+    }
+    long long total;
+    block_scan_excl(s, s_warp, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(long long* __restrict__ part, int nparts)
+{
+    // one block: exclusive scan of the tile sums in place (nparts <= 1024 * 8)
+    __shared__ long long s_warp[32];
+    __shared__ long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nparts; b0 += kScanThreads) {
+        const int j = b0 + threadIdx.x;
+        const long long x = j < nparts ? part[j] : 0;
+        long long total;
+        const long long e = block_scan_excl(x, s_warp, total);
+        if (j < nparts) part[j] = e + s_carry;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[nparts] = s_carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restrict__ in, int n,
+                                                             const long long* __restrict__ part,
+                                                             int nparts, int* __restrict__ out,
+                                                             int* __restrict__ cursor,
+                                                             long long capacity,
+                                                             long long* __restrict__ d_total,
+                                                             int* status)
+{
+    __shared__ long long s_warp[32];
+    __shared__ int s_in[kScanTile];
+    const long long base = (long long)blockIdx.x * kScanTile;
+    // coalesced load of the tile
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const long long j = base + (long long)i * kScanThreads + threadIdx.x;
+        s_in[i * kScanThreads + threadIdx.x] = j < n ? in[j] : 0;
+    }
+    __syncthreads();
+    // each thread scans kScanItems consecutive elements
+    long long loc[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        loc[i] = s;
+        s += s_in[threadIdx.x * kScanItems + i];
+    }
+    long long total;
+    const long long e = block_scan_excl(s, s_warp, total) + part[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const long long j = base + (long long)threadIdx.x * kScanItems + i;
+        if (j < n) {
+            long long v = e + loc[i];
+            if (v > capacity) v = capacity;
+            out[j] = (int)v;
+            if (cursor) cursor[j] = (int)v;
+        }
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        const long long tot = part[nparts];
+        out[n] = (int)(tot < capacity ? tot : capacity);
+        if (d_total) *d_total = tot;
+        if (status && tot > capacity) set_status(status, PS_ERR_CAPACITY);
+    }
+}
+
+cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long long capacity,
+                           long long* part, long long* d_total, int* status, cudaStream_t st)
+{
+    const int nparts = scan_tiles(n > 0 ? n : 1);
+    k_scan_sums<<<nparts, kScanThreads, 0, st>>>(in, n, part);
+    k_scan_parts<<<1, kScanThreads, 0, st>>>(part, nparts);
+    k_scan_apply<<<nparts, kScanThreads, 0, st>>>(in, n, part, nparts, out, cursor, capacity,
+                                                  d_total, status);
+    return cudaGetLastError();
+}
+
+// 2./4. one thread per (record, tile) pair ----------------------------------------
+__device__ __forceinline__ int pair_record(const int* __restrict__ off, int R, int i)
+{
+    // last r with off[r] <= i (off is non-decreasing, off[0] = 0)
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&off[mid]) <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_pair_count(const int* __restrict__ rec_off, int R,
+                                                     const int4* __restrict__ rec_info,
+                                                     int* __restrict__ tile_cnt)
+{
+    const int E = __ldg(&rec_off[R]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E; i += gridDim.x * blockDim.x) {
+        const int r = pair_record(rec_off, R, i);
+        const int4 info = __ldg(&rec_info[r]);
+        const int j = i - __ldg(&rec_off[r]);
+        const int t = info.x + (j / info.y) * info.z + (j % info.y);
+        atomicAdd(&tile_cnt[t], 1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pair_scatter(const int* __restrict__ rec_off, int R,
+                                                       const int4* __restrict__ rec_info,
+                                                       const int* __restrict__ tile_ptr,
+                                                       int* __restrict__ cursor,
+                                                       int* __restrict__ ent_tmp)
+{
+    const int E = __ldg(&rec_off[R]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E; i += gridDim.x * blockDim.x) {
+        const int r = pair_record(rec_off, R, i);
+        const int4 info = __ldg(&rec_info[r]);
+        const int j = i - __ldg(&rec_off[r]);
+        const int t = info.x + (j / info.y) * info.z + (j % info.y);
+        const int pos = atomicAdd(&cursor[t], 1);
+        // tile_ptr is clamped to the capacity: positions past it belong to lists
+        // that did not fit and are dropped (the status word says so)
+        if (pos < __ldg(&tile_ptr[t + 1])) ent_tmp[pos] = r;
+    }
+}
+
+// 5. sort ----------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long sort_key(const float* __restrict__ key, int r)
 {
     return ((unsigned long long)__float_as_uint(__ldg(&key[r])) << 32) | (unsigned)r;
@@ -182,7 +302,7 @@ __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr,
         for (int i = tid; i < n; i += NT) tile_ent[b + i] = (int)(unsigned)(s[i] & 0xffffffffu);
         return;
     }
-    // long list: rank of each element = number of smaller keys (keys unique)
+    // long list: rank of each element = number of smaller keys (keys are unique)
     for (int i0 = 0; i0 < n; i0 += NT) {
         const int i = i0 + tid;
         const unsigned long long ki = i < n ? sort_key(key, ent_tmp[b + i]) : 0ull;
@@ -203,8 +323,8 @@ __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr,
 
 extern "C" size_t ps_bin_workspace_bytes(const ps_frame* frame, long long capacity)
 {
-    if (!frame || frame->n_tiles < 0 || capacity < 0) return 0;
-    return ws_bytes(frame->n_tiles, capacity);
+    if (!frame || frame->n_tiles < 0 || frame->n_records < 0 || capacity < 0) return 0;
+    return ws_bytes(frame->n_records, frame->n_tiles, capacity);
 }
 
 extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, const int* rect,
@@ -216,25 +336,32 @@ extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, c
         return PS_ERR_ARG;
     if (capacity < 0 || capacity >= (1LL << 31) - 1) return PS_ERR_ARG;
     if (capacity > 0 && !tile_ent) return PS_ERR_ARG;
-    if (frame->n_tiles <= 0) return PS_ERR_ARG;
-    if (ws_bytes_ < ws_bytes(frame->n_tiles, capacity)) return PS_ERR_ARG;
+    if (frame->n_tiles <= 0 || frame->n_records < 0) return PS_ERR_ARG;
+    const int R = frame->n_records;
+    if (ws_bytes_ < ws_bytes(R, frame->n_tiles, capacity)) return PS_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(ws) & 255) return PS_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(rect) & 15) return PS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    BinWs w = carve(ws, frame->n_tiles, capacity);
+    BinWs w = carve(ws, R, frame->n_tiles);
     PS_CUDA_CHECK(cudaMemsetAsync(w.tile_cnt, 0, sizeof(int) * (size_t)frame->n_tiles, st));
     const int4* rc = reinterpret_cast<const int4*>(rect);
-    if (frame->max_K > 0) {
+    if (R > 0) {
         dim3 grid((frame->max_K + 127) / 128, frame->n_views);
-        k_count<<<grid, 128, 0, st>>>(rc, frame->views, w.tile_cnt);
+        k_rec_count<<<grid, 128, 0, st>>>(rc, frame->views, w.rec_cnt, w.rec_info);
+        PS_LAUNCH_CHECK();
+        // pair numbering; the total (<= n_tiles * R) is bounded by the int range check below
+        if (scan_exclusive(w.rec_cnt, R, w.rec_cnt, nullptr, (1LL << 31) - 1, w.part, nullptr,
+                           nullptr, st) != cudaSuccess)
+            return PS_ERR_CUDA;
+        k_pair_count<<<kFlatBlocks, 256, 0, st>>>(w.rec_cnt, R, w.rec_info, w.tile_cnt);
         PS_LAUNCH_CHECK();
     }
-    k_scan<<<1, kScanThreads, 0, st>>>(w.tile_cnt, frame->n_tiles, tile_ptr, w.cursor, capacity,
-                                        d_required, d_status);
-    PS_LAUNCH_CHECK();
-    if (frame->max_K > 0 && capacity > 0) {
-        dim3 grid((frame->max_K + 127) / 128, frame->n_views);
-        k_scatter<<<grid, 128, 0, st>>>(rc, frame->views, tile_ptr, w.cursor, w.ent_tmp);
+    if (scan_exclusive(w.tile_cnt, frame->n_tiles, tile_ptr, w.cursor, capacity, w.part,
+                       d_required, d_status, st) != cudaSuccess)
+        return PS_ERR_CUDA;
+    if (R > 0 && capacity > 0) {
+        k_pair_scatter<<<kFlatBlocks, 256, 0, st>>>(w.rec_cnt, R, w.rec_info, tile_ptr, w.cursor,
+                                                    w.ent_tmp);
         PS_LAUNCH_CHECK();
         k_sort<<<frame->n_tiles, 256, 0, st>>>(tile_ptr, w.ent_tmp, key, tile_ent);
         PS_LAUNCH_CHECK();

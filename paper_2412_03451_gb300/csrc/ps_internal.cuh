@@ -105,6 +105,49 @@ __device__ __forceinline__ bool eval_pair(const float4& n, const float4& vx, con
     return true;
 }
 
+// Rays through the pixel centres at the corners of a warp's pixel rectangle.
+struct WarpRegion {
+    float dxa, dxb, dya, dyb;
+};
+
+// Conservative test whether a plane can pass the filter at any pixel of a
+// warp's rectangle.  For a fixed plane, t = s / (d . n_c) and P = t (d . v_c) - a
+// are linear-fractional in the ray d = (dx, dy, 1); if d . n_c keeps its sign
+// over the rectangle they are monotone along every line, so their ranges over
+// the rectangle are spanned by the four corner rays.  The corner values use
+// the per-pixel formulas of eval_pair; the margins cover FP32 rounding.
+__device__ __forceinline__ bool region_may_hit(const float4& n, const float4& vx, const float4& vy,
+                                               const float4& r, const WarpRegion& g,
+                                               const SplatConst& c)
+{
+    float tmin = INFINITY, tmax = -INFINITY, xmin = INFINITY, xmax = -INFINITY;
+    float ymin = INFINITY, ymax = -INFINITY;
+    int npos = 0, nneg = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float dx = (k & 1) ? g.dxb : g.dxa;
+        const float dy = (k & 2) ? g.dyb : g.dya;
+        const float den = fmaf(dx, n.x, fmaf(dy, n.y, n.z));
+        npos += den > 2e-6f;
+        nneg += den < -2e-6f;
+        const float t = __fdividef(n.w, den);
+        const float dvx = fmaf(dx, vx.x, fmaf(dy, vx.y, vx.z));
+        const float dvy = fmaf(dx, vy.x, fmaf(dy, vy.y, vy.z));
+        const float X = fmaf(t, dvx, -vx.w);
+        const float Y = fmaf(t, dvy, -vy.w);
+        tmin = fminf(tmin, t); tmax = fmaxf(tmax, t);
+        xmin = fminf(xmin, X); xmax = fmaxf(xmax, X);
+        ymin = fminf(ymin, Y); ymax = fmaxf(ymax, Y);
+    }
+    if (npos != 4 && nneg != 4) return true;       // d . n_c may vanish: no bound
+    if (tmax < c.z_near * 0.99999f || tmin > c.z_far * 1.00001f) return false;
+    const float mx = c.reject + 1e-5f * (fabsf(xmin) + fabsf(xmax) + fabsf(tmax)) + 1e-6f;
+    const float my = c.reject + 1e-5f * (fabsf(ymin) + fabsf(ymax) + fabsf(tmax)) + 1e-6f;
+    if (xmax < -(r.y + mx) || xmin > r.x + mx) return false;
+    if (ymax < -(r.w + my) || ymin > r.z + my) return false;
+    return true;
+}
+
 // (t, id) lexicographic order of candidates.
 __device__ __forceinline__ bool cand_less(float ta, int ia, float tb, int ib)
 {

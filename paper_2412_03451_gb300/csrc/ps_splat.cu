@@ -1,19 +1,26 @@
 // ps_splat.cu -- forward and backward splatting, render loss.
 //
-// Forward (Sec. 3.2, Eq. 4, 6-9, 11-13).  One CTA renders one tile of
-// tile_w x tile_h pixels, one thread per pixel.  The tile's record list
-// (sorted by depth key, ps_bin.cu) is staged through shared memory in batches;
-// every thread intersects its ray with each staged plane and keeps the pairs
-// that survive the w >= w_min filter.  The M nearest pairs by (t, record id)
-// are composited front to back in exact order with a small sorted register
-// buffer: a pending pair is composited as soon as its depth is below the key
-// of the next list entry (keys bound every later depth from below).  If the
-// buffer overflows, the largest pair is dropped and remembered; compositing
-// stops at the smallest dropped pair and the pixel walks the list again from
-// the last composited pair (each such pass composites at least one pair, so
-// there are at most M + 1 passes).  A pixel stops when T reaches 0 (a plane
-// with w = 1 in front, exact in FP32) or M pairs are composited; a CTA stops
-// when all its pixels have.
+// Forward (Sec. 3.2, Eq. 4, 6-9, 11-13).  Work is split into strips of 32
+// pixels (a warp) of a tile; persistent warps take strips from a device
+// counter, so heavy and light strips balance across the GPU and no warp ever
+// waits for another.  A warp walks its tile's record list (sorted by depth key,
+// ps_bin.cu) 32 entries at a time: each lane loads one entry and tests it
+// against the warp's pixel rectangle (region_may_hit); a ballot leaves the
+// entries that can matter, which are staged in the warp's slice of shared
+// memory and evaluated by every lane for its own pixel in list order.
+//
+// Each pixel keeps the pairs that pass the w >= w_min filter and composites the
+// M nearest by (t, record id) front to back in exact order, with a small sorted
+// register buffer of pending pairs:
+//   * a pending pair is composited once its depth is below the key of the next
+//     list entry (keys bound every later depth from below);
+//   * the nearest opaque (w = 1) pair, or the M-th pair, is a cut: pairs
+//     behind it can never be composited (T = 0 behind an opaque pair) and are
+//     dropped at once, and once the list keys pass the cut the pixel is done;
+//   * if the buffer overflows, the largest pair is dropped and remembered;
+//     compositing stops at the smallest dropped pair and the warp walks the
+//     list again from the last composited pair (each pass composites at least
+//     one pair, so there are at most M + 1 passes).
 //
 // Backward.  The same walk (bit-identical arithmetic) rebuilds each pixel's
 // composited list and pushes (record, T_j) on a per-pixel stack in shared
@@ -31,8 +38,16 @@ using namespace ps;
 
 namespace {
 
-constexpr int kPend = 8;                  // pending-pair buffer per pixel
+#ifndef PS_KPEND
+#define PS_KPEND 4
+#endif
+constexpr int kPend = PS_KPEND;           // pending-pair buffer per pixel
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 4;                 // warps per CTA of the splat kernels
+
+// Kernel modes: forward only; backward from given dL/dD, dL/dN; or forward,
+// Eq. 14 loss and backward fused in one walk per pixel.
+constexpr int kFwd = 0, kBwd = 1, kFused = 2;
 
 struct SplatArgs {
     const ps_view* views;
@@ -44,6 +59,8 @@ struct SplatArgs {
     long long capacity;
     SplatConst c;
     int M;
+    int n_items;              // strips = n_tiles * (tile pixels / 32)
+    int* counter;             // work counter (zeroed before the launch)
     // forward outputs
     float* depth;
     float* normal;
@@ -53,17 +70,23 @@ struct SplatArgs {
     const float* dLdN;
     float4* g_rec;            // [R][4]
     int* status;
+    // fused mode: supervision and loss outputs
+    const float* gt_depth;
+    const float* gt_normal;
+    float* out_dLdD;          // optional
+    float* out_dLdN;          // optional
+    double* view_sums;        // [V][4]
+    float a_cos, a_l1n, a_depth;
 };
 
-template <int NT>
-struct Smem {
-    static constexpr int kBatch = NT < 128 ? NT : 128;
-    float4 rec[kBatch][4];
-    int id[kBatch];
-    float key[kBatch + 1];
-    int view, beg, end;
-    int any;
+// A warp's staging area: one list chunk.
+struct WarpStage {
+    float4 rec[32][4];
+    int id[32];
+    float key[33];            // key[32] = key of the next chunk's first entry
 };
+
+__device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
 
 // Per-pixel walk state.
 struct Walk {
@@ -79,6 +102,9 @@ struct Walk {
     bool ovf;
     float ot;
     int oid;
+    bool has_cut;     // nearest opaque (w = 1) candidate, or the M-th candidate
+    float ct;
+    int cid;
 };
 
 __device__ __forceinline__ void drop_note(Walk& s, float t, int id)
@@ -87,26 +113,52 @@ __device__ __forceinline__ void drop_note(Walk& s, float t, int id)
     s.ovf = true;
 }
 
-__device__ __forceinline__ void pend_insert(Walk& s, float t, float w, int id)
+__device__ __forceinline__ void set_cut(Walk& s, float t, int id)
 {
+    if (!s.has_cut || cand_less(t, id, s.ct, s.cid)) { s.ct = t; s.cid = id; s.has_cut = true; }
+    // pairs dropped from a full buffer that lie strictly behind the cut can never count
+    if (s.ovf && cand_less(s.ct, s.cid, s.ot, s.oid)) s.ovf = false;
+}
+
+// Adds a candidate.  Candidates behind the cut are dropped: nothing behind an
+// opaque pair (T = 0 after it) or behind the M-th pair can be composited.  An
+// opaque candidate becomes the cut and truncates the pending pairs behind it;
+// when composited + pending exceeds M the largest pending pair is beyond the
+// top M and goes, and the new M-th pair becomes the cut.
+__device__ __forceinline__ void pend_insert(Walk& s, float t, float w, int id, int M)
+{
+    if (s.has_cut && cand_less(s.ct, s.cid, t, id)) return;     // strictly behind the cut
     if (s.nb == kPend) {
         if (!cand_less(t, id, s.bt[kPend - 1], s.bid[kPend - 1])) { drop_note(s, t, id); return; }
         drop_note(s, s.bt[kPend - 1], s.bid[kPend - 1]);
         s.nb = kPend - 1;
     }
-    bool placed = false;
+    int pos = 0;
 #pragma unroll
     for (int i = kPend - 1; i >= 1; --i) {
         if (i <= s.nb) {
             if (cand_less(t, id, s.bt[i - 1], s.bid[i - 1])) {
                 s.bt[i] = s.bt[i - 1]; s.bw[i] = s.bw[i - 1]; s.bid[i] = s.bid[i - 1];
-            } else if (!placed) {
-                s.bt[i] = t; s.bw[i] = w; s.bid[i] = id; placed = true;
+            } else if (pos == 0) {
+                s.bt[i] = t; s.bw[i] = w; s.bid[i] = id; pos = i;
             }
         }
     }
-    if (!placed) { s.bt[0] = t; s.bw[0] = w; s.bid[0] = id; }
+    if (pos == 0) { s.bt[0] = t; s.bw[0] = w; s.bid[0] = id; }
     ++s.nb;
+    if (w == 1.f) {
+        set_cut(s, t, id);
+        s.nb = pos + 1;          // pending pairs behind an opaque one can never count
+    }
+    if (s.cnt + s.nb > M) {      // the largest pending pair is beyond the top M
+        s.nb = M - s.cnt;
+        float lt = s.bt[0];
+        int lid = s.bid[0];
+#pragma unroll
+        for (int i = 1; i < kPend; ++i)
+            if (i < s.nb) { lt = s.bt[i]; lid = s.bid[i]; }
+        set_cut(s, lt, lid);
+    }
 }
 
 __device__ __forceinline__ void pend_pop(Walk& s)
@@ -123,21 +175,18 @@ struct Accum {
     float D, N0, N1, N2, A;
 };
 
-template <bool BWD>
 struct Sink {
-    // forward: composite into Accum; backward: push (record, T) on the stack
+    // forward: composite into Accum; backward: push (record, T) on the stack; fused: both
     Accum acc;
-    int2* stk;        // [M][NT] (backward)
-    int stride;       // NT
+    int2* stk;        // this lane's column of the warp's stack [M][32]
 };
 
-template <bool BWD>
-__device__ __forceinline__ void composite(Walk& s, Sink<BWD>& k, const float4* __restrict__ rec,
+template <int MODE>
+__device__ __forceinline__ void composite(Walk& s, Sink& k, const float4* __restrict__ rec,
                                           float t, float w, int id, int M)
 {
-    if constexpr (BWD) {
-        k.stk[s.cnt * k.stride] = make_int2(id, __float_as_int(s.T));
-    } else {
+    if constexpr (MODE != kFwd) k.stk[s.cnt * 32] = make_int2(id, __float_as_int(s.T));
+    if constexpr (MODE != kBwd) {
         const float4 n = __ldg(&rec[(size_t)id * 4]);
         const float tw = s.T * w;
         k.acc.D = fmaf(tw, t, k.acc.D);
@@ -154,113 +203,129 @@ __device__ __forceinline__ void composite(Walk& s, Sink<BWD>& k, const float4* _
     if (s.cnt >= M || s.T == 0.f) s.done = true;
 }
 
-template <bool BWD>
-__device__ __forceinline__ void flush(Walk& s, Sink<BWD>& k, const float4* __restrict__ rec,
+template <int MODE>
+__device__ __forceinline__ void flush(Walk& s, Sink& k, const float4* __restrict__ rec,
                                       float bound, int M)
 {
+    // every later candidate lies behind the cut: nothing else can enter
+    const bool final_ = s.has_cut && bound > s.ct;
+    if (final_) bound = INFINITY;
     while (s.nb > 0 && !s.done) {
         if (!(s.bt[0] < bound)) break;
         if (s.ovf && !cand_less(s.bt[0], s.bid[0], s.ot, s.oid)) break;
         const float t = s.bt[0], w = s.bw[0];
         const int id = s.bid[0];
         pend_pop(s);
-        composite<BWD>(s, k, rec, t, w, id, M);
+        composite<MODE>(s, k, rec, t, w, id, M);
     }
+    if (final_ && s.nb == 0 && !s.ovf) s.done = true;
 }
 
-// Walks the tile list for one pixel (all threads of the CTA call it together).
-template <int NT, bool BWD>
-__device__ __forceinline__ void walk_tile(const SplatArgs& a, Smem<NT>& sm, Walk& s, Sink<BWD>& k,
-                                          float dx, float dy)
+// Walks one tile list for the warp's 32 pixels.
+template <int MODE>
+__device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Walk& s,
+                                           Sink& k, float dx, float dy, const WarpRegion& g,
+                                           int beg, int end)
 {
-    constexpr int B = Smem<NT>::kBatch;
-    const int tid = threadIdx.x;
-    const int beg = sm.beg, end = sm.end;
+    const int lane = threadIdx.x & 31;
     const float kMargin = 1.f - 1.f / 4096.f;
     for (int pass = 0; pass <= a.M + 1; ++pass) {
-        for (int base = beg; base < end; base += B) {
-            __syncthreads();
-            if (tid < B) {
-                const int i = base + tid;
-                if (i < end) {
-                    const int id = __ldg(&a.tile_ent[i]);
-                    sm.id[tid] = id;
-                    sm.key[tid] = __ldg(&a.key[id]);
-                    const float4* r = a.rec + (size_t)id * 4;
-                    sm.rec[tid][0] = __ldg(r + 0);
-                    sm.rec[tid][1] = __ldg(r + 1);
-                    sm.rec[tid][2] = __ldg(r + 2);
-                    sm.rec[tid][3] = __ldg(r + 3);
+        for (int base = beg; base < end; base += 32) {
+            if (__all_sync(kFull, s.done)) break;
+            // stage: lane l loads entry base + l and tests it against the warp's pixels
+            const int i = base + lane;
+            bool ok = false;
+            if (i < end) {
+                const int id = __ldg(&a.tile_ent[i]);
+                const float4* r = a.rec + (size_t)id * 4;
+                const float4 n = __ldg(r + 0), vx = __ldg(r + 1), vy = __ldg(r + 2), rr = __ldg(r + 3);
+                ok = region_may_hit(n, vx, vy, rr, g, a.c);
+                ws.key[lane] = __ldg(&a.key[id]);
+                if (ok) {
+                    ws.id[lane] = id;
+                    ws.rec[lane][0] = n; ws.rec[lane][1] = vx; ws.rec[lane][2] = vy; ws.rec[lane][3] = rr;
                 }
+            } else {
+                ws.key[lane] = INFINITY;
             }
-            if (tid == 0)
-                sm.key[B] = (base + B < end) ? __ldg(&a.key[__ldg(&a.tile_ent[base + B])]) : INFINITY;
-            __syncthreads();
-            const int nbat = min(B, end - base);
-            if (!s.done) {
-                for (int e = 0; e < nbat; ++e) {
+            if (lane == 0)
+                ws.key[32] = (base + 32 < end) ? __ldg(&a.key[__ldg(&a.tile_ent[base + 32])]) : INFINITY;
+            unsigned m = __ballot_sync(kFull, ok);
+            __syncwarp();
+            while (m) {
+                const int e = __ffs(m) - 1;
+                m &= m - 1;
+                if (!s.done) {
                     PairEval pe;
-                    const int id = sm.id[e];
-                    if (eval_pair(sm.rec[e][0], sm.rec[e][1], sm.rec[e][2], sm.rec[e][3], dx, dy,
+                    const int id = ws.id[e];
+                    if (eval_pair(ws.rec[e][0], ws.rec[e][1], ws.rec[e][2], ws.rec[e][3], dx, dy,
                                   a.c, pe)) {
                         if (!s.have_floor || cand_less(s.ft, s.fid, pe.t, id))
-                            pend_insert(s, pe.t, pe.w, id);
+                            pend_insert(s, pe.t, pe.w, id, a.M);
                     }
-                    const float nk = (e + 1 < nbat) ? sm.key[e + 1] : sm.key[B];
-                    if (s.nb > 0) flush<BWD>(s, k, a.rec, nk * kMargin, a.M);
-                    if (s.done) break;
+                    // keys are sorted: the next entry's key bounds every later depth
+                    if (s.nb > 0 || s.has_cut) flush<MODE>(s, k, a.rec, ws.key[e + 1] * kMargin, a.M);
                 }
             }
-            if (__syncthreads_and(s.done)) break;
+            // entries without a relevant successor in this chunk: bound by the next chunk
+            if (!s.done && (s.nb > 0 || s.has_cut)) flush<MODE>(s, k, a.rec, ws.key[32] * kMargin, a.M);
+            __syncwarp();
         }
         // end of list: everything pending below the smallest dropped pair is final
-        flush<BWD>(s, k, a.rec, INFINITY, a.M);
+        flush<MODE>(s, k, a.rec, INFINITY, a.M);
         const bool again = !s.done && s.ovf;
         if (!again) s.done = true;
-        if (!__syncthreads_or(again)) break;
+        if (!__any_sync(kFull, again)) break;
         if (again) { s.ovf = false; s.nb = 0; }
     }
 }
 
-template <int TW, int TH, bool BWD>
-__global__ void __launch_bounds__(TW * TH) k_splat(SplatArgs a)
+// One strip: pixel setup, walk, then the forward output or the backward adjoint.
+template <int TW, int TH, int MODE>
+__device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int2* stk_warp, int item)
 {
-    constexpr int NT = TW * TH;
-    __shared__ Smem<NT> sm;
-    extern __shared__ int2 dyn_stk[];   // backward: [M][NT]
-    const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
-    if (tid == 0) {
-        const int v = view_of_tile(a.views, a.n_views, tile);
-        sm.view = v;
-        const long long b = __ldg(&a.tile_ptr[tile]), e = __ldg(&a.tile_ptr[tile + 1]);
-        sm.beg = (int)min(b, a.capacity);
-        sm.end = (int)min(e, a.capacity);
-    }
-    __syncthreads();
-    const ps_view* vw = a.views + sm.view;
+    constexpr int NS = TW * TH / 32;       // strips per tile
+    const int lane = threadIdx.x & 31;
+    const int tile = item / NS;
+    const int strip = item - tile * NS;
+    const int v = view_of_tile(a.views, a.n_views, tile);
+    const ps_view* vw = a.views + v;
     const int W = __ldg(&vw->W), H = __ldg(&vw->H);
     const int tx_n = __ldg(&vw->tiles_x);
     const int lt = tile - __ldg(&vw->tile_off);
-    const int px = (lt % tx_n) * TW + tid % TW;
-    const int py = (lt / tx_n) * TH + tid / TW;
+    const int tx0 = (lt % tx_n) * TW, ty0 = (lt / tx_n) * TH;
+    const int q = strip * 32 + lane;        // pixel index within the tile, row-major
+    const int px = tx0 + q % TW, py = ty0 + q / TW;
     const bool inside = px < W && py < H;
     const float fx = __ldg(&vw->fx), fy = __ldg(&vw->fy);
     const float cx = __ldg(&vw->cx), cy = __ldg(&vw->cy);
     const float dx = __fdiv_rn((float)px + 0.5f - cx, fx);
     const float dy = __fdiv_rn((float)py + 0.5f - cy, fy);
     const long long pix = __ldg(&vw->pix_off) + (long long)py * W + px;
+    WarpRegion g;
+    {
+        constexpr int WX = TW < 32 ? TW : 32;
+        constexpr int WY = TW < 32 ? 32 / TW : 1;
+        const int q0 = strip * 32;
+        const int gx0 = tx0 + q0 % TW, gy0 = ty0 + q0 / TW;
+        g.dxa = __fdiv_rn((float)gx0 + 0.5f - cx, fx);
+        g.dxb = __fdiv_rn((float)(gx0 + WX - 1) + 0.5f - cx, fx);
+        g.dya = __fdiv_rn((float)gy0 + 0.5f - cy, fy);
+        g.dyb = __fdiv_rn((float)(gy0 + WY - 1) + 0.5f - cy, fy);
+    }
+    const int beg = (int)min((long long)__ldg(&a.tile_ptr[tile]), a.capacity);
+    const int end = (int)min((long long)__ldg(&a.tile_ptr[tile + 1]), a.capacity);
 
     Walk s;
     s.T = 1.f; s.cnt = 0; s.nb = 0; s.have_floor = false; s.ft = 0.f; s.fid = 0;
     s.ovf = false; s.ot = 0.f; s.oid = 0;
+    s.has_cut = false; s.ct = 0.f; s.cid = 0;
     s.done = !inside;
-    Sink<BWD> k;
+    Sink k;
     k.acc = Accum{0.f, 0.f, 0.f, 0.f, 0.f};
-    k.stk = dyn_stk + tid;
-    k.stride = NT;
+    k.stk = stk_warp + lane;
     float gD = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
-    if constexpr (BWD) {
+    if constexpr (MODE == kBwd) {
         if (inside) {
             gD = __ldg(&a.dLdD[pix]);
             gN0 = __ldg(&a.dLdN[3 * pix + 0]);
@@ -269,37 +334,99 @@ __global__ void __launch_bounds__(TW * TH) k_splat(SplatArgs a)
             if (gD == 0.f && gN0 == 0.f && gN1 == 0.f && gN2 == 0.f) s.done = true;
         }
     }
-    walk_tile<NT, BWD>(a, sm, s, k, dx, dy);
+    walk_strip<MODE>(a, ws, s, k, dx, dy, g, beg, end);
 
-    if constexpr (!BWD) {
+    if constexpr (MODE != kBwd) {
         if (inside) {
-            a.depth[pix] = k.acc.D;
-            a.normal[3 * pix + 0] = k.acc.N0;
-            a.normal[3 * pix + 1] = k.acc.N1;
-            a.normal[3 * pix + 2] = k.acc.N2;
+            if (a.depth) a.depth[pix] = k.acc.D;
+            if (a.normal) {
+                a.normal[3 * pix + 0] = k.acc.N0;
+                a.normal[3 * pix + 1] = k.acc.N1;
+                a.normal[3 * pix + 2] = k.acc.N2;
+            }
             if (a.alpha) a.alpha[pix] = k.acc.A;
         }
-    } else {
+    }
+    bool supervised = inside;
+    if constexpr (MODE == kFused) {
+        // Eq. 14 at this pixel and its gradient with respect to D and N
+        float sc = 0.f, sl = 0.f, sd = 0.f, one = 0.f;
+        if (inside) {
+            const float Dg = __ldg(&a.gt_depth[pix]);
+            supervised = Dg > 0.f;
+            if (supervised) {
+                const float G0 = __ldg(&a.gt_normal[3 * pix]), G1 = __ldg(&a.gt_normal[3 * pix + 1]),
+                            G2 = __ldg(&a.gt_normal[3 * pix + 2]);
+                const float N0 = k.acc.N0, N1 = k.acc.N1, N2 = k.acc.N2;
+                const float c = 1.f - (N0 * G0 + N1 * G1 + N2 * G2);
+                const float e0 = N0 - G0, e1 = N1 - G1, e2 = N2 - G2;
+                const float dd = k.acc.D - Dg;
+                sc = fabsf(c);
+                sl = fabsf(e0) + fabsf(e1) + fabsf(e2);
+                sd = fabsf(dd);
+                one = 1.f;
+                gD = a.a_depth * sgnf(dd);
+                const float scc = -a.a_cos * sgnf(c);
+                gN0 = scc * G0 + a.a_l1n * sgnf(e0);
+                gN1 = scc * G1 + a.a_l1n * sgnf(e1);
+                gN2 = scc * G2 + a.a_l1n * sgnf(e2);
+            }
+            if (a.out_dLdD) a.out_dLdD[pix] = gD;
+            if (a.out_dLdN) {
+                a.out_dLdN[3 * pix + 0] = gN0;
+                a.out_dLdN[3 * pix + 1] = gN1;
+                a.out_dLdN[3 * pix + 2] = gN2;
+            }
+        }
+        // the strip's 32 pixels belong to one view: one set of atomics per strip
+        double x0 = sc, x1 = sl, x2 = sd, x3 = one;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x0 += __shfl_xor_sync(kFull, x0, o);
+            x1 += __shfl_xor_sync(kFull, x1, o);
+            x2 += __shfl_xor_sync(kFull, x2, o);
+            x3 += __shfl_xor_sync(kFull, x3, o);
+        }
+        if (lane == 0 && x3 > 0.0) {
+            double* vs = a.view_sums + 4 * (size_t)v;
+            atomicAdd(vs + 0, x0);
+            atomicAdd(vs + 1, x1);
+            atomicAdd(vs + 2, x2);
+            atomicAdd(vs + 3, x3);
+        }
+    }
+    if constexpr (MODE != kFwd) {
         // back to front over the stack
-        const int lane = tid & 31;
-        const int cnt = inside ? s.cnt : 0;
+        const int cnt = supervised ? s.cnt : 0;
         int wmax = cnt;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, o));
         float A = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
         const float lam5 = a.c.lam5;
+        // software pipeline: the record of stack entry j - 1 is loaded while j is processed
+        int2 nxt = make_int2(-1, 0);
+        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f), qx = qn, qy = qn, qr = qn;
+        if (wmax - 1 >= 0 && wmax - 1 < cnt) {
+            nxt = k.stk[(wmax - 1) * 32];
+            const float4* r = a.rec + (size_t)nxt.x * 4;
+            qn = __ldg(r + 0); qx = __ldg(r + 1); qy = __ldg(r + 2); qr = __ldg(r + 3);
+        }
         for (int j = wmax - 1; j >= 0; --j) {
             const bool act = j < cnt;
-            float g[16];
+            float gr[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g[q] = 0.f;
+            for (int c = 0; c < 16; ++c) gr[c] = 0.f;
             int id = -1;
+            const int2 e = nxt;
+            const float4 n = qn, vx = qx, vy = qy, rr = qr;
+            if (j - 1 >= 0 && j - 1 < cnt) {
+                nxt = k.stk[(j - 1) * 32];
+                const float4* r = a.rec + (size_t)nxt.x * 4;
+                qn = __ldg(r + 0); qx = __ldg(r + 1); qy = __ldg(r + 2); qr = __ldg(r + 3);
+            }
             if (act) {
-                const int2 e = dyn_stk[j * NT + tid];
                 id = e.x;
                 const float Tj = __int_as_float(e.y);
-                const float4* r = a.rec + (size_t)id * 4;
-                const float4 n = __ldg(r + 0), vx = __ldg(r + 1), vy = __ldg(r + 2), rr = __ldg(r + 3);
                 PairEval pe;
                 eval_pair(n, vx, vy, rr, dx, dy, a.c, pe);   // same arithmetic as the walk
                 const float t = pe.t, w = pe.w;
@@ -314,7 +441,7 @@ __global__ void __launch_bounds__(TW * TH) k_splat(SplatArgs a)
                 B2 = fmaf(w, n.z, (1.f - w) * B2);
                 // Eq. 7-9: w = 2 sigmoid(5 lambda m) below the clamp, dw/dm = 5 lambda w (1 - w/2)
                 const float gm = (pe.m < 0.f) ? gw * lam5 * w * (1.f - 0.5f * w) : 0.f;
-                // m = r_side - |P|: radius gets gm, P gets -gm sgn(P)
+                // m = r_side - |P|: the radius gets gm, P gets -gm sgn(P)
                 const int ridx = (pe.sideX ? 0 : 2) + (pe.pos ? 0 : 1);
                 const float gP = (pe.P > 0.f) ? -gm : ((pe.P < 0.f) ? gm : 0.f);
                 // Eq. 6 in record form: P = t (d . v_c) - a
@@ -326,19 +453,19 @@ __global__ void __launch_bounds__(TW * TH) k_splat(SplatArgs a)
                 gnx = fmaf(gden, dx, gnx);
                 gny = fmaf(gden, dy, gny);
                 gnz = gnz + gden;
-                g[0] = gnx; g[1] = gny; g[2] = gnz; g[3] = gs;
+                gr[0] = gnx; gr[1] = gny; gr[2] = gnz; gr[3] = gs;
                 const int vo = pe.sideX ? 4 : 8;
 #pragma unroll
-                for (int q = 4; q < 12; q += 4) {
-                    if (q == vo) {
-                        g[q + 0] = gv * dx;
-                        g[q + 1] = gv * dy;
-                        g[q + 2] = gv;
-                        g[q + 3] = -gP;
+                for (int c = 4; c < 12; c += 4) {
+                    if (c == vo) {
+                        gr[c + 0] = gv * dx;
+                        gr[c + 1] = gv * dy;
+                        gr[c + 2] = gv;
+                        gr[c + 3] = -gP;
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) g[12 + q] = (q == ridx) ? gm : 0.f;
+                for (int c = 0; c < 4; ++c) gr[12 + c] = (c == ridx) ? gm : 0.f;
             }
             // warp aggregation: one atomic set per distinct record
             const unsigned actm = __ballot_sync(kFull, act);
@@ -347,40 +474,68 @@ __global__ void __launch_bounds__(TW * TH) k_splat(SplatArgs a)
             const bool uni = __all_sync(kFull, !act || peers == actm);
             if (uni) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    float x = g[q];
+                for (int c = 0; c < 16; ++c) {
+                    float x = gr[c];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-                    g[q] = x;
+                    gr[c] = x;
                 }
                 const int leader = __ffs(actm) - 1;
                 id = __shfl_sync(kFull, id, leader);
                 if (lane == leader) {
                     float4* dst = a.g_rec + (size_t)id * 4;
-                    atomicAdd(dst + 0, make_float4(g[0], g[1], g[2], g[3]));
-                    atomicAdd(dst + 1, make_float4(g[4], g[5], g[6], g[7]));
-                    atomicAdd(dst + 2, make_float4(g[8], g[9], g[10], g[11]));
-                    atomicAdd(dst + 3, make_float4(g[12], g[13], g[14], g[15]));
+                    atomicAdd(dst + 0, make_float4(gr[0], gr[1], gr[2], gr[3]));
+                    atomicAdd(dst + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
+                    atomicAdd(dst + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
+                    atomicAdd(dst + 3, make_float4(gr[12], gr[13], gr[14], gr[15]));
                 }
             } else if (act) {
                 float4* dst = a.g_rec + (size_t)id * 4;
-                atomicAdd(dst + 0, make_float4(g[0], g[1], g[2], g[3]));
-                atomicAdd(dst + 1, make_float4(g[4], g[5], g[6], g[7]));
-                atomicAdd(dst + 2, make_float4(g[8], g[9], g[10], g[11]));
-                atomicAdd(dst + 3, make_float4(g[12], g[13], g[14], g[15]));
+                atomicAdd(dst + 0, make_float4(gr[0], gr[1], gr[2], gr[3]));
+                atomicAdd(dst + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
+                atomicAdd(dst + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
+                atomicAdd(dst + 3, make_float4(gr[12], gr[13], gr[14], gr[15]));
             }
         }
     }
 }
 
+// Persistent warps: each takes strips from the work counter until none is left.
+template <int TW, int TH, int MODE>
+__global__ void __launch_bounds__(kWarps * 32, 4) k_splat(SplatArgs a)
+{
+    __shared__ WarpStage stage[kWarps];
+    extern __shared__ int2 dyn_stk[];       // backward: [kWarps][M][32]
+    const int w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    int2* stk_warp = dyn_stk + (size_t)w * a.M * 32;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= a.n_items) break;
+        run_strip<TW, TH, MODE>(a, stage[w], stk_warp, item);
+        __syncwarp();
+    }
+}
+
 // Work counts (diagnostic): full walk of every tile list, no early exit.
+template <int NT>
+struct CountSmem {
+    static constexpr int kBatch = NT < 128 ? NT : 128;
+    float4 rec[kBatch][4];
+    int id[kBatch];
+    int view, beg, end;
+};
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) k_count_pairs(SplatArgs a, unsigned long long* counts)
 {
     constexpr int NT = TW * TH;
-    __shared__ Smem<NT> sm;
+    __shared__ CountSmem<NT> sm;
     __shared__ unsigned long long red[3];
-    constexpr int B = Smem<NT>::kBatch;
+    constexpr int B = CountSmem<NT>::kBatch;
+
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
     if (tid == 0) {
@@ -552,8 +707,6 @@ struct LossArgs {
     float a_cos, a_l1n, a_depth;
 };
 
-__device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
-
 __global__ void __launch_bounds__(256) k_loss(LossArgs a)
 {
     const int v = blockIdx.y;
@@ -609,25 +762,46 @@ __global__ void __launch_bounds__(256) k_loss(LossArgs a)
 // ---------------------------------------------------------------------------
 // Host side.
 
-template <int TW, int TH>
-cudaError_t launch_splat(const SplatArgs& a, int n_tiles, bool bwd, int M, cudaStream_t st)
+struct LaunchCache {
+    int dev = -1;
+    int blocks_per_sm = 0;
+    size_t dyn = 0;
+};
+
+template <int TW, int TH, int MODE>
+cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st)
 {
-    constexpr int NT = TW * TH;
-    if (!bwd) {
-        k_splat<TW, TH, false><<<n_tiles, NT, 0, st>>>(a);
-        return cudaGetLastError();
-    }
-    const size_t dyn = sizeof(int2) * (size_t)M * NT;
-    static int configured_max[64] = {0};   // per device: largest dynamic smem set so far
+    constexpr int NS = TW * TH / 32;
+    a.n_items = n_tiles * NS;
+    const size_t dyn = MODE != kFwd ? sizeof(int2) * (size_t)kWarps * M * 32 : 0;
+    static LaunchCache cache[8];
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && configured_max[dev] < (int)dyn) {
-        cudaError_t e = cudaFuncSetAttribute(k_splat<TW, TH, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    LaunchCache& c = cache[dev & 7];
+    if (c.dev != dev || c.dyn != dyn) {
+        if (dyn > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_splat<TW, TH, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dyn);
+            if (e != cudaSuccess) return e;
+        }
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_splat<TW, TH, MODE>, kWarps * 32, dyn);
         if (e != cudaSuccess) return e;
-        configured_max[dev] = (int)dyn;
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        c.dev = dev;
+        c.dyn = dyn;
+        c.blocks_per_sm = (nb > 0 ? nb : 1) * sms;
     }
-    k_splat<TW, TH, true><<<n_tiles, NT, dyn, st>>>(a);
+    int blocks = c.blocks_per_sm;
+    const int need = (a.n_items + kWarps - 1) / kWarps;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_splat<TW, TH, MODE><<<blocks, kWarps * 32, dyn, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -658,11 +832,12 @@ SplatConst make_const(const ps_settings* s)
     return c;
 }
 
-cudaError_t dispatch(const SplatArgs& a, const ps_settings* s, int n_tiles, bool bwd, cudaStream_t st)
+template <int MODE>
+cudaError_t dispatch(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st)
 {
-    if (s->tile_w == 16) return launch_splat<16, 16>(a, n_tiles, bwd, s->M, st);
-    if (s->tile_w == 8) return launch_splat<8, 8>(a, n_tiles, bwd, s->M, st);
-    return launch_splat<32, 8>(a, n_tiles, bwd, s->M, st);
+    if (s->tile_w == 16) return launch_splat<16, 16, MODE>(a, n_tiles, s->M, st);
+    if (s->tile_w == 8) return launch_splat<8, 8, MODE>(a, n_tiles, s->M, st);
+    return launch_splat<32, 8, MODE>(a, n_tiles, s->M, st);
 }
 
 template <int TW, int TH>
@@ -672,25 +847,38 @@ cudaError_t launch_count(const SplatArgs& a, int n_tiles, unsigned long long* co
     return cudaGetLastError();
 }
 
-inline size_t bwd_ws(const ps_frame* f) { return sizeof(float4) * 4 * (size_t)f->n_records; }
+constexpr size_t kCounterBytes = 256;
+
+inline size_t bwd_ws(const ps_frame* f)
+{
+    return sizeof(float4) * 4 * (size_t)f->n_records + kCounterBytes;
+}
 
 }  // namespace
+
+extern "C" size_t ps_fwd_workspace_bytes(const ps_frame* f)
+{
+    (void)f;
+    return kCounterBytes;
+}
 
 extern "C" ps_status ps_splat_fwd(const ps_frame* f, const ps_settings* s, const float* rec,
                                   const float* key, const int* tile_ptr, const int* tile_ent,
                                   long long capacity, float* depth, float* normal, float* alpha,
-                                  int* d_status, ps_stream stream)
+                                  void* ws, size_t ws_bytes, int* d_status, ps_stream stream)
 {
     ps_status e = check_common(f, s, rec, key, tile_ptr, tile_ent, capacity);
     if (e != PS_OK) return e;
-    if (!depth || !normal) return PS_ERR_ARG;
+    if (!depth || !normal || !ws) return PS_ERR_ARG;
+    if (ws_bytes < kCounterBytes || (reinterpret_cast<uintptr_t>(ws) & 15)) return PS_ERR_ARG;
     SplatArgs a{};
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
     a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
     a.c = make_const(s); a.M = s->M;
+    a.counter = static_cast<int*>(ws);
     a.depth = depth; a.normal = normal; a.alpha = alpha; a.status = d_status;
-    if (dispatch(a, s, f->n_tiles, false, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    if (dispatch<kFwd>(a, s, f->n_tiles, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
         return PS_ERR_CUDA;
     return PS_OK;
 }
@@ -715,14 +903,58 @@ extern "C" ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* f, co
     if (ws_bytes < bwd_ws(f) || (reinterpret_cast<uintptr_t>(ws) & 15)) return PS_ERR_ARG;
     if (f->n_records == 0) return PS_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, bwd_ws(f), st));
+    const size_t grec_bytes = sizeof(float4) * 4 * (size_t)f->n_records;
+    PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, grec_bytes, st));
     SplatArgs a{};
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
     a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
     a.c = make_const(s); a.M = s->M;
     a.dLdD = dLdD; a.dLdN = dLdN; a.g_rec = reinterpret_cast<float4*>(ws); a.status = d_status;
-    if (dispatch(a, s, f->n_tiles, true, st) != cudaSuccess) return PS_ERR_CUDA;
+    a.counter = reinterpret_cast<int*>(static_cast<char*>(ws) + grec_bytes);
+    if (dispatch<kBwd>(a, s, f->n_tiles, st) != cudaSuccess) return PS_ERR_CUDA;
+    ChainArgs c;
+    c.views = f->views; c.center = planes->center; c.quat = planes->quat; c.radii = planes->radii;
+    c.g_rec = a.g_rec; c.g_center = g_center; c.g_quat = g_quat; c.g_radii = g_radii;
+    c.single_radii = (s->flags & PS_SINGLE_RADII) ? 1 : 0;
+    dim3 grid((f->max_K + 127) / 128, f->n_views);
+    k_chain<<<grid, 128, 0, st>>>(c);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
+
+extern "C" ps_status ps_splat_fused(const ps_planes* planes, const ps_frame* f,
+                                    const ps_settings* s, const float* rec, const float* key,
+                                    const int* tile_ptr, const int* tile_ent, long long capacity,
+                                    const float* gt_depth, const float* gt_normal, float* depth,
+                                    float* normal, float* dL_dD, float* dL_dN, double* view_sums,
+                                    float* g_center, float* g_quat, float* g_radii, void* ws,
+                                    size_t ws_bytes, int* d_status, ps_stream stream)
+{
+    ps_status e = check_common(f, s, rec, key, tile_ptr, tile_ent, capacity);
+    if (e != PS_OK) return e;
+    if (!planes || !planes->center || !planes->quat || !planes->radii) return PS_ERR_ARG;
+    if (!gt_depth || !gt_normal || !view_sums || !g_center || !g_quat || !g_radii || !ws)
+        return PS_ERR_ARG;
+    if (s->flags & PS_HARD) return PS_ERR_ARG;
+    if (ws_bytes < bwd_ws(f) || (reinterpret_cast<uintptr_t>(ws) & 15)) return PS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PS_CUDA_CHECK(cudaMemsetAsync(view_sums, 0, sizeof(double) * 4 * (size_t)f->n_views, st));
+    const size_t grec_bytes = sizeof(float4) * 4 * (size_t)f->n_records;
+    if (grec_bytes) PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, grec_bytes, st));
+    SplatArgs a{};
+    a.views = f->views; a.n_views = f->n_views;
+    a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
+    a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
+    a.c = make_const(s); a.M = s->M;
+    a.depth = depth; a.normal = normal; a.alpha = nullptr;
+    a.g_rec = reinterpret_cast<float4*>(ws); a.status = d_status;
+    a.counter = reinterpret_cast<int*>(static_cast<char*>(ws) + grec_bytes);
+    a.gt_depth = gt_depth; a.gt_normal = gt_normal;
+    a.out_dLdD = dL_dD; a.out_dLdN = dL_dN; a.view_sums = view_sums;
+    a.a_cos = s->a_cos; a.a_l1n = s->a_l1n; a.a_depth = s->a_depth;
+    if (dispatch<kFused>(a, s, f->n_tiles, st) != cudaSuccess) return PS_ERR_CUDA;
+    if (f->n_records == 0) return PS_OK;
     ChainArgs c;
     c.views = f->views; c.center = planes->center; c.quat = planes->quat; c.radii = planes->radii;
     c.g_rec = a.g_rec; c.g_center = g_center; c.g_quat = g_quat; c.g_radii = g_radii;

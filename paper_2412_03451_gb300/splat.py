@@ -83,6 +83,8 @@ class Renderer:
         self.view_sums = torch.zeros((self.V, 4), dtype=torch.float64, device=dev)
         self.bwd_ws = torch.zeros((B.ps_bwd_workspace_bytes(f) + 255) // 256 * 64,
                                   dtype=torch.float32, device=dev)
+        self.fwd_ws = torch.zeros((B.ps_fwd_workspace_bytes(f) + 255) // 256 * 64,
+                                  dtype=torch.float32, device=dev)
         self._batches = None
         self.settings = None
 
@@ -154,7 +156,7 @@ class Renderer:
     def splat_forward(self, alpha=True):
         B.ps_splat_fwd(self.frame, self.settings, self.rec, self.key, self.tile_ptr, self.tile_ent,
                        self.capacity, self.depth, self.normal, self.alpha if alpha else None,
-                       self.status)
+                       self.fwd_ws, self.status)
         return self.depth, self.normal
 
     def forward(self, flat: torch.Tensor, lam: float, flags=None, alpha=True):
@@ -169,6 +171,21 @@ class Renderer:
     def loss(self, gt_depth, gt_normal):
         B.ps_loss(self.frame, self.settings, self.depth, self.normal, gt_depth, gt_normal,
                   self.dLdD, self.dLdN, self.view_sums)
+        return self.view_sums
+
+    def fused(self, flat: torch.Tensor, grad_flat: torch.Tensor, gt_depth, gt_normal,
+              write_maps: bool = False):
+        """Forward + Eq. 14 loss + backward in one pass (after project_bin).
+        Accumulates the loss gradient into grad_flat; fills view_sums; writes
+        depth/normal/dL maps only if write_maps."""
+        pl = self.planes_struct(flat)
+        gc, gq, gr = flat_views(grad_flat, self.P)
+        m = write_maps
+        B.ps_splat_fused(pl, self.frame, self.settings, self.rec, self.key, self.tile_ptr,
+                         self.tile_ent, self.capacity, gt_depth, gt_normal,
+                         self.depth if m else None, self.normal if m else None,
+                         self.dLdD if m else None, self.dLdN if m else None, self.view_sums,
+                         gc, gq, gr, self.bwd_ws, self.status)
         return self.view_sums
 
     def backward(self, flat: torch.Tensor, grad_flat: torch.Tensor, dLdD=None, dLdN=None):
@@ -204,8 +221,10 @@ class Fitter:
     """Adam fit of the planes of a batch (Sec. 3.3): per step, lambda from
     Eq. 10, render, Eq. 14 loss, backward, Adam with lr 1e-3 for every group."""
 
-    def __init__(self, renderer: Renderer, flat: torch.Tensor, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    def __init__(self, renderer: Renderer, flat: torch.Tensor, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8,
+                 fused: bool = True):
         self.r = renderer
+        self.fused = fused
         self.flat = flat
         self.grad = torch.zeros_like(flat)
         self.m = torch.zeros_like(flat)
@@ -227,13 +246,17 @@ class Fitter:
         mark("start")
         r.project_bin(self.flat, lam)
         mark("project_bin")
-        r.splat_forward(alpha=False)
-        mark("splat_fwd")
-        r.loss(gt_depth, gt_normal)
         self.grad.zero_()
-        mark("loss")
-        r.backward(self.flat, self.grad)
-        mark("splat_bwd")
+        if self.fused:
+            r.fused(self.flat, self.grad, gt_depth, gt_normal)
+            mark("splat_fused")
+        else:
+            r.splat_forward(alpha=False)
+            mark("splat_fwd")
+            r.loss(gt_depth, gt_normal)
+            mark("loss")
+            r.backward(self.flat, self.grad)
+            mark("splat_bwd")
         P = r.P
         t = self.ite + 1
         B.ps_adam_step(self.flat[:7 * P], self.grad[:7 * P], self.m[:7 * P], self.v[:7 * P],

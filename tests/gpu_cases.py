@@ -91,3 +91,37 @@ def grad_errors(g_gpu, g_or, rel=1e-3, floor=1e-6):
     bound = rel * n_or + floor * max(n_or.max(), 1e-30)
     ratio = err / np.maximum(bound, 1e-300)
     return int((err > bound).sum()), float(ratio.max())
+
+
+def gpu_fused_vs_split(planes: S.Planes, cams: S.Cameras, lam: float, gt_depth, gt_normal,
+                       tile=(16, 16), M=30):
+    """Runs the fused forward+loss+backward and the separate fwd -> loss -> bwd
+    calls on the same inputs; returns both results as numpy arrays."""
+    import torch
+    from paper_2412_03451_gb300 import splat as SP
+    V = cams.V
+    r = SP.Renderer([cams.H] * V, [cams.W] * V, [0] * V, [0, planes.K], tile=tile, M=M)
+    r.set_cameras(cams.w2c, cams.intr)
+    flat = SP.planes_to_flat(planes.center, planes.quat, planes.radii, "cuda")
+    r.ensure_capacity(flat, lam)
+    gD = torch.from_numpy(np.asarray(gt_depth, np.float32).reshape(-1)).cuda()
+    gN = torch.from_numpy(np.asarray(gt_normal, np.float32).reshape(-1, 3)).cuda()
+    r.status.zero_()
+    # separate path
+    r.forward(flat, lam)
+    r.loss(gD, gN)
+    g_split = torch.zeros_like(flat)
+    r.backward(flat, g_split)
+    split = dict(depth=r.depth.clone(), normal=r.normal.clone(), dLdD=r.dLdD.clone(),
+                 dLdN=r.dLdN.clone(), sums=r.view_sums.clone(), grad=g_split)
+    # fused path
+    r.depth.zero_(); r.normal.zero_(); r.dLdD.zero_(); r.dLdN.zero_()
+    r.project_bin(flat, lam)
+    g_fused = torch.zeros_like(flat)
+    r.fused(flat, g_fused, gD, gN, write_maps=True)
+    fused = dict(depth=r.depth.clone(), normal=r.normal.clone(), dLdD=r.dLdD.clone(),
+                 dLdN=r.dLdN.clone(), sums=r.view_sums.clone(), grad=g_fused)
+    torch.cuda.synchronize()
+    status = int(r.status.item())
+    to_np = lambda d: {k: v.cpu().numpy() for k, v in d.items()}
+    return to_np(split), to_np(fused), status

@@ -89,7 +89,7 @@ def test_null_arguments_rejected_before_launch(lib):
     s = B.make_settings(20.0, B.filter_margin(20.0))
     assert lib.ps_project_cull(None, None, ctypes.byref(s), None, None, None, None, None) == B.PS_ERR_ARG
     assert lib.ps_splat_fwd(None, ctypes.byref(s), None, None, None, None, 0, None, None, None,
-                            None, None) == B.PS_ERR_ARG
+                            None, 0, None, None) == B.PS_ERR_ARG
     assert lib.ps_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 1, 0.0,
                             None) == B.PS_ERR_ARG
     assert lib.ps_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, 0.0,
@@ -108,5 +108,5 @@ def test_settings_validation(lib):
         kw.update(bad)
         s = B.make_settings(kw.pop("lam"), kw.pop("delta"), **kw)
         code = lib.ps_splat_fwd(ctypes.byref(frame), ctypes.byref(s), dummy, dummy, dummy, dummy,
-                                1, dummy, dummy, None, None, None)
+                                1, dummy, dummy, None, dummy, 256, None, None)
         assert code == B.PS_ERR_ARG, bad

@@ -322,3 +322,50 @@ def test_paper_scale_backward_sampled_rows(big_case):
     report("bwd_big", **res)
     for k, (nbad, worst) in res.items():
         assert nbad == 0, (k, nbad, worst)
+
+
+# ---------------------------------------------------------------------------
+# Fused forward + loss + backward.
+
+@pytest.mark.parametrize("lam,tile", [(20.0 / np.e, (16, 16)), (20.0, (8, 8)), (300.0, (32, 8))])
+def test_fused_equals_separate_kernels(lam, tile):
+    from gpu_cases import gpu_fused_vs_split
+    room, init = tiny_init()
+    D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, room.cams.w2c,
+                        room.cams.intr, room.cams.H, room.cams.W)
+    sp, fu, status = gpu_fused_vs_split(init, room.cams, lam, D, N, tile=tile)
+    assert status == 0
+    # same walk, same arithmetic: maps and loss gradients are identical
+    assert np.array_equal(sp["depth"], fu["depth"]) and np.array_equal(sp["normal"], fu["normal"])
+    assert np.array_equal(sp["dLdD"], fu["dLdD"]) and np.array_equal(sp["dLdN"], fu["dLdN"])
+    assert np.allclose(sp["sums"], fu["sums"], rtol=1e-6)
+    # gradients differ only by the order of float atomics
+    K = init.K
+    for a, b in ((0, 3 * K), (3 * K, 7 * K), (7 * K, 11 * K)):
+        gs, gf = sp["grad"][a:b], fu["grad"][a:b]
+        assert np.linalg.norm(gs - gf) <= 1e-5 * np.linalg.norm(gs) + 1e-6
+    report("fused_vs_split", lam=lam, tile=tile)
+
+
+def test_fused_gradient_against_oracle():
+    from gpu_cases import gpu_fused_vs_split
+    room, init = tiny_init(4)
+    lam = 20.0
+    D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, room.cams.w2c,
+                        room.cams.intr, room.cams.H, room.cams.W)
+    sp, fu, status = gpu_fused_vs_split(init, room.cams, lam, D, N)
+    o = oracle_render(init, room.cams, lam)
+    tot, dD, dN, sums = O.loss(o["depth"], o["normal"], D, N)
+    gc, gq, gr = O.backward(init.center, init.quat, init.radii, room.cams.w2c, room.cams.intr,
+                            room.cams.H, room.cams.W, f32(lam), dD, dN, z_near=f32(0.01))
+    K = init.K
+    g = fu["grad"]
+    res = {k: grad_errors(g[a:b].reshape(K, -1), ref) for k, (a, b), ref in
+           (("g_center", (0, 3 * K), gc), ("g_quat", (3 * K, 7 * K), gq),
+            ("g_radii", (7 * K, 11 * K), gr))}
+    loss_gpu = float((fu["sums"][:, :3] * np.array([5.0, 5.0, 1.0])).sum())
+    report("fused_vs_oracle", loss_rel=abs(loss_gpu - tot) / tot, **res)
+    assert abs(loss_gpu - tot) <= 1e-4 * tot
+    # unmasked upstream: a few ill-conditioned pixels may move a plane's gradient
+    nbad = sum(v[0] for v in res.values())
+    assert nbad <= 0.05 * 3 * K, res
