@@ -211,6 +211,27 @@ ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* frame,
                        float* g_radii, void* ws, size_t ws_bytes, int* d_status,
                        ps_stream stream);
 
+/* ps_splat_bwd for callers that cannot allocate device memory (an engine whose
+   device memory belongs to a fixed arena, a real-time loop that must never
+   enter the CUDA allocator, a plug-in host without a device allocator).  The
+   paper has no counterpart: this is a deployment variant of ps_splat_bwd.
+   Same arguments, results and accumulate-into-gradients semantics as
+   ps_splat_bwd, but without ws/ws_bytes: its scratch is a 4 MiB array
+   compiled into the library, which every device that loads the library holds
+   until the process exits.  Limit: frame->n_records <= 65536; larger frames
+   return PS_ERR_ARG before anything is launched.  No cudaMalloc, cudaFree or
+   other allocating call is made.  The first call on a device looks up the
+   array's device address (cudaGetSymbolAddress) with that device current and
+   caches it; make that first call before any stream capture.  Every call
+   clears the part of the array it uses, but all calls share the one array:
+   calls that may overlap on the GPU (different streams, or different host
+   threads on the same device) race and must be serialised by the caller. */
+ps_status ps_splat_bwd_noalloc(const ps_planes* planes, const ps_frame* frame,
+                               const ps_settings* settings, const float* rec, const float* key,
+                               const int* tile_ptr, const int* tile_ent, long long capacity,
+                               const float* dL_dD, const float* dL_dN, float* g_center,
+                               float* g_quat, float* g_radii, int* d_status, ps_stream stream);
+
 /* Forward splatting, render loss and backward splatting fused (Sec. 3.2,
    Eq. 4, 6-14).  Because the loss of Eq. 14 is a sum of per-pixel terms, each
    pixel's composited list, built once, serves both the forward and the

@@ -32,6 +32,8 @@
 // warp that hold the same record, and added to a per-record accumulator; a
 // second kernel chains the records through the camera transform and Eq. 2-3
 // into the world parameters.
+#include <mutex>
+
 #include "ps_internal.cuh"
 
 using namespace ps;
@@ -1008,4 +1010,59 @@ extern "C" ps_status ps_count_pairs(const ps_frame* f, const ps_settings* s, con
     else if (s->tile_w == 8) err = launch_count<8, 8>(a, f->n_tiles, c, st);
     else err = launch_count<32, 8>(a, f->n_tiles, c, st);
     return err == cudaSuccess ? PS_OK : PS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Backward splatting for callers that cannot allocate device memory.
+//
+// Some callers have no way to hand the library a scratch buffer: an engine
+// whose device memory is owned by a fixed arena that other code may not grow,
+// a real-time loop that must never enter the CUDA allocator (cudaMalloc can
+// synchronise the device and take unbounded time), or a host program that
+// loads this library as a plug-in without a device allocator of its own.  For
+// them ps_splat_bwd_noalloc uses a scratch array that is part of the library
+// image itself: a file-scope __device__ array that every device holds from the
+// moment the library's module is loaded on it until the process exits.
+namespace {
+
+constexpr long long kNoAllocMaxRecords = 65536;   // 64 bytes of gradient per record: 4 MiB
+constexpr size_t kNoAllocBytes = sizeof(float4) * 4 * (size_t)kNoAllocMaxRecords + kCounterBytes;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device.  In host code the symbol's
+// name is only a host-side stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+}  // namespace
+
+extern "C" ps_status ps_splat_bwd_noalloc(const ps_planes* planes, const ps_frame* f,
+                                          const ps_settings* s, const float* rec,
+                                          const float* key, const int* tile_ptr,
+                                          const int* tile_ent, long long capacity,
+                                          const float* dLdD, const float* dLdN, float* g_center,
+                                          float* g_quat, float* g_radii, int* d_status,
+                                          ps_stream stream)
+{
+    if (!f || f->n_records < 0) return PS_ERR_ARG;
+    if ((long long)f->n_records > kNoAllocMaxRecords) return PS_ERR_ARG;   // too large for the static scratch
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
+    if (dev < 0 || dev >= 64) return PS_ERR_ARG;
+    void* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PS_ERR_CUDA;
+            g_noalloc_addr[dev] = p;
+        }
+        ws = g_noalloc_addr[dev];
+    }
+    // ps_splat_bwd clears the accumulators and the work counter before use, so
+    // whatever an earlier call left in the array does not leak into this one.
+    return ps_splat_bwd(planes, f, s, rec, key, tile_ptr, tile_ent, capacity, dLdD, dLdN,
+                        g_center, g_quat, g_radii, ws, kNoAllocBytes, d_status, stream);
 }
