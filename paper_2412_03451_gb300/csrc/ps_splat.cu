@@ -327,6 +327,16 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
     k.acc = Accum{0.f, 0.f, 0.f, 0.f, 0.f};
     k.stk = stk_warp + lane;
     float gD = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
+    // fused: the pixel's supervision is loaded before the walk so its latency is hidden
+    float Dg = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
+    if constexpr (MODE == kFused) {
+        if (inside) {
+            Dg = __ldg(&a.gt_depth[pix]);
+            G0 = __ldg(&a.gt_normal[3 * pix]);
+            G1 = __ldg(&a.gt_normal[3 * pix + 1]);
+            G2 = __ldg(&a.gt_normal[3 * pix + 2]);
+        }
+    }
     if constexpr (MODE == kBwd) {
         if (inside) {
             gD = __ldg(&a.dLdD[pix]);
@@ -354,11 +364,8 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
         // Eq. 14 at this pixel and its gradient with respect to D and N
         float sc = 0.f, sl = 0.f, sd = 0.f, one = 0.f;
         if (inside) {
-            const float Dg = __ldg(&a.gt_depth[pix]);
             supervised = Dg > 0.f;
             if (supervised) {
-                const float G0 = __ldg(&a.gt_normal[3 * pix]), G1 = __ldg(&a.gt_normal[3 * pix + 1]),
-                            G2 = __ldg(&a.gt_normal[3 * pix + 2]);
                 const float N0 = k.acc.N0, N1 = k.acc.N1, N2 = k.acc.N2;
                 const float c = 1.f - (N0 * G0 + N1 * G1 + N2 * G2);
                 const float e0 = N0 - G0, e1 = N1 - G1, e2 = N2 - G2;
@@ -469,34 +476,62 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
 #pragma unroll
                 for (int c = 0; c < 4; ++c) gr[12 + c] = (c == ridx) ? gm : 0.f;
             }
-            // warp aggregation: one atomic set per distinct record
+            // warp aggregation: for each distinct record among the active lanes, the
+            // 16 gradient floats are summed over its lanes by a transpose-reduction
+            // (16 shuffles leave lane pair (2c, 2c+1) holding the total of float c)
+            // and added with one 16-lane atomic instruction
             const unsigned actm = __ballot_sync(kFull, act);
             if (actm == 0) continue;
             const unsigned peers = __match_any_sync(kFull, id);
-            const bool uni = __all_sync(kFull, !act || peers == actm);
-            if (uni) {
+            unsigned rem = actm;
+            while (rem) {
+                const int leader = __ffs(rem) - 1;
+                const unsigned gmask = __shfl_sync(kFull, peers, leader);
+                const int gid = __shfl_sync(kFull, id, leader);
+                rem &= ~gmask;
+                const bool member = (gmask >> lane) & 1u;
+                float v[16];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    float x = gr[c];
+                for (int c = 0; c < 16; ++c) v[c] = member ? gr[c] : 0.f;
+                // round 0: 16 -> 8 values (partner lane ^ 16)
+                {
+                    const bool hi = lane & 16;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-                    gr[c] = x;
+                    for (int c = 0; c < 8; ++c) {
+                        const float send = hi ? v[c] : v[c + 8];
+                        const float keep = hi ? v[c + 8] : v[c];
+                        v[c] = keep + __shfl_xor_sync(kFull, send, 16);
+                    }
                 }
-                const int leader = __ffs(actm) - 1;
-                id = __shfl_sync(kFull, id, leader);
-                if (lane == leader) {
-                    float4* dst = a.g_rec + (size_t)id * 4;
-                    atomicAdd(dst + 0, make_float4(gr[0], gr[1], gr[2], gr[3]));
-                    atomicAdd(dst + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
-                    atomicAdd(dst + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
-                    atomicAdd(dst + 3, make_float4(gr[12], gr[13], gr[14], gr[15]));
+                {
+                    const bool hi = lane & 8;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float send = hi ? v[c] : v[c + 4];
+                        const float keep = hi ? v[c + 4] : v[c];
+                        v[c] = keep + __shfl_xor_sync(kFull, send, 8);
+                    }
                 }
-            } else if (act) {
-                float4* dst = a.g_rec + (size_t)id * 4;
-                atomicAdd(dst + 0, make_float4(gr[0], gr[1], gr[2], gr[3]));
-                atomicAdd(dst + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
-                atomicAdd(dst + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
-                atomicAdd(dst + 3, make_float4(gr[12], gr[13], gr[14], gr[15]));
+                {
+                    const bool hi = lane & 4;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const float send = hi ? v[c] : v[c + 2];
+                        const float keep = hi ? v[c + 2] : v[c];
+                        v[c] = keep + __shfl_xor_sync(kFull, send, 4);
+                    }
+                }
+                {
+                    const bool hi = lane & 2;
+                    const float send = hi ? v[0] : v[1];
+                    const float keep = hi ? v[1] : v[0];
+                    v[0] = keep + __shfl_xor_sync(kFull, send, 2);
+                }
+                v[0] += __shfl_xor_sync(kFull, v[0], 1);
+                if ((lane & 1) == 0) {
+                    float* dst = reinterpret_cast<float*>(a.g_rec + (size_t)gid * 4);
+                    atomicAdd(dst + ((lane >> 1) & 15), v[0]);
+                }
             }
         }
     }
