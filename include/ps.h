@@ -73,6 +73,15 @@ typedef enum {
 
 #define PS_MAX_M 64        /* largest supported M (nearest intersections per ray) */
 
+/* Per-iteration scalars kept in device memory, so that a captured CUDA graph of
+   an optimisation step can be replayed for every iteration (see ps_step_advance). */
+typedef struct ps_step_state {
+    double delta;          /* binning margin of this iteration (see ps_settings.delta) */
+    float lambda;          /* Eq. 10 value of this iteration */
+    int step;              /* Adam step number, from 1 */
+    float bc1, bc2;        /* Adam bias corrections 1 - b1^step, 1 - b2^step */
+} ps_step_state;
+
 /* Per-step settings.  Passed by host pointer; read on the host. */
 typedef struct ps_settings {
     float lambda;          /* Eq. 10 value for this iteration */
@@ -84,6 +93,8 @@ typedef struct ps_settings {
     int flags;             /* PS_SINGLE_RADII | PS_HARD */
     float a_cos, a_l1n, a_depth;  /* Eq. 14 weights: alpha_1 = 5, alpha_1 = 5, alpha_2 = 1 */
     int reserved;
+    const ps_step_state* d_state; /* optional (device): if not NULL, lambda and delta are read
+                                     from *d_state when the kernels run, not from the fields above */
 } ps_settings;
 
 /* Per-view descriptor, 128 bytes.  Filled on the host by ps_plan_views and
@@ -269,6 +280,18 @@ ps_status ps_adam_step(float* param, const float* grad, float* m, float* v, long
 ps_status ps_count_pairs(const ps_frame* frame, const ps_settings* settings, const float* rec,
                          const float* key, const int* tile_ptr, const int* tile_ent,
                          long long capacity, long long* d_counts, ps_stream stream);
+
+/* Graph replay support: copies d_sched[min(*d_iter, n_sched - 1)] into *d_state
+   and increments *d_iter (one device thread; device pointers).  Launched at the
+   start of a captured step, it makes every replay use the next iteration's
+   lambda, delta and Adam bias corrections. */
+ps_status ps_step_advance(ps_step_state* d_state, const ps_step_state* d_sched, int n_sched,
+                          int* d_iter, ps_stream stream);
+
+/* ps_adam_step with the step's bias corrections read from d_state (device). */
+ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v, long long n,
+                             float lr, float b1, float b2, float eps,
+                             const ps_step_state* d_state, float clamp_min, ps_stream stream);
 
 /* Human-readable name of a status code. */
 const char* ps_status_string(ps_status status);

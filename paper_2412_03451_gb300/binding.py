@@ -25,7 +25,8 @@ PS_MAX_M = 64
 EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin_tiles",
            "ps_fwd_workspace_bytes", "ps_splat_fwd", "ps_loss", "ps_bwd_workspace_bytes", "ps_splat_bwd",
            "ps_splat_fused", "ps_adam_step",
-           "ps_count_pairs", "ps_status_string", "ps_version")
+           "ps_count_pairs", "ps_step_advance", "ps_adam_step_state", "ps_status_string",
+           "ps_version")
 
 
 class PsSettings(ctypes.Structure):
@@ -34,7 +35,12 @@ class PsSettings(ctypes.Structure):
                 ("delta", ctypes.c_double), ("M", ctypes.c_int),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("flags", ctypes.c_int),
                 ("a_cos", ctypes.c_float), ("a_l1n", ctypes.c_float), ("a_depth", ctypes.c_float),
-                ("reserved", ctypes.c_int)]
+                ("reserved", ctypes.c_int), ("d_state", ctypes.c_void_p)]
+
+
+class PsStepState(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("lambda_", ctypes.c_float), ("step", ctypes.c_int),
+                ("bc1", ctypes.c_float), ("bc2", ctypes.c_float)]
 
 
 class PsView(ctypes.Structure):
@@ -58,7 +64,8 @@ class PsPlanes(ctypes.Structure):
 
 
 assert ctypes.sizeof(PsView) == 128
-assert ctypes.sizeof(PsSettings) == 56
+assert ctypes.sizeof(PsSettings) == 64
+assert ctypes.sizeof(PsStepState) == 24
 
 _lock = threading.Lock()
 _lib = None
@@ -92,6 +99,8 @@ def load():
             "ps_splat_fused": ([P, P, P, P, P, P, P, LL, P, P, P, P, P, P, P, P, P, P, P, SZ, P, P], I),
             "ps_adam_step": ([P, P, P, P, LL, F, F, F, F, I, F, P], I),
             "ps_count_pairs": ([P, P, P, P, P, P, LL, P, P], I),
+            "ps_step_advance": ([P, P, I, P, P], I),
+            "ps_adam_step_state": ([P, P, P, P, LL, F, F, F, F, P, F, P], I),
             "ps_status_string": ([I], ctypes.c_char_p),
             "ps_version": ([], I),
         }
@@ -144,7 +153,7 @@ def ps_plan_views(H, W, scene_of_view, plane_ptr, w2c, intr, tile_w, tile_h):
 
 
 def make_settings(lam, delta, M=30, tile_w=16, tile_h=16, flags=0, w_min=1e-4, z_near=0.01,
-                  z_far=100.0, a_cos=5.0, a_l1n=5.0, a_depth=1.0) -> PsSettings:
+                  z_far=100.0, a_cos=5.0, a_l1n=5.0, a_depth=1.0, d_state=None) -> PsSettings:
     s = PsSettings()
     s.lambda_ = float(lam)
     s.w_min = float(w_min)
@@ -155,7 +164,24 @@ def make_settings(lam, delta, M=30, tile_w=16, tile_h=16, flags=0, w_min=1e-4, z
     s.tile_w, s.tile_h = int(tile_w), int(tile_h)
     s.flags = int(flags)
     s.a_cos, s.a_l1n, s.a_depth = float(a_cos), float(a_l1n), float(a_depth)
+    s.d_state = None if d_state is None else d_state.data_ptr()
     return s
+
+
+def step_schedule(n: int, first: int = 0, b1: float = 0.9, b2: float = 0.999) -> bytes:
+    """Packed ps_step_state entries for iterations first .. first + n - 1: lambda
+    (Eq. 10, rounded to f32), the binning margin of that f32 lambda, the Adam
+    step number and bias corrections -- the same values the host path uses."""
+    arr = (PsStepState * n)()
+    for i in range(n):
+        ite = first + i
+        lam = float(np.float32(lambda_schedule(ite)))
+        arr[i].lambda_ = lam
+        arr[i].delta = filter_margin(lam)
+        arr[i].step = ite + 1
+        arr[i].bc1 = float(np.float32(1.0 - b1 ** (ite + 1)))
+        arr[i].bc2 = float(np.float32(1.0 - b2 ** (ite + 1)))
+    return bytes(arr)
 
 
 def filter_margin(lam: float, w_min: float = 1e-4) -> float:
@@ -247,6 +273,18 @@ def ps_count_pairs(frame, settings, rec, key, tile_ptr, tile_ent, capacity, coun
     _check(load().ps_count_pairs(ctypes.byref(frame), ctypes.byref(settings), _ptr(rec), _ptr(key),
                                  _ptr(tile_ptr), _ptr(tile_ent), int(capacity), _ptr(counts),
                                  _stream(stream)), "ps_count_pairs")
+
+
+def ps_step_advance(d_state, d_sched, n_sched, d_iter, stream=None):
+    _check(load().ps_step_advance(_ptr(d_state), _ptr(d_sched), int(n_sched), _ptr(d_iter),
+                                  _stream(stream)), "ps_step_advance")
+
+
+def ps_adam_step_state(param, grad, m, v, lr, b1, b2, eps, d_state, clamp_min=float("nan"),
+                       stream=None):
+    _check(load().ps_adam_step_state(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
+                                     float(lr), float(b1), float(b2), float(eps), _ptr(d_state),
+                                     float(clamp_min), _stream(stream)), "ps_adam_step_state")
 
 
 def ps_status_string(code: int) -> str:

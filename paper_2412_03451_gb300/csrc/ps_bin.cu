@@ -15,8 +15,10 @@
 //   3. tile scan: tile_ptr = exclusive prefix sum, total -> d_required;
 //   4. scatter: one thread per pair writes its record id into a slot of its
 //      tile (unordered, via per-tile cursors);
-//   5. sort: each tile's slots by (key, record id): shared-memory bitonic sort
-//      up to kSortCap entries, an O(n^2) rank sort beyond.
+//   5. sort: each tile's slots by (key, record id): one warp per tile sorts up
+//      to 32 entries in registers and up to kWarpSortCap in its slice of shared
+//      memory (bitonic networks); a CTA per tile takes longer lists (bitonic up
+//      to kSortCap entries, an O(n^2) rank sort beyond).
 // Every pair gets its own thread, so a plane covering a thousand tiles costs
 // no more latency than one covering a single tile.
 #include "ps_internal.cuh"
@@ -25,7 +27,9 @@ using namespace ps;
 
 namespace {
 
-constexpr int kSortCap = 4096;     // entries sorted in shared memory (32 KB of u64)
+constexpr int kSortCap = 4096;     // entries sorted in shared memory by a CTA (32 KB of u64)
+constexpr int kWarpSortCap = 1024; // entries sorted by one warp (8 KB of u64 per warp)
+constexpr int kSortWarps = 8;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;      // elements per thread per scan tile
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -265,6 +269,61 @@ __device__ __forceinline__ unsigned long long sort_key(const float* __restrict__
     return ((unsigned long long)__float_as_uint(__ldg(&key[r])) << 32) | (unsigned)r;
 }
 
+// Short lists: one warp per tile.
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __restrict__ tile_ptr,
+                                                               int n_tiles,
+                                                               const int* __restrict__ ent_tmp,
+                                                               const float* __restrict__ key,
+                                                               int* __restrict__ tile_ent)
+{
+    extern __shared__ unsigned long long s_warp_keys[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * kSortWarps + w;
+    if (t >= n_tiles) return;
+    const int b = tile_ptr[t], e = tile_ptr[t + 1];
+    const int n = e - b;
+    if (n <= 0 || n > kWarpSortCap) return;
+    if (n == 1) {
+        if (lane == 0) tile_ent[b] = ent_tmp[b];
+        return;
+    }
+    if (n <= 32) {
+        unsigned long long v = lane < n ? sort_key(key, ent_tmp[b + lane]) : ~0ull;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
+                const bool up = (lane & k) == 0;
+                const bool lower = (lane & j) == 0;
+                v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
+            }
+        }
+        if (lane < n) tile_ent[b + lane] = (int)(unsigned)(v & 0xffffffffu);
+        return;
+    }
+    unsigned long long* s = s_warp_keys + (size_t)w * kWarpSortCap;
+    int N = 64;
+    while (N < n) N <<= 1;
+    for (int i = lane; i < N; i += 32) s[i] = i < n ? sort_key(key, ent_tmp[b + i]) : ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < N; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long x = s[i], y = s[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) { s[i] = y; s[ixj] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    for (int i = lane; i < n; i += 32) tile_ent[b + i] = (int)(unsigned)(s[i] & 0xffffffffu);
+}
+
+// Long lists: one CTA per tile (tiles with at most kWarpSortCap entries return at once).
 __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr,
                                                const int* __restrict__ ent_tmp,
                                                const float* __restrict__ key,
@@ -274,12 +333,8 @@ __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr,
     const int t = blockIdx.x;
     const int b = tile_ptr[t], e = tile_ptr[t + 1];
     const int n = e - b;
-    if (n <= 0) return;
+    if (n <= kWarpSortCap) return;
     const int tid = threadIdx.x, NT = blockDim.x;
-    if (n == 1) {
-        if (tid == 0) tile_ent[b] = ent_tmp[b];
-        return;
-    }
     if (n <= kSortCap) {
         int N = 2;
         while (N < n) N <<= 1;
@@ -302,7 +357,7 @@ __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr,
         for (int i = tid; i < n; i += NT) tile_ent[b + i] = (int)(unsigned)(s[i] & 0xffffffffu);
         return;
     }
-    // long list: rank of each element = number of smaller keys (keys are unique)
+    // rank of each element = number of smaller keys (keys are unique)
     for (int i0 = 0; i0 < n; i0 += NT) {
         const int i = i0 + tid;
         const unsigned long long ki = i < n ? sort_key(key, ent_tmp[b + i]) : 0ull;
@@ -362,6 +417,17 @@ extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, c
     if (R > 0 && capacity > 0) {
         k_pair_scatter<<<kFlatBlocks, 256, 0, st>>>(w.rec_cnt, R, w.rec_info, tile_ptr, w.cursor,
                                                     w.ent_tmp);
+        PS_LAUNCH_CHECK();
+        static int configured[64] = {0};   // dynamic shared memory attribute of k_sort_warp, per device
+        const int dyn = (int)(sizeof(unsigned long long) * kWarpSortCap * kSortWarps);
+        int dev = 0;
+        PS_CUDA_CHECK(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64 || !configured[dev]) {
+            PS_CUDA_CHECK(cudaFuncSetAttribute(k_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+            if (dev >= 0 && dev < 64) configured[dev] = 1;
+        }
+        k_sort_warp<<<(frame->n_tiles + kSortWarps - 1) / kSortWarps, kSortWarps * 32, dyn, st>>>(
+            tile_ptr, frame->n_tiles, w.ent_tmp, key, tile_ent);
         PS_LAUNCH_CHECK();
         k_sort<<<frame->n_tiles, 256, 0, st>>>(tile_ptr, w.ent_tmp, key, tile_ent);
         PS_LAUNCH_CHECK();

@@ -104,6 +104,7 @@ struct ProjArgs {
     float* key;
     int* status;
     double delta, z_near, z_far;
+    const ps_step_state* d_state;
     int single_radii;
     int tile_w, tile_h;
 };
@@ -169,7 +170,8 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
             vyc[i] = row3(R, i, vyw);
             nc[i] = row3(R, i, nw);
         }
-        const double r0 = rf[0], r1 = a.single_radii ? (double)rf[0] : (double)rf[1];
+        const double delta = a.d_state ? __ldg(&a.d_state->delta) : a.delta;
+    const double r0 = rf[0], r1 = a.single_radii ? (double)rf[0] : (double)rf[1];
         const double r2 = rf[2], r3 = a.single_radii ? (double)rf[2] : (double)rf[3];
 
         // record (rounded to f32)
@@ -182,8 +184,8 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
         out[12] = (float)r0; out[13] = (float)r1; out[14] = (float)r2; out[15] = (float)r3;
 
         // binning: widened quad, corners (+x,+y), (-x,+y), (-x,-y), (+x,-y)
-        const double exp_ = ad(r0, a.delta), exm = ad(r1, a.delta);
-        const double eyp = ad(r2, a.delta), eym = ad(r3, a.delta);
+        const double exp_ = ad(r0, delta), exm = ad(r1, delta);
+        const double eyp = ad(r2, delta), eym = ad(r3, delta);
         const double ax[4] = {exp_, -exm, -exm, exp_};
         const double ay[4] = {eyp, eyp, -eym, -eym};
         double C[4][3];
@@ -263,7 +265,8 @@ extern "C" ps_status ps_project_cull(const ps_planes* planes, const ps_frame* fr
     if (!planes->center || !planes->quat || !planes->radii) return PS_ERR_ARG;
     if (frame->n_views <= 0 || frame->max_K < 0) return PS_ERR_ARG;
     if (s->tile_w <= 0 || s->tile_h <= 0) return PS_ERR_ARG;
-    if (!(s->delta >= 0.0) || !(s->z_near > 0.f) || !(s->z_far > s->z_near)) return PS_ERR_ARG;
+    if (!(s->delta >= 0.0) && !s->d_state) return PS_ERR_ARG;
+    if (!(s->z_near > 0.f) || !(s->z_far > s->z_near)) return PS_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(rec) & 15) || (reinterpret_cast<uintptr_t>(rect) & 15))
         return PS_ERR_ARG;
     if (frame->max_K == 0 || frame->n_records == 0) return PS_OK;
@@ -273,6 +276,7 @@ extern "C" ps_status ps_project_cull(const ps_planes* planes, const ps_frame* fr
     a.views = frame->views;
     a.rec = rec; a.rect = reinterpret_cast<int4*>(rect); a.key = key; a.status = d_status;
     a.delta = s->delta; a.z_near = (double)s->z_near; a.z_far = (double)s->z_far;
+    a.d_state = s->d_state;
     a.single_radii = (s->flags & PS_SINGLE_RADII) ? 1 : 0;
     a.tile_w = s->tile_w; a.tile_h = s->tile_h;
     dim3 grid((frame->max_K + 127) / 128, frame->n_views);
@@ -285,6 +289,34 @@ extern "C" ps_status ps_project_cull(const ps_planes* planes, const ps_frame* fr
 // Adam.
 
 namespace {
+__global__ void k_step_advance(ps_step_state* st, const ps_step_state* sched, int n, int* iter)
+{
+    const int i = *iter;
+    *st = sched[i < n ? i : n - 1];
+    *iter = i + 1;
+}
+
+__global__ void k_adam_state(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                             float* __restrict__ v, long long n, float lr, float b1, float b2,
+                             float eps, const ps_step_state* __restrict__ st, float clamp_min,
+                             int do_clamp)
+{
+    const float bc1 = __ldg(&st->bc1), bc2 = __ldg(&st->bc2);
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) {
+        const float gi = g[i];
+        const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+        const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+        m[i] = mi;
+        v[i] = vi;
+        const float mh = mi / bc1, vh = vi / bc2;
+        float pi = p[i] - lr * mh / (sqrtf(vh) + eps);
+        if (do_clamp && pi < clamp_min) pi = clamp_min;
+        p[i] = pi;
+    }
+}
+
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
                        float bc1, float bc2, float clamp_min, int do_clamp)
@@ -319,6 +351,33 @@ extern "C" ps_status ps_adam_step(float* param, const float* grad, float* m, flo
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_adam<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
         param, grad, m, v, n, lr, b1, b2, eps, bc1, bc2, clamp_min, do_clamp);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
+
+extern "C" ps_status ps_step_advance(ps_step_state* d_state, const ps_step_state* d_sched,
+                                     int n_sched, int* d_iter, ps_stream stream)
+{
+    if (!d_state || !d_sched || !d_iter || n_sched < 1) return PS_ERR_ARG;
+    k_step_advance<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(d_state, d_sched, n_sched,
+                                                                        d_iter);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
+
+extern "C" ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v,
+                                        long long n, float lr, float b1, float b2, float eps,
+                                        const ps_step_state* d_state, float clamp_min,
+                                        ps_stream stream)
+{
+    if (n < 0 || !d_state) return PS_ERR_ARG;
+    if (n == 0) return PS_OK;
+    if (!param || !grad || !m || !v) return PS_ERR_ARG;
+    const int do_clamp = isnan(clamp_min) ? 0 : 1;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_adam_state<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        param, grad, m, v, n, lr, b1, b2, eps, d_state, clamp_min, do_clamp);
     PS_LAUNCH_CHECK();
     return PS_OK;
 }

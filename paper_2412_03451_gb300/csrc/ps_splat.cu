@@ -63,6 +63,7 @@ struct SplatArgs {
     int M;
     int n_items;              // strips = n_tiles * (tile pixels / 32)
     int* counter;             // work counter (zeroed before the launch)
+    const ps_step_state* d_state;   // if set, lambda and delta come from here
     // forward outputs
     float* depth;
     float* normal;
@@ -478,8 +479,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
             }
             // warp aggregation: for each distinct record among the active lanes, the
             // 16 gradient floats are summed over its lanes by a transpose-reduction
-            // (16 shuffles leave lane pair (2c, 2c+1) holding the total of float c)
-            // and added with one 16-lane atomic instruction
+            // and added with two 8-lane atomic instructions
             const unsigned actm = __ballot_sync(kFull, act);
             if (actm == 0) continue;
             const unsigned peers = __match_any_sync(kFull, id);
@@ -490,47 +490,41 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
                 const int gid = __shfl_sync(kFull, id, leader);
                 rem &= ~gmask;
                 const bool member = (gmask >> lane) & 1u;
-                float v[16];
+                float* dst = reinterpret_cast<float*>(a.g_rec + (size_t)gid * 4);
+                // two halves of 8 floats: 9 shuffles each leave lanes 4c..4c+3 holding
+                // the total of float c of the half
 #pragma unroll
-                for (int c = 0; c < 16; ++c) v[c] = member ? gr[c] : 0.f;
-                // round 0: 16 -> 8 values (partner lane ^ 16)
-                {
-                    const bool hi = lane & 16;
+                for (int h = 0; h < 2; ++h) {
+                    float v[8];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float send = hi ? v[c] : v[c + 8];
-                        const float keep = hi ? v[c + 8] : v[c];
-                        v[c] = keep + __shfl_xor_sync(kFull, send, 16);
+                    for (int c = 0; c < 8; ++c) v[c] = member ? gr[8 * h + c] : 0.f;
+                    {
+                        const bool hi = lane & 16;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float send = hi ? v[c] : v[c + 4];
+                            const float keep = hi ? v[c + 4] : v[c];
+                            v[c] = keep + __shfl_xor_sync(kFull, send, 16);
+                        }
                     }
-                }
-                {
-                    const bool hi = lane & 8;
+                    {
+                        const bool hi = lane & 8;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float send = hi ? v[c] : v[c + 4];
-                        const float keep = hi ? v[c + 4] : v[c];
-                        v[c] = keep + __shfl_xor_sync(kFull, send, 8);
+                        for (int c = 0; c < 2; ++c) {
+                            const float send = hi ? v[c] : v[c + 2];
+                            const float keep = hi ? v[c + 2] : v[c];
+                            v[c] = keep + __shfl_xor_sync(kFull, send, 8);
+                        }
                     }
-                }
-                {
-                    const bool hi = lane & 4;
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const float send = hi ? v[c] : v[c + 2];
-                        const float keep = hi ? v[c + 2] : v[c];
-                        v[c] = keep + __shfl_xor_sync(kFull, send, 4);
+                    {
+                        const bool hi = lane & 4;
+                        const float send = hi ? v[0] : v[1];
+                        const float keep = hi ? v[1] : v[0];
+                        v[0] = keep + __shfl_xor_sync(kFull, send, 4);
                     }
-                }
-                {
-                    const bool hi = lane & 2;
-                    const float send = hi ? v[0] : v[1];
-                    const float keep = hi ? v[1] : v[0];
-                    v[0] = keep + __shfl_xor_sync(kFull, send, 2);
-                }
-                v[0] += __shfl_xor_sync(kFull, v[0], 1);
-                if ((lane & 1) == 0) {
-                    float* dst = reinterpret_cast<float*>(a.g_rec + (size_t)gid * 4);
-                    atomicAdd(dst + ((lane >> 1) & 15), v[0]);
+                    v[0] += __shfl_xor_sync(kFull, v[0], 2);
+                    v[0] += __shfl_xor_sync(kFull, v[0], 1);
+                    if ((lane & 3) == 0) atomicAdd(dst + 8 * h + ((lane >> 2) & 7), v[0]);
                 }
             }
         }
@@ -538,9 +532,20 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
 }
 
 // Persistent warps: each takes strips from the work counter until none is left.
-template <int TW, int TH, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_splat(SplatArgs a)
+// lambda and the quick-reject margin from the device state (graph replay)
+__device__ __forceinline__ void load_state(SplatArgs& a)
 {
+    if (a.d_state && !a.c.hard) {
+        a.c.lam5 = 5.f * __ldg(&a.d_state->lambda);
+        a.c.reject = (float)(__ldg(&a.d_state->delta) * 1.02 + 1e-6);
+    }
+}
+
+template <int TW, int TH, int MODE>
+__global__ void __launch_bounds__(kWarps * 32, 5) k_splat(SplatArgs a_in)
+{
+    SplatArgs a = a_in;
+    load_state(a);
     __shared__ WarpStage stage[kWarps];
     extern __shared__ int2 dyn_stk[];       // backward: [kWarps][M][32]
     const int w = threadIdx.x >> 5;
@@ -566,8 +571,10 @@ struct CountSmem {
 };
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) k_count_pairs(SplatArgs a, unsigned long long* counts)
+__global__ void __launch_bounds__(TW * TH) k_count_pairs(SplatArgs a_in, unsigned long long* counts)
 {
+    SplatArgs a = a_in;
+    load_state(a);
     constexpr int NT = TW * TH;
     __shared__ CountSmem<NT> sm;
     __shared__ unsigned long long red[3];
@@ -849,8 +856,10 @@ ps_status check_common(const ps_frame* f, const ps_settings* s, const float* rec
     if (capacity < 0 || (capacity > 0 && !tile_ent)) return PS_ERR_ARG;
     if (f->n_tiles <= 0 || f->n_views <= 0) return PS_ERR_ARG;
     if (s->M < 1 || s->M > PS_MAX_M) return PS_ERR_ARG;
-    if (!(s->lambda > 0.f) || !(s->w_min > 0.f) || !(s->w_min < 1.f)) return PS_ERR_ARG;
-    if (!(s->z_near > 0.f) || !(s->z_far > s->z_near) || !(s->delta >= 0.0)) return PS_ERR_ARG;
+    if (!s->d_state && !(s->lambda > 0.f)) return PS_ERR_ARG;
+    if (!(s->w_min > 0.f) || !(s->w_min < 1.f)) return PS_ERR_ARG;
+    if (!(s->z_near > 0.f) || !(s->z_far > s->z_near)) return PS_ERR_ARG;
+    if (!s->d_state && !(s->delta >= 0.0)) return PS_ERR_ARG;
     const int tw = s->tile_w, th = s->tile_h;
     if (!((tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8))) return PS_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(rec) & 15) return PS_ERR_ARG;
@@ -912,7 +921,7 @@ extern "C" ps_status ps_splat_fwd(const ps_frame* f, const ps_settings* s, const
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
     a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
-    a.c = make_const(s); a.M = s->M;
+    a.c = make_const(s); a.M = s->M; a.d_state = s->d_state;
     a.counter = static_cast<int*>(ws);
     a.depth = depth; a.normal = normal; a.alpha = alpha; a.status = d_status;
     if (dispatch<kFwd>(a, s, f->n_tiles, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
@@ -946,7 +955,7 @@ extern "C" ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* f, co
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
     a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
-    a.c = make_const(s); a.M = s->M;
+    a.c = make_const(s); a.M = s->M; a.d_state = s->d_state;
     a.dLdD = dLdD; a.dLdN = dLdN; a.g_rec = reinterpret_cast<float4*>(ws); a.status = d_status;
     a.counter = reinterpret_cast<int*>(static_cast<char*>(ws) + grec_bytes);
     if (dispatch<kBwd>(a, s, f->n_tiles, st) != cudaSuccess) return PS_ERR_CUDA;
@@ -983,7 +992,7 @@ extern "C" ps_status ps_splat_fused(const ps_planes* planes, const ps_frame* f,
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
     a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
-    a.c = make_const(s); a.M = s->M;
+    a.c = make_const(s); a.M = s->M; a.d_state = s->d_state;
     a.depth = depth; a.normal = normal; a.alpha = nullptr;
     a.g_rec = reinterpret_cast<float4*>(ws); a.status = d_status;
     a.counter = reinterpret_cast<int*>(static_cast<char*>(ws) + grec_bytes);
@@ -1038,7 +1047,7 @@ extern "C" ps_status ps_count_pairs(const ps_frame* f, const ps_settings* s, con
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
     a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
-    a.c = make_const(s); a.M = s->M;
+    a.c = make_const(s); a.M = s->M; a.d_state = s->d_state;
     unsigned long long* c = reinterpret_cast<unsigned long long*>(d_counts);
     cudaError_t err;
     if (s->tile_w == 16) err = launch_count<16, 16>(a, f->n_tiles, c, st);

@@ -120,11 +120,11 @@ class Renderer:
     def select(self, i: int):
         self.frame.views = self._batches[i].data_ptr()
 
-    def make_settings(self, lam, flags=None):
+    def make_settings(self, lam, flags=None, d_state=None):
         fl = self.flags if flags is None else flags
         delta = 0.0 if (fl & B.PS_HARD) else B.filter_margin(float(np.float32(lam)))
         self.settings = B.make_settings(lam, delta, M=self.M, tile_w=self.tile[0],
-                                        tile_h=self.tile[1], flags=fl)
+                                        tile_h=self.tile[1], flags=fl, d_state=d_state)
         return self.settings
 
     def planes_struct(self, flat: torch.Tensor) -> B.PsPlanes:
@@ -135,8 +135,8 @@ class Renderer:
         return p
 
     # -- the path ----------------------------------------------------------------
-    def project_bin(self, flat: torch.Tensor, lam: float, flags=None):
-        s = self.make_settings(lam, flags)
+    def project_bin(self, flat: torch.Tensor, lam: float, flags=None, d_state=None):
+        s = self.make_settings(lam, flags, d_state)
         pl = self.planes_struct(flat)
         B.ps_project_cull(pl, self.frame, s, self.rec, self.rect, self.key, self.status)
         B.ps_bin_tiles(self.frame, s, self.rect, self.key, self.tile_ptr, self.tile_ent,
@@ -231,6 +231,58 @@ class Fitter:
         self.v = torch.zeros_like(flat)
         self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
         self.ite = 0
+
+    # -- captured CUDA graphs ------------------------------------------------------
+    def enable_graphs(self, n_iters: int, batches, gt_slices):
+        """Captures one CUDA graph per camera batch of a full optimisation step
+        (schedule advance, projection, binning, fused splat/loss/backward, Adam),
+        with lambda, the binning margin and Adam's bias corrections read from a
+        device-side per-iteration schedule, so that replaying graph s % n_batches
+        at iteration s reproduces the eager step.  Capacity must already suffice
+        (checked after replays through the status word)."""
+        dev = self.flat.device
+        sched = B.step_schedule(n_iters)
+        self.d_sched = torch.frombuffer(bytearray(sched), dtype=torch.uint8).to(dev)
+        self.n_sched = n_iters
+        self.d_state = torch.zeros(32, dtype=torch.uint8, device=dev)
+        self.d_iter = torch.tensor([self.ite], dtype=torch.int32, device=dev)
+        self.graphs = []
+        r = self.r
+        stream = torch.cuda.Stream(device=dev)
+        stream.wait_stream(torch.cuda.current_stream())
+        # warm the library's per-device launch caches outside capture
+        with torch.cuda.stream(stream):
+            r.select(batches[0])
+            saved = (self.flat.clone(), self.m.clone(), self.v.clone(), int(self.d_iter.item()))
+            self._graph_body(*gt_slices[0])
+            torch.cuda.synchronize()
+            self.flat.copy_(saved[0]); self.m.copy_(saved[1]); self.v.copy_(saved[2])
+            self.d_iter.fill_(saved[3])
+        for b, (gd, gn) in zip(batches, gt_slices):
+            r.select(b)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                self._graph_body(gd, gn)
+            self.graphs.append(g)
+        torch.cuda.synchronize()
+
+    def _graph_body(self, gt_depth, gt_normal):
+        r = self.r
+        P = r.P
+        B.ps_step_advance(self.d_state, self.d_sched, self.n_sched, self.d_iter)
+        r.project_bin(self.flat, 1.0, d_state=self.d_state)
+        self.grad.zero_()
+        r.fused(self.flat, self.grad, gt_depth, gt_normal)
+        B.ps_adam_step_state(self.flat[:7 * P], self.grad[:7 * P], self.m[:7 * P], self.v[:7 * P],
+                             self.lr, self.b1, self.b2, self.eps, self.d_state)
+        B.ps_adam_step_state(self.flat[7 * P:], self.grad[7 * P:], self.m[7 * P:], self.v[7 * P:],
+                             self.lr, self.b1, self.b2, self.eps, self.d_state, clamp_min=R_MIN)
+
+    def replay(self, batch_index: int):
+        """One optimisation step by graph replay (iteration counter on the device)."""
+        self.graphs[batch_index].replay()
+        self.ite += 1
+        return self.r.view_sums
 
     def step(self, gt_depth, gt_normal, lam=None, marks=None):
         """One iteration.  If marks is a list, CUDA events are recorded on the

@@ -52,7 +52,8 @@ def test_binding_exports_match_header(lib):
 def test_struct_sizes_match_header(lib):
     from paper_2412_03451_gb300 import binding as B
     assert ctypes.sizeof(B.PsView) == 128
-    assert ctypes.sizeof(B.PsSettings) == 56
+    assert ctypes.sizeof(B.PsSettings) == 64
+    assert ctypes.sizeof(B.PsStepState) == 24
     assert ctypes.sizeof(B.PsFrame) == 32
 
 

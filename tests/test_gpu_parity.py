@@ -369,3 +369,50 @@ def test_fused_gradient_against_oracle():
     # unmasked upstream: a few ill-conditioned pixels may move a plane's gradient
     nbad = sum(v[0] for v in res.values())
     assert nbad <= 0.05 * 3 * K, res
+
+
+# ---------------------------------------------------------------------------
+# CUDA-graph replay of a whole optimisation step.
+
+def test_graph_replay_matches_eager_step():
+    import torch
+    from paper_2412_03451_gb300 import binding as B
+    from paper_2412_03451_gb300 import splat as SP
+    room, init = tiny_init()
+    cams = room.cams
+    V, H, W = cams.V, cams.H, cams.W
+    D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, cams.w2c, cams.intr, H, W)
+    gd = torch.from_numpy(D.astype(np.float32).reshape(-1)).cuda()
+    gn = torch.from_numpy(N.astype(np.float32).reshape(-1, 3)).cuda()
+    half = V // 2
+
+    def make():
+        r = SP.Renderer([H] * half, [W] * half, [0] * half, [0, init.K], capacity=1 << 15)
+        r.preplan([cams.w2c[:half], cams.w2c[half:]], [cams.intr[:half], cams.intr[half:]])
+        flat = SP.planes_to_flat(init.center, init.quat, init.radii, "cuda")
+        return r, SP.Fitter(r, flat)
+
+    slices = [(gd[:half * H * W], gn[:half * H * W]), (gd[half * H * W:], gn[half * H * W:])]
+    # eager: three steps
+    r1, f1 = make()
+    eager = []
+    for s in range(3):
+        r1.select(s % 2)
+        vs = f1.step(*slices[s % 2])
+        eager.append((vs.clone(), f1.grad.clone(), f1.flat.clone()))
+    # graphs: same three steps by replay
+    r2, f2 = make()
+    f2.enable_graphs(50, [0, 1], slices)
+    for s in range(3):
+        vs = f2.replay(s % 2)
+        torch.cuda.synchronize()
+        ve, ge, pe = eager[s]
+        assert torch.allclose(vs, ve, rtol=1e-6), s
+        assert (torch.linalg.norm(f2.grad - ge) <= 1e-5 * torch.linalg.norm(ge) + 1e-6), s
+        if s == 0:
+            # first step from the same state: Adam moves each parameter by at most lr
+            assert (f2.flat - pe).abs().max() <= 2.1e-3
+    st = B.PsStepState.from_buffer_copy(bytes(f2.d_state.cpu().numpy()[:24]))
+    assert st.step == 3 and st.lambda_ == np.float32(B.lambda_schedule(2))
+    assert st.delta == B.filter_margin(float(np.float32(B.lambda_schedule(2))))
+    assert int(f2.d_iter.item()) == 3 and int(r2.status.item()) == 0
