@@ -110,7 +110,11 @@ typedef struct ps_view {
     int K;                 /* planes in the view's scene */
     long long pix_off;     /* first pixel of this view in per-pixel buffers */
     int scene;             /* scene index */
-    int reserved[5];
+    int reserved;
+    long long gt_off;      /* first pixel of this view in the supervision buffers (gt_depth,
+                              gt_normal); ps_plan_views sets it to pix_off, callers may point a
+                              view at any image of a larger resident array */
+    int reserved2[2];
 } ps_view;
 
 /* A batch of views: totals (host) and the descriptor array (device). */

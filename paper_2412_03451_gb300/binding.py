@@ -49,7 +49,8 @@ class PsView(ctypes.Structure):
                 ("W", ctypes.c_int), ("tiles_x", ctypes.c_int), ("tiles_y", ctypes.c_int),
                 ("tile_off", ctypes.c_int), ("rec_off", ctypes.c_int), ("plane_off", ctypes.c_int),
                 ("K", ctypes.c_int), ("pix_off", ctypes.c_longlong), ("scene", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("reserved", ctypes.c_int), ("gt_off", ctypes.c_longlong),
+                ("reserved2", ctypes.c_int * 2)]
 
 
 class PsFrame(ctypes.Structure):
@@ -133,8 +134,9 @@ def _stream(stream):
 # ---------------------------------------------------------------------------
 # Host planning.
 
-def ps_plan_views(H, W, scene_of_view, plane_ptr, w2c, intr, tile_w, tile_h):
-    """Plans a batch of views.  Returns (PsView array (host), PsFrame with views=NULL)."""
+def ps_plan_views(H, W, scene_of_view, plane_ptr, w2c, intr, tile_w, tile_h, gt_off=None):
+    """Plans a batch of views.  Returns (PsView array (host), PsFrame with views=NULL).
+    gt_off (optional, per view) points each view at its supervision pixels."""
     lib = load()
     V = len(H)
     Ha = np.ascontiguousarray(H, dtype=np.int32)
@@ -149,6 +151,9 @@ def ps_plan_views(H, W, scene_of_view, plane_ptr, w2c, intr, tile_w, tile_h):
                              pp.ctypes.data, w2.ctypes.data, it.ctypes.data, int(tile_w),
                              int(tile_h), ctypes.byref(views), ctypes.byref(frame))
     _check(code, "ps_plan_views")
+    if gt_off is not None:
+        for v in range(V):
+            views[v].gt_off = int(gt_off[v])
     return views, frame
 
 

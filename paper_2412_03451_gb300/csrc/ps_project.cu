@@ -61,6 +61,7 @@ extern "C" ps_status ps_plan_views(int n_views, const int* H, const int* W, cons
         o.plane_off = plane_ptr[s];
         o.K = plane_ptr[s + 1] - plane_ptr[s];
         o.pix_off = pix;
+        o.gt_off = pix;
         o.scene = s;
         tiles += (long long)o.tiles_x * o.tiles_y;
         recs += o.K;

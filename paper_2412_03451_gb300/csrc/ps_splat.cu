@@ -305,6 +305,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
     const float dx = __fdiv_rn((float)px + 0.5f - cx, fx);
     const float dy = __fdiv_rn((float)py + 0.5f - cy, fy);
     const long long pix = __ldg(&vw->pix_off) + (long long)py * W + px;
+    const long long gpix = __ldg(&vw->gt_off) + (long long)py * W + px;   // supervision pixel
     WarpRegion g;
     {
         constexpr int WX = TW < 32 ? TW : 32;
@@ -332,10 +333,10 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
     float Dg = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
     if constexpr (MODE == kFused) {
         if (inside) {
-            Dg = __ldg(&a.gt_depth[pix]);
-            G0 = __ldg(&a.gt_normal[3 * pix]);
-            G1 = __ldg(&a.gt_normal[3 * pix + 1]);
-            G2 = __ldg(&a.gt_normal[3 * pix + 2]);
+            Dg = __ldg(&a.gt_depth[gpix]);
+            G0 = __ldg(&a.gt_normal[3 * gpix]);
+            G1 = __ldg(&a.gt_normal[3 * gpix + 1]);
+            G2 = __ldg(&a.gt_normal[3 * gpix + 2]);
         }
     }
     if constexpr (MODE == kBwd) {
@@ -757,11 +758,13 @@ __global__ void __launch_bounds__(256) k_loss(LossArgs a)
     const ps_view* vw = a.views + v;
     const long long HW = (long long)__ldg(&vw->H) * __ldg(&vw->W);
     const long long off = __ldg(&vw->pix_off);
+    const long long goff = __ldg(&vw->gt_off);
     float sc = 0.f, sl = 0.f, sd = 0.f, cnt = 0.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < HW;
          i += (long long)gridDim.x * blockDim.x) {
         const long long p = off + i;
-        const float Dg = __ldg(&a.gt_depth[p]);
+        const long long q = goff + i;
+        const float Dg = __ldg(&a.gt_depth[q]);
         if (!(Dg > 0.f)) {
             a.dLdD[p] = 0.f;
             a.dLdN[3 * p + 0] = 0.f; a.dLdN[3 * p + 1] = 0.f; a.dLdN[3 * p + 2] = 0.f;
@@ -770,8 +773,8 @@ __global__ void __launch_bounds__(256) k_loss(LossArgs a)
         const float D = __ldg(&a.depth[p]);
         const float N0 = __ldg(&a.normal[3 * p]), N1 = __ldg(&a.normal[3 * p + 1]),
                     N2 = __ldg(&a.normal[3 * p + 2]);
-        const float G0 = __ldg(&a.gt_normal[3 * p]), G1 = __ldg(&a.gt_normal[3 * p + 1]),
-                    G2 = __ldg(&a.gt_normal[3 * p + 2]);
+        const float G0 = __ldg(&a.gt_normal[3 * q]), G1 = __ldg(&a.gt_normal[3 * q + 1]),
+                    G2 = __ldg(&a.gt_normal[3 * q + 2]);
         const float c = 1.f - (N0 * G0 + N1 * G1 + N2 * G2);
         const float e0 = N0 - G0, e1 = N1 - G1, e2 = N2 - G2;
         const float dd = D - Dg;

@@ -413,6 +413,34 @@ def surface_init(room: Room, n: int, seed: int, radius: float = 0.2) -> Planes:
     return Planes(centers.astype(np.float32), quat.astype(np.float32), radii.astype(np.float32))
 
 
+def surface_init_nn(room: Room, n: int, seed: int, scale: float = 0.5) -> Planes:
+    """Like surface_init, but every radius is scale x the distance to the nearest
+    other centre (Sec. 3.1: initial radii 0.5 Dist(pi)), so coverage follows the
+    plane count."""
+    p = surface_init(room, n, seed)
+    from scipy.spatial import cKDTree
+    d, _ = cKDTree(p.center.astype(np.float64)).query(p.center.astype(np.float64), k=2)
+    r = np.clip(scale * d[:, 1], 0.02, 2.0)
+    p.radii[:] = r[:, None].astype(np.float32)
+    return p
+
+
+def batch_rooms(n_rooms: int, seed0: int = 1000, planes=(200, 3000), views=(16, 96),
+                sizes=((240, 320), (360, 480), (480, 640)), n_rect: int = 2000) -> list:
+    """n_rooms independent rooms as large_room, each with its own plane count
+    K ~ U{planes}, view count V ~ U{views} and resolution drawn from sizes
+    (fx = fy = 500 W / 640).  Returns [(Room, K)]."""
+    rng = np.random.default_rng(seed0 - 1)
+    out = []
+    for s in range(n_rooms):
+        K = int(rng.integers(planes[0], planes[1] + 1))
+        V = int(rng.integers(views[0], views[1] + 1))
+        H, W = sizes[int(rng.integers(0, len(sizes)))]
+        room = large_room(seed0 + s, n_rect=n_rect, n_views=V, H=H, W=W, f=500.0 * W / 640.0)
+        out.append((room, K))
+    return out
+
+
 def random_planes_in_view(seed: int, K: int, depth_range=(1.0, 4.0), half=(0.1, 0.6),
                           fov=0.6, tilt_deg=40.0) -> Planes:
     """K random rectangles in front of an identity camera (for small tests):

@@ -105,14 +105,17 @@ class Renderer:
         self.views_dev.copy_(torch.from_numpy(raw))
         self.frame.views = self.views_dev.data_ptr()
 
-    def preplan(self, w2c_batches, intr_batches):
+    def preplan(self, w2c_batches, intr_batches, gt_off_batches=None):
         """Plans several camera batches of this renderer's shape once and keeps
         their descriptors on the device; select(i) then switches batches with no
-        host-to-device traffic (and so can run inside a captured graph)."""
+        host-to-device traffic (and so can run inside a captured graph).
+        gt_off_batches (optional) gives every view of every batch the offset of its
+        supervision image in resident ground-truth arrays."""
         raws = []
-        for w2c, intr in zip(w2c_batches, intr_batches):
+        for i, (w2c, intr) in enumerate(zip(w2c_batches, intr_batches)):
+            go = None if gt_off_batches is None else gt_off_batches[i]
             vh, _ = B.ps_plan_views(self.H, self.W, self.scene_of_view, self.plane_ptr, w2c, intr,
-                                    *self.tile)
+                                    *self.tile, gt_off=go)
             raws.append(np.frombuffer(bytes(vh), dtype=np.uint8))
         self._batches = torch.from_numpy(np.stack(raws)).to(self.device)
         self.select(0)
@@ -174,7 +177,7 @@ class Renderer:
         return self.view_sums
 
     def fused(self, flat: torch.Tensor, grad_flat: torch.Tensor, gt_depth, gt_normal,
-              write_maps: bool = False):
+              write_maps: bool = False, view_sums=None):
         """Forward + Eq. 14 loss + backward in one pass (after project_bin).
         Accumulates the loss gradient into grad_flat; fills view_sums; writes
         depth/normal/dL maps only if write_maps."""
@@ -184,9 +187,10 @@ class Renderer:
         B.ps_splat_fused(pl, self.frame, self.settings, self.rec, self.key, self.tile_ptr,
                          self.tile_ent, self.capacity, gt_depth, gt_normal,
                          self.depth if m else None, self.normal if m else None,
-                         self.dLdD if m else None, self.dLdN if m else None, self.view_sums,
+                         self.dLdD if m else None, self.dLdN if m else None,
+                         self.view_sums if view_sums is None else view_sums,
                          gc, gq, gr, self.bwd_ws, self.status)
-        return self.view_sums
+        return self.view_sums if view_sums is None else view_sums
 
     def backward(self, flat: torch.Tensor, grad_flat: torch.Tensor, dLdD=None, dLdN=None):
         """Accumulates d(sum dLdD*D + dLdN.N)/dparams into grad_flat (same layout)."""
@@ -248,31 +252,33 @@ class Fitter:
         self.d_iter = torch.tensor([self.ite], dtype=torch.int32, device=dev)
         self.graphs = []
         r = self.r
+        # each graph writes its own loss sums, so a host check after a rotation sees every batch
+        self.graph_sums = [torch.zeros_like(r.view_sums) for _ in batches]
         stream = torch.cuda.Stream(device=dev)
         stream.wait_stream(torch.cuda.current_stream())
         # warm the library's per-device launch caches outside capture
         with torch.cuda.stream(stream):
             r.select(batches[0])
             saved = (self.flat.clone(), self.m.clone(), self.v.clone(), int(self.d_iter.item()))
-            self._graph_body(*gt_slices[0])
+            self._graph_body(*gt_slices[0], self.graph_sums[0])
             torch.cuda.synchronize()
             self.flat.copy_(saved[0]); self.m.copy_(saved[1]); self.v.copy_(saved[2])
             self.d_iter.fill_(saved[3])
-        for b, (gd, gn) in zip(batches, gt_slices):
+        for i, (b, (gd, gn)) in enumerate(zip(batches, gt_slices)):
             r.select(b)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
-                self._graph_body(gd, gn)
+                self._graph_body(gd, gn, self.graph_sums[i])
             self.graphs.append(g)
         torch.cuda.synchronize()
 
-    def _graph_body(self, gt_depth, gt_normal):
+    def _graph_body(self, gt_depth, gt_normal, view_sums):
         r = self.r
         P = r.P
         B.ps_step_advance(self.d_state, self.d_sched, self.n_sched, self.d_iter)
         r.project_bin(self.flat, 1.0, d_state=self.d_state)
         self.grad.zero_()
-        r.fused(self.flat, self.grad, gt_depth, gt_normal)
+        r.fused(self.flat, self.grad, gt_depth, gt_normal, view_sums=view_sums)
         B.ps_adam_step_state(self.flat[:7 * P], self.grad[:7 * P], self.m[:7 * P], self.v[:7 * P],
                              self.lr, self.b1, self.b2, self.eps, self.d_state)
         B.ps_adam_step_state(self.flat[7 * P:], self.grad[7 * P:], self.m[7 * P:], self.v[7 * P:],
@@ -282,7 +288,7 @@ class Fitter:
         """One optimisation step by graph replay (iteration counter on the device)."""
         self.graphs[batch_index].replay()
         self.ite += 1
-        return self.r.view_sums
+        return self.graph_sums[batch_index]
 
     def step(self, gt_depth, gt_normal, lam=None, marks=None):
         """One iteration.  If marks is a list, CUDA events are recorded on the

@@ -416,3 +416,40 @@ def test_graph_replay_matches_eager_step():
     assert st.step == 3 and st.lambda_ == np.float32(B.lambda_schedule(2))
     assert st.delta == B.filter_margin(float(np.float32(B.lambda_schedule(2))))
     assert int(f2.d_iter.item()) == 3 and int(r2.status.item()) == 0
+
+
+# ---------------------------------------------------------------------------
+# Multi-scene frames: scenes of uneven size in one launch behave as alone.
+
+def test_multi_scene_frame_equals_single_scene_runs():
+    import torch
+    from paper_2412_03451_gb300 import batch as BT
+    rooms = S.batch_rooms(3, seed0=1500, planes=(150, 600), views=(8, 20), n_rect=300)
+    inits = [S.surface_init_nn(room, K, seed=1600 + i) for i, (room, K) in enumerate(rooms)]
+    ss = BT.SceneSet([room for room, _ in rooms], inits, views_per_step=4)
+    lam = 20.0
+    res = {}
+    for scenes in ([0, 1, 2], [0], [1], [2]):
+        r = ss.renderer(scenes)
+        flat = ss.flat_for(scenes)
+        r.select(1)
+        r.ensure_capacity(flat, lam)
+        r.project_bin(flat, lam)
+        g = torch.zeros_like(flat)
+        vs = r.fused(flat, g, ss.gt_depth, ss.gt_normal).clone()
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        res[tuple(scenes)] = (g.cpu().numpy(), vs.cpu().numpy(), [ss.K[s] for s in scenes])
+    g_all, vs_all, K_all = res[(0, 1, 2)]
+    P = sum(K_all)
+    off = 0
+    for s in range(3):
+        g1, vs1, (K,) = res[(s,)]
+        # the flat layouts differ: [c | q | r] over the batch vs over the scene
+        for grp, width in ((0, 3), (3, 4), (7, 4)):
+            a = g_all[grp * P + off * width: grp * P + (off + K) * width]
+            b = g1[grp * K: grp * K + K * width]
+            assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b) + 1e-6, (s, grp)
+        assert np.allclose(vs_all[4 * s:4 * s + 4], vs1, rtol=1e-6)
+        off += K
+    report("multi_scene", K=K_all)
