@@ -58,9 +58,10 @@ SM_COUNT, FP32_LANES = 152, 128
 LAUNCHES_FUSED = 1 + 1 + 11 + 2 + 2
 LAUNCHES_SPLIT = 1 + 11 + 4 + 2
 
-# DRAM traffic per launch of ps_splat_bwd's main kernel, from the ncu capture
-# summarised in profiles/ (valid only for the kernel source it was taken on).
-TRAFFIC = {"splat_bwd": None, "splat_fwd": None, "src_sha": None}
+# DRAM bytes (read + write) per launch of the fused splat kernel from the ncu
+# capture summarised in profiles/k_splat_fused_room640_8x8.md; reported only while
+# the kernel source is the one it was taken on.
+TRAFFIC = {"splat_fused": 45941504 + 372480, "src_sha": "f3fdc222c08c2bea"}
 
 
 def src_hash() -> str:
@@ -74,7 +75,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", default="16x16", choices=["16x16", "8x8", "32x8"])
+    ap.add_argument("--tile", default="auto", choices=["auto", "16x16", "8x8", "32x8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ttd", type=int, default=0,
@@ -84,13 +85,15 @@ def parse():
     ap.add_argument("--batched", type=int, default=32,
                     help="rooms in the batched-vs-plain time-to-2cm comparison (0: skip)")
     ap.add_argument("--batched-iters", type=int, default=5000)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="for ncu: set up, warm up 3 steps, run one step inside a profiler range, exit")
     return ap.parse_args()
 
 
 def workload_config(args, world):
     return {"workload": "synthetic room 8x10x3 m, %d GT rectangles, %d planes, %d of %d views "
                         "per step at %dx%d" % (N_GT, N_INIT, VIEWS_PER_STEP, N_VIEWS, W, H),
-            "views_per_step": VIEWS_PER_STEP, "image": [H, W], "planes": N_INIT, "tile": args.tile,
+            "views_per_step": VIEWS_PER_STEP, "image": [H, W], "planes": N_INIT,
             "M": 30, "l2": "flushed between steps (256 MB write, outside the timed events)",
             "start_iteration": args.start_ite, "replicas": world,
             "seed": "scene 1000 + rank, init 2000 + rank"}
@@ -242,6 +245,27 @@ def time_steps(wl, first, K, flush, counts_out=None):
     return per_step, stages
 
 
+def autotune_tile(rank, device):
+    """Picks the tile shape for this workload by timing each candidate on its
+    first camera batch (outside every timed region)."""
+    from paper_2412_03451_gb300 import autotune
+    from paper_2412_03451_gb300 import splat as SP
+    wl = Workload(rank, (16, 16), device)
+    gd, gn = wl.gt_slice(0)
+    cams = wl.room.cams
+
+    def make(tile):
+        r = SP.Renderer([H] * VIEWS_PER_STEP, [W] * VIEWS_PER_STEP, [0] * VIEWS_PER_STEP,
+                        [0, N_INIT], tile=tile, device=device)
+        r.set_cameras(cams.w2c[:VIEWS_PER_STEP], cams.intr[:VIEWS_PER_STEP])
+        return r
+
+    key = autotune.key_for([(H, W)], VIEWS_PER_STEP, N_INIT)
+    tile, times = autotune.pick_tile(make, wl.flat, gd, gn, wl.B.lambda_schedule(0), key)
+    del wl
+    return tile, times
+
+
 def time_replays(wl, first, K, flush):
     """Times K graph replays (one optimisation step each) from step index `first`."""
     torch = wl.torch
@@ -266,7 +290,11 @@ def run_ours(args, rank, world, local_rank):
     __graft_entry__.build()
     device = "cuda:%d" % local_rank
     torch.cuda.set_device(local_rank)
-    tile = tuple(int(x) for x in args.tile.split("x"))
+    tuning = None
+    if args.tile == "auto":
+        tile, tuning = autotune_tile(rank, device)
+    else:
+        tile = tuple(int(x) for x in args.tile.split("x"))
     wl = Workload(rank, tile, device)
     wl.reset(args.start_ite)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
@@ -355,6 +383,9 @@ def run_ours(args, rank, world, local_rank):
                                "tested_pairs": tested // K, "ms": round(dom_ms, 4)}}
 
     cfg = workload_config(args, world)
+    cfg["tile"] = "%dx%d" % tile
+    if tuning:
+        cfg["autotune_ms"] = {k: round(v, 4) for k, v in tuning.items()}
     cfg["launch"] = "captured CUDA graph per step" if use_graphs else "eager launches"
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -399,6 +430,18 @@ def run_batched(args, rank, device):
     rooms = S.batch_rooms(n, seed0=3000 + 100 * rank)
     inits = [S.surface_init_nn(room, K, 4000 + 100 * rank + i) for i, (room, K) in enumerate(rooms)]
     ss = BT.SceneSet([r for r, _ in rooms], inits, device=device)
+    from paper_2412_03451_gb300 import autotune
+
+    def make(tile):
+        ss.tile = tile
+        r = ss.renderer()
+        r.select(0)
+        return r
+
+    key = autotune.key_for([(rm.cams.H, rm.cams.W) for rm in ss.rooms], ss.vps * n, sum(ss.K))
+    tile, tuning = autotune.pick_tile(make, ss.flat_init(), ss.gt_depth, ss.gt_normal,
+                                      1.0 * 20.0 / 2.718281828459045, key)
+    ss.tile = tile
     bat = BT.fit_until(ss, list(range(n)), max_iters=args.batched_iters)
     plain = [BT.fit_until(ss, [s], max_iters=args.batched_iters) for s in range(n)]
     t_bat = bat["gpu_ms"] / 1e3
@@ -411,6 +454,7 @@ def run_batched(args, rank, device):
             "reached_plain": sum(p["done_at"][0] is not None for p in plain),
             "iteration_cap": args.batched_iters,
             "batched": "all rooms in one launch per kernel per step; rooms leave the batch when done",
+            "tile": "%dx%d" % tile, "autotune_ms": {k: round(v, 4) for k, v in tuning.items()},
             "init": "random surface points, radii 0.5 x nearest-neighbour distance, random orientation"}
 
 
@@ -575,8 +619,33 @@ def run_reference(args):
     }
 
 
+def profile_case(args):
+    """One eager optimisation step of the workload inside cudaProfilerStart/Stop
+    (for `ncu --profile-from-start off`), after 3 warm-up steps."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    tile = (16, 16) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
+    wl = Workload(0, tile, "cuda:0")
+    wl.reset(args.start_ite)
+    for i in range(3):
+        wl.grow_if_needed(i)
+        wl.step(i)
+    wl.grow_if_needed(3)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    wl.step(3)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    status = int(wl.r.status.item())
+    print(json.dumps({"profile_case": "step 3", "tile": "%dx%d" % tile, "status": status}))
+    return 0 if status == 0 else 1
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
