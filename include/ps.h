@@ -297,6 +297,18 @@ ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v
                              float lr, float b1, float b2, float eps,
                              const ps_step_state* d_state, float clamp_min, ps_stream stream);
 
+/* BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor memory)
+   for the seed-proposal network (not part of the paper's renderer):
+   C[M, N] = A[M, K] . B[N, K]^T (+ bias[N]) (then ReLU if relu).
+   A, B: device bf16, row-major with K contiguous, 16-byte aligned; K must be a
+   multiple of 64 (zero-pad).  C32: device fp32 [M, ldc] or NULL; C16: device
+   bf16 [M, ldc] or NULL (at least one); with accumulate, C32 += result.
+   bias: device fp32 [N] or NULL.  d_err: device int set to 1 if a bounded wait
+   for the tensor cores timed out (the tile is then not written). */
+ps_status ps_gemm_bf16(const void* A, const void* B, const float* bias, float* C32, void* C16,
+                       int M, int N, int K, int ldc, int relu, int accumulate, int* d_err,
+                       ps_stream stream);
+
 /* Human-readable name of a status code. */
 const char* ps_status_string(ps_status status);
 

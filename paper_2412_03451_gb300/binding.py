@@ -25,8 +25,8 @@ PS_MAX_M = 64
 EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin_tiles",
            "ps_fwd_workspace_bytes", "ps_splat_fwd", "ps_loss", "ps_bwd_workspace_bytes", "ps_splat_bwd",
            "ps_splat_fused", "ps_adam_step",
-           "ps_count_pairs", "ps_step_advance", "ps_adam_step_state", "ps_status_string",
-           "ps_version")
+           "ps_count_pairs", "ps_step_advance", "ps_adam_step_state", "ps_gemm_bf16",
+           "ps_status_string", "ps_version")
 
 
 class PsSettings(ctypes.Structure):
@@ -101,6 +101,7 @@ def load():
             "ps_adam_step": ([P, P, P, P, LL, F, F, F, F, I, F, P], I),
             "ps_count_pairs": ([P, P, P, P, P, P, LL, P, P], I),
             "ps_step_advance": ([P, P, I, P, P], I),
+            "ps_gemm_bf16": ([P, P, P, P, P, I, I, I, I, I, I, P, P], I),
             "ps_adam_step_state": ([P, P, P, P, LL, F, F, F, F, P, F, P], I),
             "ps_status_string": ([I], ctypes.c_char_p),
             "ps_version": ([], I),
@@ -290,6 +291,16 @@ def ps_adam_step_state(param, grad, m, v, lr, b1, b2, eps, d_state, clamp_min=fl
     _check(load().ps_adam_step_state(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
                                      float(lr), float(b1), float(b2), float(eps), _ptr(d_state),
                                      float(clamp_min), _stream(stream)), "ps_adam_step_state")
+
+
+def ps_gemm_bf16(A, B, bias, C32, C16, relu=False, accumulate=False, err=None, stream=None):
+    """C = A . B^T (+ bias) (ReLU) on the tensor cores; A [M, K], B [N, K] bf16."""
+    M, K = A.shape
+    N = B.shape[0]
+    C = C32 if C32 is not None else C16
+    _check(load().ps_gemm_bf16(_ptr(A), _ptr(B), _ptr(bias), _ptr(C32), _ptr(C16), int(M), int(N),
+                               int(K), int(C.stride(0)), int(bool(relu)), int(bool(accumulate)),
+                               _ptr(err), _stream(stream)), "ps_gemm_bf16")
 
 
 def ps_status_string(code: int) -> str:
