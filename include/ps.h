@@ -192,6 +192,16 @@ ps_status ps_splat_fwd(const ps_frame* frame, const ps_settings* settings, const
                        long long capacity, float* depth, float* normal, float* alpha,
                        void* ws, size_t ws_bytes, int* d_status, ps_stream stream);
 
+/* Plane-index map: for every pixel, the index (row of the plane arrays) of the
+   nearest composited plane, -1 where none passes the filter.  With PS_HARD
+   this is the plane a ray hits first.  Same walk as ps_splat_fwd; ids
+   [n_pixels] (device, written), depth (device, optional) as in ps_splat_fwd;
+   ws as in ps_splat_fwd.  Used to cut training patches into planes. */
+ps_status ps_splat_ids(const ps_frame* frame, const ps_settings* settings, const float* rec,
+                       const float* key, const int* tile_ptr, const int* tile_ent,
+                       long long capacity, int* ids, float* depth, void* ws, size_t ws_bytes,
+                       int* d_status, ps_stream stream);
+
 /* Render loss (Eq. 14) and its gradient with respect to the rendered maps.
    Pixels with gt_depth <= 0 are not supervised (zero gradient).
    dL_dD [n_pixels], dL_dN [n_pixels][3] (device, written);
@@ -308,6 +318,47 @@ ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v
 ps_status ps_gemm_bf16(const void* A, const void* B, const float* bias, float* C32, void* C16,
                        int M, int N, int K, int ldc, int relu, int accumulate, int* d_err,
                        ps_stream stream);
+
+/* ---- Seed-proposal network (not part of the paper: a learned initialiser of
+   the planes of Sec. 3.1).  Four 3x3 stride-2 convolutions (64 channels, ReLU),
+   global average pooling and a 64 -> 96 linear layer map a 64x64 patch of depth
+   and camera-frame normals to 8 plane seeds.  Convolutions are im2col +
+   ps_gemm_bf16.  Activations NHWC bf16; gradients fp32; the im2col column
+   order is (ky, kx, c) zero-padded to Kp (a multiple of 64).  All pointers are
+   device pointers; every call is asynchronous on the stream. ---- */
+
+/* A[B*Ho*Wo, Kp] (bf16) = im2col of x[B, H, W, C] (bf16) for a 3x3 window,
+   stride 2, padding 1; Ho = ceil(H/2), Wo = ceil(W/2). */
+ps_status ps_seed_im2col(const void* x, int B, int H, int W, int C, int Kp, void* A,
+                         ps_stream stream);
+/* dx[B, H, W, C] (fp32) = adjoint of ps_seed_im2col applied to dA[B*Ho*Wo, Kp] (fp32). */
+ps_status ps_seed_col2im(const float* dA, int B, int H, int W, int C, int Kp, float* dx,
+                         ps_stream stream);
+/* dz = scale * dy * (y > 0) over n elements (ReLU backward); dy fp32, y bf16;
+   dz16 (bf16) and/or dz32 (fp32) written. */
+ps_status ps_seed_relu_bwd(const float* dy, const void* y, long long n, float scale, void* dz16,
+                           float* dz32, ps_stream stream);
+/* out[c, r] = in[r, c] (bf16 out, leading dimension ldo >= R; columns R..ldo-1
+   zero); in is bf16 if in_is_bf16 else fp32, leading dimension ldi. */
+ps_status ps_seed_transpose(const void* in, int in_is_bf16, int R, int C, int ldi, void* out,
+                            int ldo, ps_stream stream);
+/* db[c] = sum over R rows of dz[r, c] (fp32, C <= 256). */
+ps_status ps_seed_colsum(const float* dz, long long R, int C, float* db, ps_stream stream);
+/* h[b, c] = mean over S positions of y[b, s, c] (y bf16; h32 fp32 and/or h16 bf16). */
+ps_status ps_seed_pool(const void* y, int B, int S, int C, float* h32, void* h16,
+                       ps_stream stream);
+/* dy[b, s, c] = dh[b, c] / S (fp32). */
+ps_status ps_seed_pool_bwd(const float* dh, int B, int S, int C, float* dy, ps_stream stream);
+/* Set loss of the seed slots and its gradient.  out[B, slots * 12]: per slot
+   centre (3), quaternion (4, unnormalised), log extents (4), confidence logit;
+   tgt[B, slots, 12]: valid flag, centre, unit quaternion, log extents.  Per slot
+   BCE(logit, valid) + valid (|c - c*|_1 + (1 - |q/|q| . q*|) + 0.5 |e - e*|_1),
+   mean over the batch.  dout (fp32, same shape as out) written; sums[4] (or
+   NULL) receives the four terms summed over the batch. */
+ps_status ps_seed_loss(const float* out, const float* tgt, int B, int slots, float* dout,
+                       float* sums, ps_stream stream);
+/* out[R, Cp] (bf16) = in[R, Cin] (fp32) with zero columns Cin..Cp-1. */
+ps_status ps_cast_bf16(const float* in, int R, int Cin, int Cp, void* out, ps_stream stream);
 
 /* Human-readable name of a status code. */
 const char* ps_status_string(ps_status status);

@@ -23,9 +23,11 @@ PS_HARD = 2
 PS_MAX_M = 64
 
 EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin_tiles",
-           "ps_fwd_workspace_bytes", "ps_splat_fwd", "ps_loss", "ps_bwd_workspace_bytes", "ps_splat_bwd",
+           "ps_fwd_workspace_bytes", "ps_splat_fwd", "ps_splat_ids", "ps_loss", "ps_bwd_workspace_bytes", "ps_splat_bwd",
            "ps_splat_fused", "ps_adam_step",
            "ps_count_pairs", "ps_step_advance", "ps_adam_step_state", "ps_gemm_bf16",
+           "ps_seed_im2col", "ps_seed_col2im", "ps_seed_relu_bwd", "ps_seed_transpose",
+           "ps_seed_colsum", "ps_seed_pool", "ps_seed_pool_bwd", "ps_seed_loss", "ps_cast_bf16",
            "ps_status_string", "ps_version")
 
 
@@ -94,6 +96,7 @@ def load():
             "ps_bin_tiles": ([P, P, P, P, P, P, LL, P, P, SZ, P, P], I),
             "ps_fwd_workspace_bytes": ([P], SZ),
             "ps_splat_fwd": ([P, P, P, P, P, P, LL, P, P, P, P, SZ, P, P], I),
+            "ps_splat_ids": ([P, P, P, P, P, P, LL, P, P, P, SZ, P, P], I),
             "ps_loss": ([P, P, P, P, P, P, P, P, P, P], I),
             "ps_bwd_workspace_bytes": ([P], SZ),
             "ps_splat_bwd": ([P, P, P, P, P, P, P, LL, P, P, P, P, P, P, SZ, P, P], I),
@@ -102,6 +105,15 @@ def load():
             "ps_count_pairs": ([P, P, P, P, P, P, LL, P, P], I),
             "ps_step_advance": ([P, P, I, P, P], I),
             "ps_gemm_bf16": ([P, P, P, P, P, I, I, I, I, I, I, P, P], I),
+            "ps_seed_im2col": ([P, I, I, I, I, I, P, P], I),
+            "ps_seed_col2im": ([P, I, I, I, I, I, P, P], I),
+            "ps_seed_relu_bwd": ([P, P, LL, F, P, P, P], I),
+            "ps_seed_transpose": ([P, I, I, I, I, P, I, P], I),
+            "ps_seed_colsum": ([P, LL, I, P, P], I),
+            "ps_seed_pool": ([P, I, I, I, P, P, P], I),
+            "ps_seed_pool_bwd": ([P, I, I, I, P, P], I),
+            "ps_seed_loss": ([P, P, I, I, P, P, P], I),
+            "ps_cast_bf16": ([P, I, I, I, P, P], I),
             "ps_adam_step_state": ([P, P, P, P, LL, F, F, F, F, P, F, P], I),
             "ps_status_string": ([I], ctypes.c_char_p),
             "ps_version": ([], I),
@@ -237,6 +249,14 @@ def ps_splat_fwd(frame, settings, rec, key, tile_ptr, tile_ent, capacity, depth,
            "ps_splat_fwd")
 
 
+def ps_splat_ids(frame, settings, rec, key, tile_ptr, tile_ent, capacity, ids, depth, ws, status,
+                 stream=None):
+    nbytes = ws.numel() * ws.element_size()
+    _check(load().ps_splat_ids(ctypes.byref(frame), ctypes.byref(settings), _ptr(rec), _ptr(key),
+                               _ptr(tile_ptr), _ptr(tile_ent), int(capacity), _ptr(ids), _ptr(depth),
+                               _ptr(ws), nbytes, _ptr(status), _stream(stream)), "ps_splat_ids")
+
+
 def ps_loss(frame, settings, depth, normal, gt_depth, gt_normal, dLdD, dLdN, view_sums, stream=None):
     _check(load().ps_loss(ctypes.byref(frame), ctypes.byref(settings), _ptr(depth), _ptr(normal),
                           _ptr(gt_depth), _ptr(gt_normal), _ptr(dLdD), _ptr(dLdN),
@@ -301,6 +321,52 @@ def ps_gemm_bf16(A, B, bias, C32, C16, relu=False, accumulate=False, err=None, s
     _check(load().ps_gemm_bf16(_ptr(A), _ptr(B), _ptr(bias), _ptr(C32), _ptr(C16), int(M), int(N),
                                int(K), int(C.stride(0)), int(bool(relu)), int(bool(accumulate)),
                                _ptr(err), _stream(stream)), "ps_gemm_bf16")
+
+
+def ps_seed_im2col(x, B, H, W, C, Kp, A, stream=None):
+    _check(load().ps_seed_im2col(_ptr(x), B, H, W, C, Kp, _ptr(A), _stream(stream)), "ps_seed_im2col")
+
+
+def ps_seed_col2im(dA, B, H, W, C, Kp, dx, stream=None):
+    _check(load().ps_seed_col2im(_ptr(dA), B, H, W, C, Kp, _ptr(dx), _stream(stream)), "ps_seed_col2im")
+
+
+def ps_seed_relu_bwd(dy, y, scale, dz16=None, dz32=None, stream=None):
+    _check(load().ps_seed_relu_bwd(_ptr(dy), _ptr(y), dy.numel(), float(scale), _ptr(dz16),
+                                   _ptr(dz32), _stream(stream)), "ps_seed_relu_bwd")
+
+
+def ps_seed_transpose(inp, out, R=None, stream=None):
+    """out[c, r] = inp[r, c] for the 2-D tensor inp; out must be [C, ldo >= R]."""
+    Rr, C = inp.shape
+    R = Rr if R is None else R
+    _check(load().ps_seed_transpose(_ptr(inp), int(inp.dtype != __import__("torch").float32), R, C,
+                                    inp.stride(0), _ptr(out), out.stride(0), _stream(stream)),
+           "ps_seed_transpose")
+
+
+def ps_seed_colsum(dz, db, stream=None):
+    R, C = dz.shape
+    _check(load().ps_seed_colsum(_ptr(dz), R, C, _ptr(db), _stream(stream)), "ps_seed_colsum")
+
+
+def ps_seed_pool(y, B, S, C, h32=None, h16=None, stream=None):
+    _check(load().ps_seed_pool(_ptr(y), B, S, C, _ptr(h32), _ptr(h16), _stream(stream)), "ps_seed_pool")
+
+
+def ps_seed_pool_bwd(dh, B, S, C, dy, stream=None):
+    _check(load().ps_seed_pool_bwd(_ptr(dh), B, S, C, _ptr(dy), _stream(stream)), "ps_seed_pool_bwd")
+
+
+def ps_seed_loss(out, tgt, B, slots, dout, sums=None, stream=None):
+    _check(load().ps_seed_loss(_ptr(out), _ptr(tgt), B, slots, _ptr(dout), _ptr(sums),
+                               _stream(stream)), "ps_seed_loss")
+
+
+def ps_cast_bf16(inp, out, stream=None):
+    R, Cin = inp.shape
+    _check(load().ps_cast_bf16(_ptr(inp), R, Cin, out.shape[1], _ptr(out), _stream(stream)),
+           "ps_cast_bf16")
 
 
 def ps_status_string(code: int) -> str:

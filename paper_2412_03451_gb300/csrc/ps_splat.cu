@@ -68,6 +68,7 @@ struct SplatArgs {
     float* depth;
     float* normal;
     float* alpha;
+    int* ids;                 // optional: plane index of the nearest composited pair
     // backward inputs / outputs
     const float* dLdD;
     const float* dLdN;
@@ -176,6 +177,7 @@ __device__ __forceinline__ void pend_pop(Walk& s)
 // Forward accumulators.
 struct Accum {
     float D, N0, N1, N2, A;
+    int first;        // record id of the first composited pair, -1 if none
 };
 
 struct Sink {
@@ -190,6 +192,7 @@ __device__ __forceinline__ void composite(Walk& s, Sink& k, const float4* __rest
 {
     if constexpr (MODE != kFwd) k.stk[s.cnt * 32] = make_int2(id, __float_as_int(s.T));
     if constexpr (MODE != kBwd) {
+        if (k.acc.first < 0) k.acc.first = id;
         const float4 n = __ldg(&rec[(size_t)id * 4]);
         const float tw = s.T * w;
         k.acc.D = fmaf(tw, t, k.acc.D);
@@ -326,7 +329,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
     s.has_cut = false; s.ct = 0.f; s.cid = 0;
     s.done = !inside;
     Sink k;
-    k.acc = Accum{0.f, 0.f, 0.f, 0.f, 0.f};
+    k.acc = Accum{0.f, 0.f, 0.f, 0.f, 0.f, -1};
     k.stk = stk_warp + lane;
     float gD = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
     // fused: the pixel's supervision is loaded before the walk so its latency is hidden
@@ -359,6 +362,10 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
                 a.normal[3 * pix + 2] = k.acc.N2;
             }
             if (a.alpha) a.alpha[pix] = k.acc.A;
+            if (a.ids)
+                a.ids[pix] = k.acc.first < 0
+                                 ? -1
+                                 : k.acc.first - __ldg(&vw->rec_off) + __ldg(&vw->plane_off);
         }
     }
     bool supervised = inside;
@@ -927,6 +934,27 @@ extern "C" ps_status ps_splat_fwd(const ps_frame* f, const ps_settings* s, const
     a.c = make_const(s); a.M = s->M; a.d_state = s->d_state;
     a.counter = static_cast<int*>(ws);
     a.depth = depth; a.normal = normal; a.alpha = alpha; a.status = d_status;
+    if (dispatch<kFwd>(a, s, f->n_tiles, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return PS_ERR_CUDA;
+    return PS_OK;
+}
+
+extern "C" ps_status ps_splat_ids(const ps_frame* f, const ps_settings* s, const float* rec,
+                                  const float* key, const int* tile_ptr, const int* tile_ent,
+                                  long long capacity, int* ids, float* depth, void* ws,
+                                  size_t ws_bytes, int* d_status, ps_stream stream)
+{
+    ps_status e = check_common(f, s, rec, key, tile_ptr, tile_ent, capacity);
+    if (e != PS_OK) return e;
+    if (!ids || !ws) return PS_ERR_ARG;
+    if (ws_bytes < kCounterBytes || (reinterpret_cast<uintptr_t>(ws) & 15)) return PS_ERR_ARG;
+    SplatArgs a{};
+    a.views = f->views; a.n_views = f->n_views;
+    a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
+    a.tile_ptr = tile_ptr; a.tile_ent = tile_ent; a.capacity = capacity;
+    a.c = make_const(s); a.M = s->M; a.d_state = s->d_state;
+    a.counter = static_cast<int*>(ws);
+    a.depth = depth; a.normal = nullptr; a.alpha = nullptr; a.ids = ids; a.status = d_status;
     if (dispatch<kFwd>(a, s, f->n_tiles, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
         return PS_ERR_CUDA;
     return PS_OK;

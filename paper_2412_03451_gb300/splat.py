@@ -166,6 +166,15 @@ class Renderer:
         self.project_bin(flat, lam, flags)
         return self.splat_forward(alpha)
 
+    def plane_ids(self, flat: torch.Tensor, lam: float = 300.0, hard: bool = True):
+        """Per-pixel index of the nearest composited plane (-1: none) and depth."""
+        fl = B.PS_HARD if hard else 0
+        self.project_bin(flat, lam, flags=fl)
+        ids = torch.empty(int(self.frame.n_pixels), dtype=torch.int32, device=self.device)
+        B.ps_splat_ids(self.frame, self.settings, self.rec, self.key, self.tile_ptr, self.tile_ent,
+                       self.capacity, ids, self.depth, self.fwd_ws, self.status)
+        return ids, self.depth
+
     def count_pairs(self, counts: torch.Tensor):
         """Work counts of the current tile lists (tested, candidate, composited pairs)."""
         B.ps_count_pairs(self.frame, self.settings, self.rec, self.key, self.tile_ptr,

@@ -453,3 +453,22 @@ def test_multi_scene_frame_equals_single_scene_runs():
         assert np.allclose(vs_all[4 * s:4 * s + 4], vs1, rtol=1e-6)
         off += K
     report("multi_scene", K=K_all)
+
+
+def test_plane_ids_match_ray_caster():
+    import torch
+    from paper_2412_03451_gb300 import splat as SP
+    room = S.tiny_room(0)
+    cams = room.cams
+    V, H, W = cams.V, cams.H, cams.W
+    r = SP.Renderer([H] * V, [W] * V, [0] * V, [0, room.gt.K])
+    r.set_cameras(cams.w2c, cams.intr)
+    flat = SP.planes_to_flat(room.gt.center, room.gt.quat, room.gt.radii, "cuda")
+    r.ensure_capacity(flat, 300.0)
+    ids, _ = r.plane_ids(flat)
+    torch.cuda.synchronize()
+    _, _, pid = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, cams.w2c, cams.intr, H, W,
+                          z_near=f32(0.01))
+    same = ids.cpu().numpy().reshape(V, H, W) == pid
+    report("plane_ids", frac_same=float(same.mean()))
+    assert same.mean() > 0.995
