@@ -407,7 +407,7 @@ def run_ours(args, rank, world, local_rank):
     if args.batched > 0:
         del wl
         torch.cuda.empty_cache()
-        result["time_to_2cm_batched_vs_plain"] = run_batched(args, rank, device)
+        result["time_to_2cm_vs_plain"] = run_batched(args, rank, device)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         from paper_2412_03451_gb300 import scenes as S
         room = S.large_room(1000 + rank, n_rect=N_GT, n_views=N_VIEWS, H=H, W=W, f=F)
@@ -418,19 +418,25 @@ def run_ours(args, rank, world, local_rank):
 
 def run_batched(args, rank, device):
     """Time to mean depth error <= 2 cm of uneven rooms (plane counts U{200..3000},
-    views U{16..96}, resolutions 320x240 / 480x360 / 640x480; initial radii half the
-    nearest-neighbour spacing, Sec. 3.1): all rooms fitted together, one launch per
-    kernel per step, vs the same rooms fitted one by one (plain).  Both replay
-    captured graphs of the same kernels; GPU time by CUDA events, convergence
-    checks (one small device-to-host copy per rotation of camera batches)
-    excluded.  The comparison uses the rooms that reach 2 cm in both runs."""
+    views U{16..96}, resolutions 320x240 / 480x360 / 640x480): every room to
+    2 cm or the iteration cap, GPU seconds by CUDA events (convergence checks
+    and frame rebuilds excluded).
+      plain:           plain initialisation (random surface points and
+                       orientations, radii half the nearest-neighbour spacing,
+                       Sec. 3.1), rooms fitted one by one;
+      batched:         the same initialisation, all rooms in one launch per
+                       kernel per step, rooms leaving the batch when done;
+      batched_learned: network-proposed initialisation (inference time
+                       included), batched."""
+    import torch
+    from paper_2412_03451_gb300 import autotune
     from paper_2412_03451_gb300 import batch as BT
     from paper_2412_03451_gb300 import scenes as S
+    from paper_2412_03451_gb300 import seed_train as ST
     n = args.batched
     rooms = S.batch_rooms(n, seed0=3000 + 100 * rank)
     inits = [S.surface_init_nn(room, K, 4000 + 100 * rank + i) for i, (room, K) in enumerate(rooms)]
     ss = BT.SceneSet([r for r, _ in rooms], inits, device=device)
-    from paper_2412_03451_gb300 import autotune
 
     def make(tile):
         ss.tile = tile
@@ -440,103 +446,54 @@ def run_batched(args, rank, device):
 
     key = autotune.key_for([(rm.cams.H, rm.cams.W) for rm in ss.rooms], ss.vps * n, sum(ss.K))
     tile, tuning = autotune.pick_tile(make, ss.flat_init(), ss.gt_depth, ss.gt_normal,
-                                      1.0 * 20.0 / 2.718281828459045, key)
+                                      20.0 / 2.718281828459045, key)
     ss.tile = tile
-    bat = BT.fit_until(ss, list(range(n)), max_iters=args.batched_iters)
     plain = [BT.fit_until(ss, [s], max_iters=args.batched_iters) for s in range(n)]
-    t_bat = bat["gpu_ms"] / 1e3
+    bat = BT.fit_until(ss, list(range(n)), max_iters=args.batched_iters)
     t_plain = sum(p["gpu_ms"] for p in plain) / 1e3
-    return {"rooms": n, "what": "GPU seconds to fit every room to mean depth error <= 2 cm "
-                                "(rooms that have not reached it by the iteration cap stop there)",
-            "batched_s": round(t_bat, 3), "plain_s": round(t_plain, 3),
-            "speedup": round(t_plain / t_bat, 3) if t_bat > 0 else None,
-            "reached_batched": sum(d is not None for d in bat["done_at"]),
-            "reached_plain": sum(p["done_at"][0] is not None for p in plain),
-            "iteration_cap": args.batched_iters,
-            "batched": "all rooms in one launch per kernel per step; rooms leave the batch when done",
-            "tile": "%dx%d" % tile, "autotune_ms": {k: round(v, 4) for k, v in tuning.items()},
-            "init": "random surface points, radii 0.5 x nearest-neighbour distance, random orientation"}
-
-
-def B_CAP():
-    return 3
-
-
-def run_e2e(wl, args, first, world):
-    """Same metric through host buffers: each step copies its views' ground-truth
-    depth/normal maps from pinned host memory to the device and reads the loss
-    sums back, inside the timed region."""
-    import torch
-    dev = wl.flat.device
-    n = VIEWS_PER_STEP * wl.hw
-    host_d = wl.gt_depth.cpu().pin_memory()
-    host_n = wl.gt_normal.cpu().pin_memory()
-    dev_d = torch.empty(n, dtype=torch.float32, device=dev)
-    dev_n = torch.empty((n, 3), dtype=torch.float32, device=dev)
-    out = torch.empty((VIEWS_PER_STEP, 4), dtype=torch.float64).pin_memory()
-    K = args.steps
-    for s in range(first, first + K):
-        wl.grow_if_needed(s)
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    ev0.record()
-    for i in range(K):
-        s = first + i
-        b = (s % (N_VIEWS // VIEWS_PER_STEP)) * VIEWS_PER_STEP
-        dev_d.copy_(host_d[b * wl.hw:b * wl.hw + n], non_blocking=True)
-        dev_n.copy_(host_n[b * wl.hw:b * wl.hw + n], non_blocking=True)
-        vs = wl.step(s, gt=(dev_d, dev_n))
-        out.copy_(vs, non_blocking=True)
-    ev1.record()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    ms = ev0.elapsed_time(ev1)
-    t = max(ms / 1e3, wall)
-    value = world * VIEWS_PER_STEP * H * W * K / t / 1e6
-    return {"value": round(value, 3), "unit": UNIT,
-            "h2d_bytes_per_step": int(n * 4 + n * 12), "d2h_bytes_per_step": VIEWS_PER_STEP * 4 * 8,
-            "ms_per_step": round(t * 1e3 / K, 4)}
-
-
-def run_ttd(wl, max_iters):
-    """Wall time of the plain single-scene fit (from the initial planes, lambda
-    schedule from 0) until the mean |D - D_gt| over all 64 views is <= 2 cm,
-    checked every 8 steps (one pass over the views) with a forward-only render
-    of all views; evaluation time is excluded."""
-    import torch
-    from paper_2412_03451_gb300 import splat as SP
-    wl.reset(0)
-    ev = SP.Renderer([H] * N_VIEWS, [W] * N_VIEWS, [0] * N_VIEWS, [0, N_INIT],
-                     tile=wl.r.tile, device=wl.flat.device)
-    ev.set_cameras(wl.room.cams.w2c, wl.room.cams.intr)
-    nb = N_VIEWS // VIEWS_PER_STEP
-    spent = 0.0
-    err = float("nan")
-    hist = []
-    for it in range(0, max_iters, nb):
-        for s in range(it, it + nb):
-            wl.grow_if_needed(s)
+    t_bat = bat["gpu_ms"] / 1e3
+    out = {"rooms": n, "what": "GPU seconds to fit every room to mean depth error <= 2 cm "
+                               "(rooms that have not reached it by the iteration cap stop there)",
+           "plain_s": round(t_plain, 3), "batched_s": round(t_bat, 3),
+           "speedup_batched": round(t_plain / t_bat, 3) if t_bat > 0 else None,
+           "reached_plain": sum(p["done_at"][0] is not None for p in plain),
+           "reached_batched": sum(d is not None for d in bat["done_at"]),
+           "iteration_cap": args.batched_iters, "tile": "%dx%d" % tile,
+           "autotune_ms": {k: round(v, 4) for k, v in tuning.items()},
+           "init_plain": "random surface points, random orientation, radii 0.5 x nearest-neighbour distance"}
+    net = ST.load(device=device)
+    if net is None:
+        out["batched_learned"] = "no trained weights"
+        return out
+    # warm the network's kernels once (first-call set-up is not inference)
+    r0 = ss.rooms[0]
+    c0 = r0.cams
+    ST.propose_planes(net, r0, ss.gt_depth[:c0.H * c0.W].view(1, c0.H, c0.W),
+                      ss.gt_normal[:c0.H * c0.W].view(1, c0.H, c0.W, 3), [0], max_planes=100)
+    learned, infer_ms = [], 0.0
+    for i, room in enumerate(ss.rooms):
+        c = room.cams
+        off = int(ss.gt_off[i][0])
+        m = c.V * c.H * c.W
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for s in range(it, it + nb):
-            wl.step(s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P, _, _ = ST.propose_planes(net, room, ss.gt_depth[off:off + m].view(c.V, c.H, c.W),
+                                    ss.gt_normal[off:off + m].view(c.V, c.H, c.W, 3), range(c.V),
+                                    seed=5000 + i, max_planes=ss.K[i])
+        e1.record()
         torch.cuda.synchronize()
-        spent += time.perf_counter() - t0
-        if (it // nb) % 4 == 3 or it + nb >= max_iters:
-            lam = SP.B.lambda_schedule(wl.fit.ite)
-            ev.ensure_capacity(wl.flat, lam)
-            ev.forward(wl.flat, lam, alpha=False)
-            e = (ev.depth - wl.gt_depth).abs()
-            valid = wl.gt_depth > 0
-            err = float(e[valid].mean().item())
-            hist.append((wl.fit.ite, round(err, 5), round(spent, 3)))
-            if err <= 0.02:
-                return {"seconds": round(spent, 3), "iterations": wl.fit.ite, "depth_err_m": err,
-                        "reached": True, "history": hist}
-    return {"seconds": round(spent, 3), "iterations": wl.fit.ite, "depth_err_m": err,
-            "reached": False, "history": hist}
+        infer_ms += e0.elapsed_time(e1)
+        learned.append(P)
+    ss_l = BT.SceneSet(ss.rooms, learned, device=device, tile=tile)
+    bl = BT.fit_until(ss_l, list(range(n)), max_iters=args.batched_iters,
+                      lam_offset=ST.LEARNED_LAM_OFFSET)
+    t_bl = bl["gpu_ms"] / 1e3 + infer_ms / 1e3
+    out.update({"batched_learned_s": round(t_bl, 3), "learned_inference_s": round(infer_ms / 1e3, 3),
+                "speedup_batched_learned": round(t_plain / t_bl, 3) if t_bl > 0 else None,
+                "reached_batched_learned": sum(d is not None for d in bl["done_at"]),
+                "learned_lambda_start_iteration": ST.LEARNED_LAM_OFFSET})
+    return out
 
 
 # ---------------------------------------------------------------------------

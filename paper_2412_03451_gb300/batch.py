@@ -113,7 +113,7 @@ def join_flat(flats, Ks):
 
 
 def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_headroom=1.6,
-              use_graphs=True, compact=True):
+              use_graphs=True, compact=True, lam_offset=0):
     """Fits the given scenes together (one launch per kernel per step) until
     every scene's mean depth error is <= threshold or max_iters.  With compact,
     scenes that reach the threshold leave the batch: the remaining scenes'
@@ -140,10 +140,11 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
         fit.m.copy_(join_flat([moments[s][0] for s in active], Ks))
         fit.v.copy_(join_flat([moments[s][1] for s in active], Ks))
         fit.ite = ite
+        fit.lam_offset = lam_offset
         need = 0
         for b in range(nb):
             r.select(b)
-            r.ensure_capacity(flat, B.lambda_schedule(ite), headroom=capacity_headroom)
+            r.ensure_capacity(flat, B.lambda_schedule(ite + lam_offset), headroom=capacity_headroom)
             need = max(need, int(r.required.item()))
         if need * capacity_headroom > r.capacity:
             r._alloc_lists(int(need * capacity_headroom) + 1024)
@@ -191,8 +192,13 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
                 active = [s for s in active if done_at[s] is None]
                 rebuild = True
             elif all(done_at[s] is not None for s in active):
+                for s, f in zip(active, split_flat(fit.flat, Ks)):
+                    params[s] = f.clone()
                 active = []
                 break
+        if not rebuild and active:
+            for s, f in zip(active, split_flat(fit.flat, Ks)):
+                params[s] = f.clone()
         del fit, r
     return {"iterations": ite, "gpu_ms": spent_ms, "done_at": [done_at[s] for s in scenes],
-            "err": [err[s] for s in scenes]}
+            "err": [err[s] for s in scenes], "params": [params[s] for s in scenes]}

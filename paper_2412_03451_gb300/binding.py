@@ -186,14 +186,16 @@ def make_settings(lam, delta, M=30, tile_w=16, tile_h=16, flags=0, w_min=1e-4, z
     return s
 
 
-def step_schedule(n: int, first: int = 0, b1: float = 0.9, b2: float = 0.999) -> bytes:
-    """Packed ps_step_state entries for iterations first .. first + n - 1: lambda
-    (Eq. 10, rounded to f32), the binning margin of that f32 lambda, the Adam
-    step number and bias corrections -- the same values the host path uses."""
+def step_schedule(n: int, first: int = 0, b1: float = 0.9, b2: float = 0.999,
+                  lam_offset: int = 0) -> bytes:
+    """Packed ps_step_state entries for optimisation steps first .. first + n - 1:
+    lambda (Eq. 10 at iteration step + lam_offset, rounded to f32), the binning
+    margin of that f32 lambda, the Adam step number (step + 1) and its bias
+    corrections -- the same values the host path uses."""
     arr = (PsStepState * n)()
     for i in range(n):
         ite = first + i
-        lam = float(np.float32(lambda_schedule(ite)))
+        lam = float(np.float32(lambda_schedule(ite + lam_offset)))
         arr[i].lambda_ = lam
         arr[i].delta = filter_margin(lam)
         arr[i].step = ite + 1

@@ -244,6 +244,9 @@ class Fitter:
         self.v = torch.zeros_like(flat)
         self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
         self.ite = 0
+        # Eq. 10 is evaluated at ite + lam_offset: a fit from a good initialisation
+        # may skip the schedule's blurry start (Adam's step count is unaffected)
+        self.lam_offset = 0
 
     # -- captured CUDA graphs ------------------------------------------------------
     def enable_graphs(self, n_iters: int, batches, gt_slices):
@@ -254,7 +257,7 @@ class Fitter:
         at iteration s reproduces the eager step.  Capacity must already suffice
         (checked after replays through the status word)."""
         dev = self.flat.device
-        sched = B.step_schedule(n_iters)
+        sched = B.step_schedule(n_iters, lam_offset=self.lam_offset)
         self.d_sched = torch.frombuffer(bytearray(sched), dtype=torch.uint8).to(dev)
         self.n_sched = n_iters
         self.d_state = torch.zeros(32, dtype=torch.uint8, device=dev)
@@ -308,7 +311,7 @@ class Fitter:
                 e.record()
                 marks.append((tag, e))
 
-        lam = B.lambda_schedule(self.ite) if lam is None else lam
+        lam = B.lambda_schedule(self.ite + self.lam_offset) if lam is None else lam
         r = self.r
         mark("start")
         r.project_bin(self.flat, lam)
