@@ -36,6 +36,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2412_03451_gb300 import ranks as RK  # noqa: E402
+
 METRIC = "fwd+bwd splat Mpixel-views/s & time-to-depth-err≤2cm vs plain, 1×GB300"
 UNIT = "Mpixel-views/s"
 CAPACITY_BIT = 1 << 3          # PS_ERR_CAPACITY in the device status word
@@ -168,8 +170,9 @@ class Workload:
         from paper_2412_03451_gb300 import scenes as S
         from paper_2412_03451_gb300 import splat as SP
         self.torch, self.B, self.SP = torch, B, SP
-        self.room = S.large_room(1000 + rank, n_rect=N_GT, n_views=N_VIEWS, H=H, W=W, f=F)
-        self.init = S.surface_init(self.room, N_INIT, 2000 + rank)
+        seeds = RK.rank_seeds(rank)
+        self.room = S.large_room(seeds["scene"], n_rect=N_GT, n_views=N_VIEWS, H=H, W=W, f=F)
+        self.init = S.surface_init(self.room, N_INIT, seeds["init"])
         cams = self.room.cams
         # ground truth: exact ray casting of the GT rectangles with the library's hard mode
         gtr = SP.Renderer([H] * N_VIEWS, [W] * N_VIEWS, [0] * N_VIEWS, [0, N_GT], tile=tile,
@@ -286,7 +289,6 @@ def time_replays(wl, first, K, flush):
 
 def run_ours(args, rank, world, local_rank):
     import torch
-    import torch.distributed as dist
     import __graft_entry__
     __graft_entry__.build()
     device = "cuda:%d" % local_rank
@@ -332,8 +334,7 @@ def run_ours(args, rank, world, local_rank):
         wl.fit.enable_graphs(first + args.steps + 8, list(range(nb)),
                              [wl.gt_slice(b) for b in range(nb)])
         wl.r.status.zero_()
-    if world > 1:
-        dist.barrier()
+    RK.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
     if use_graphs:
@@ -349,14 +350,11 @@ def run_ours(args, rank, world, local_rank):
     if status & CAPACITY_BIT:
         raise RuntimeError("tile-list capacity overflow inside the timed region")
 
-    dev_ms = sum(per_step)
-    t_max = torch.tensor([dev_ms], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    dev_ms = float(t_max.item())
+    # slowest rank's device time; units summed over ranks (each renders its own room)
+    dev_ms = RK.max_over_ranks(sum(per_step), device)
+    RK.barrier()
     pix = VIEWS_PER_STEP * H * W
-    value = world * pix * args.steps / (dev_ms / 1e3) / 1e6
+    value = RK.job_throughput(RK.sum_over_ranks(pix * args.steps, device), dev_ms / 1e3) / 1e6
 
     # roofline of the dominant kernel (ALU-bound: FP32 work of the formulas),
     # its duration from the eager pass's CUDA events on the launching stream
@@ -528,8 +526,8 @@ def run_e2e(wl, args, first, world):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ms = ev0.elapsed_time(ev1)
-    t = max(ms / 1e3, wall)
-    value = world * VIEWS_PER_STEP * H * W * K / t / 1e6
+    t = RK.max_over_ranks(max(ms / 1e3, wall), dev)
+    value = RK.job_throughput(RK.sum_over_ranks(VIEWS_PER_STEP * H * W * K, dev), t) / 1e6
     return {"value": round(value, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(n * 4 + n * 12), "d2h_bytes_per_step": VIEWS_PER_STEP * 4 * 8,
             "ms_per_step": round(t * 1e3 / K, 4)}
