@@ -64,7 +64,7 @@ LAUNCHES_SPLIT = 1 + 11 + 4 + 2
 # DRAM bytes (read + write) per launch of the fused splat kernel from the ncu
 # capture summarised in profiles/k_splat_fused_room640_8x8.md; reported only while
 # the kernel source is the one it was taken on.
-TRAFFIC = {"splat_fused": 45941504 + 372480, "src_sha": "f3fdc222c08c2bea"}
+TRAFFIC = {"splat_fused": 45935104 + 398592, "src_sha": "75432b19998e4ea0"}
 
 
 def src_hash() -> str:
