@@ -69,40 +69,34 @@ struct SplatConst {
     int hard;          // PS_HARD
 };
 
+// Every operation is executed for every lane and the filter is applied at the
+// end: lanes of a warp leave at different tests, so early returns would only
+// serialise the warp.  The selected values are the same as with early exits.
 __device__ __forceinline__ bool eval_pair(const float4& n, const float4& vx, const float4& vy,
                                           const float4& r, float dx, float dy,
                                           const SplatConst& c, PairEval& o)
 {
-    float den = fmaf(dx, n.x, fmaf(dy, n.y, n.z));
-    if (!(fabsf(den) > 1e-6f)) return false;
-    float t = __fdividef(n.w, den);
-    if (!(t > c.z_near && t < c.z_far)) return false;
-    float dvx = fmaf(dx, vx.x, fmaf(dy, vx.y, vx.z));
-    float dvy = fmaf(dx, vy.x, fmaf(dy, vy.y, vy.z));
-    float X = fmaf(t, dvx, -vx.w);
-    float Y = fmaf(t, dvy, -vy.w);
-    float mX = (X > 0.f ? r.x : r.y) - fabsf(X);
-    float mY = (Y > 0.f ? r.z : r.w) - fabsf(Y);
-    bool sx = mX < mY;
-    float m = sx ? mX : mY;
-    if (m < -c.reject) return false;
-    float w;
-    if (m >= 0.f) {
-        w = 1.f;
-    } else if (c.hard) {
-        return false;
-    } else {
-        // 2 sigmoid(x) = 2 e^x / (1 + e^x) for x = 5 lambda m < 0
-        float e = __expf(c.lam5 * m);
-        w = __fdividef(2.f * e, 1.f + e);
-    }
-    if (!(w >= c.w_min)) return false;
+    const float den = fmaf(dx, n.x, fmaf(dy, n.y, n.z));
+    const float t = __fdividef(n.w, den);
+    const float dvx = fmaf(dx, vx.x, fmaf(dy, vx.y, vx.z));
+    const float dvy = fmaf(dx, vy.x, fmaf(dy, vy.y, vy.z));
+    const float X = fmaf(t, dvx, -vx.w);
+    const float Y = fmaf(t, dvy, -vy.w);
+    const float mX = (X > 0.f ? r.x : r.y) - fabsf(X);
+    const float mY = (Y > 0.f ? r.z : r.w) - fabsf(Y);
+    const bool sx = mX < mY;
+    const float m = sx ? mX : mY;
+    // w = min(1, 2 sigmoid(5 lambda m)); below the clamp 2 sigmoid(x) = 2 e^x / (1 + e^x)
+    const float e = __expf(c.lam5 * m);
+    const float w = (m >= 0.f) ? 1.f : __fdividef(2.f * e, 1.f + e);
+    const bool ok = (fabsf(den) > 1e-6f) && (t > c.z_near && t < c.z_far) && !(m < -c.reject) &&
+                    (m >= 0.f || !c.hard) && (w >= c.w_min);
     o.t = t; o.w = w; o.m = m; o.den = den;
     o.sideX = sx;
     o.P = sx ? X : Y;
     o.dv = sx ? dvx : dvy;
     o.pos = o.P > 0.f;
-    return true;
+    return ok;
 }
 
 // Rays through the pixel centres at the corners of a warp's pixel rectangle.
