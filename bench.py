@@ -55,11 +55,19 @@ N_VIEWS, VIEWS_PER_STEP, N_GT, N_INIT = 64, 8, 2000, 3000
 #     + record accumulation 16                                         = 66
 FLOP_CAND, FLOP_COMP_FWD, FLOP_COMP_BWD = 27, 12, 66
 SM_COUNT, FP32_LANES = 152, 128
-# kernels of one step: schedule advance 1 (graphs); project 1; bin 1 + 3 (record scan) + 1
-# + 3 (tile scan) + 1 + 2 (sorts); fused splat 1 + chain 1 (split: fwd 1, loss 1, bwd 1 +
+# kernels of one step: schedule advance 1 (graphs); project 1; bin: record counts 1,
+# record scan, pair count 1, tile scan, scatter 1, sorts 2 (a scan is one launch up to
+# 65,536 elements, three beyond); fused splat 1 + chain 1 (split: fwd 1, loss 1, bwd 1 +
 # chain 1); Adam 2
-LAUNCHES_FUSED = 1 + 1 + 11 + 2 + 2
-LAUNCHES_SPLIT = 1 + 11 + 4 + 2
+
+
+def scan_launches(n: int) -> int:
+    return 1 if n <= 65536 else 3  # one launch up to 8 scan tiles of 8,192
+
+
+def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:
+    binning = 5 + scan_launches(n_records) + scan_launches(n_tiles)
+    return (1 + 1 + binning + 2 + 2) if fused else (1 + binning + 4 + 2)
 
 # DRAM bytes (read + write) per launch of the fused splat kernel from the ncu
 # capture summarised in profiles/k_splat_fused_room640_8x8.md; reported only while
@@ -395,7 +403,8 @@ def run_ours(args, rank, world, local_rank):
         "eager_ms_per_step": round(sum(per_step_eager) / args.steps, 4),
         "wall_s_timed": round(wall, 4),
         "roofline": roofline, "clocks": clocks,
-        "gpu_launches": (LAUNCHES_FUSED if wl.fit.fused else LAUNCHES_SPLIT) * args.steps,
+        "gpu_launches": step_launches(int(wl.r.frame.n_records), int(wl.r.frame.n_tiles),
+                                      wl.fit.fused) * args.steps,
         "culling": {"tested_per_candidate": round(tested / max(cand, 1), 2)},
     }
 

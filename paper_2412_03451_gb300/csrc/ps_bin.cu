@@ -16,9 +16,9 @@
 //   4. scatter: one thread per pair writes its record id into a slot of its
 //      tile (unordered, via per-tile cursors);
 //   5. sort: each tile's slots by (key, record id): one warp per tile sorts up
-//      to 32 entries in registers and up to kWarpSortCap in its slice of shared
-//      memory (bitonic networks); a CTA per tile takes longer lists (bitonic up
-//      to kSortCap entries, an O(n^2) rank sort beyond).
+//      to 64 entries in registers and up to kWarpSortCap in its slice of shared
+//      memory (bitonic networks); persistent CTAs take the longer lists
+//      (bitonic up to kSortCap entries, an O(n^2) rank sort beyond).
 // Every pair gets its own thread, so a plane covering a thousand tiles costs
 // no more latency than one covering a single tile.
 #include "ps_internal.cuh"
@@ -34,6 +34,7 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;      // elements per thread per scan tile
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kFlatBlocks = 152 * 8;
+constexpr int kSortBlocks = 152 * 4;  // persistent blocks of the long-list sort
 
 struct BinWs {
     int* rec_cnt;       // [R + 1] tiles per record -> exclusive prefix (pair numbering)
@@ -207,9 +208,71 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
     }
 }
 
+// Arrays of up to kScanOneMax elements: one CTA walks the array in tiles of
+// kScanTile elements (coalesced loads into shared memory, kScanItems
+// consecutive elements per thread, a block scan, a running carry): one launch
+// instead of three.
+constexpr int kScanOneMax = 8 * kScanTile;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_one(const int* __restrict__ in, int n,
+                                                           int* __restrict__ out,
+                                                           int* __restrict__ cursor,
+                                                           long long capacity,
+                                                           long long* __restrict__ d_total,
+                                                           int* status)
+{
+    __shared__ long long s_warp[32];
+    __shared__ int s_in[kScanTile];
+    long long carry = 0;
+    for (int base = 0; base < n; base += kScanTile) {
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int j = base + i * kScanThreads + threadIdx.x;
+            s_in[i * kScanThreads + threadIdx.x] = j < n ? in[j] : 0;
+        }
+        __syncthreads();
+        long long loc[kScanItems];
+        long long sum = 0;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            loc[i] = sum;
+            sum += s_in[threadIdx.x * kScanItems + i];
+        }
+        long long total;
+        const long long e = block_scan_excl(sum, s_warp, total) + carry;
+        // results back through shared memory for coalesced stores (values clamped to int)
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const long long v = e + loc[i];
+            s_in[threadIdx.x * kScanItems + i] = (int)(v < capacity ? v : capacity);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int j = base + i * kScanThreads + threadIdx.x;
+            if (j < n) {
+                const int v = s_in[i * kScanThreads + threadIdx.x];
+                out[j] = v;
+                if (cursor) cursor[j] = v;
+            }
+        }
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[n] = (int)(carry < capacity ? carry : capacity);
+        if (d_total) *d_total = carry;
+        if (status && carry > capacity) set_status(status, PS_ERR_CAPACITY);
+    }
+}
+
 cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long long capacity,
                            long long* part, long long* d_total, int* status, cudaStream_t st)
 {
+    if (n <= kScanOneMax) {
+        k_scan_one<<<1, kScanThreads, 0, st>>>(in, n, out, cursor, capacity, d_total, status);
+        return cudaGetLastError();
+    }
     const int nparts = scan_tiles(n > 0 ? n : 1);
     k_scan_sums<<<nparts, kScanThreads, 0, st>>>(in, n, part);
     k_scan_parts<<<1, kScanThreads, 0, st>>>(part, nparts);
@@ -219,10 +282,9 @@ cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long lon
 }
 
 // 2./4. one thread per (record, tile) pair ----------------------------------------
-__device__ __forceinline__ int pair_record(const int* __restrict__ off, int R, int i)
+__device__ __forceinline__ int pair_record(const int* __restrict__ off, int lo, int hi, int i)
 {
-    // last r with off[r] <= i (off is non-decreasing, off[0] = 0)
-    int lo = 0, hi = R - 1;
+    // last r in [lo, hi] with off[r] <= i (off is non-decreasing, off[lo] <= i)
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(&off[mid]) <= i) lo = mid; else hi = mid - 1;
@@ -230,17 +292,36 @@ __device__ __forceinline__ int pair_record(const int* __restrict__ off, int R, i
     return lo;
 }
 
+// Pairs base .. base + blockDim.x - 1 of a block belong to records s_rng[0] ..
+// s_rng[1]: two threads search the whole record range once, the others only
+// that narrow range.
+__device__ __forceinline__ void block_record_range(const int* __restrict__ off, int R, int E,
+                                                   int base, int* s_rng)
+{
+    if (threadIdx.x < 2) {
+        const int i = threadIdx.x == 0 ? base : min(base + (int)blockDim.x, E) - 1;
+        s_rng[threadIdx.x] = pair_record(off, 0, R - 1, i);
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) k_pair_count(const int* __restrict__ rec_off, int R,
                                                      const int4* __restrict__ rec_info,
                                                      int* __restrict__ tile_cnt)
 {
+    __shared__ int s_rng[2];
     const int E = __ldg(&rec_off[R]);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E; i += gridDim.x * blockDim.x) {
-        const int r = pair_record(rec_off, R, i);
-        const int4 info = __ldg(&rec_info[r]);
-        const int j = i - __ldg(&rec_off[r]);
-        const int t = info.x + (j / info.y) * info.z + (j % info.y);
-        atomicAdd(&tile_cnt[t], 1);
+    for (int base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
+        block_record_range(rec_off, R, E, base, s_rng);
+        const int i = base + threadIdx.x;
+        if (i < E) {
+            const int r = pair_record(rec_off, s_rng[0], s_rng[1], i);
+            const int4 info = __ldg(&rec_info[r]);
+            const int j = i - __ldg(&rec_off[r]);
+            const int t = info.x + (j / info.y) * info.z + (j % info.y);
+            atomicAdd(&tile_cnt[t], 1);
+        }
+        __syncthreads();
     }
 }
 
@@ -250,16 +331,22 @@ __global__ void __launch_bounds__(256) k_pair_scatter(const int* __restrict__ re
                                                        int* __restrict__ cursor,
                                                        int* __restrict__ ent_tmp)
 {
+    __shared__ int s_rng[2];
     const int E = __ldg(&rec_off[R]);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E; i += gridDim.x * blockDim.x) {
-        const int r = pair_record(rec_off, R, i);
-        const int4 info = __ldg(&rec_info[r]);
-        const int j = i - __ldg(&rec_off[r]);
-        const int t = info.x + (j / info.y) * info.z + (j % info.y);
-        const int pos = atomicAdd(&cursor[t], 1);
-        // tile_ptr is clamped to the capacity: positions past it belong to lists
-        // that did not fit and are dropped (the status word says so)
-        if (pos < __ldg(&tile_ptr[t + 1])) ent_tmp[pos] = r;
+    for (int base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
+        block_record_range(rec_off, R, E, base, s_rng);
+        const int i = base + threadIdx.x;
+        if (i < E) {
+            const int r = pair_record(rec_off, s_rng[0], s_rng[1], i);
+            const int4 info = __ldg(&rec_info[r]);
+            const int j = i - __ldg(&rec_off[r]);
+            const int t = info.x + (j / info.y) * info.z + (j % info.y);
+            const int pos = atomicAdd(&cursor[t], 1);
+            // tile_ptr is clamped to the capacity: positions past it belong to lists
+            // that did not fit and are dropped (the status word says so)
+            if (pos < __ldg(&tile_ptr[t + 1])) ent_tmp[pos] = r;
+        }
+        __syncthreads();
     }
 }
 
@@ -302,6 +389,32 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __rest
         if (lane < n) tile_ent[b + lane] = (int)(unsigned)(v & 0xffffffffu);
         return;
     }
+    if (n <= 64) {
+        // element lane in v0, element lane + 32 in v1
+        unsigned long long v0 = sort_key(key, ent_tmp[b + lane]);
+        unsigned long long v1 = lane + 32 < n ? sort_key(key, ent_tmp[b + lane + 32]) : ~0ull;
+#pragma unroll
+        for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                if (j == 32) {           // partners in the same lane (k = 64: ascending)
+                    const unsigned long long lo = v0 < v1 ? v0 : v1, hi = v0 < v1 ? v1 : v0;
+                    v0 = lo; v1 = hi;
+                } else {
+                    const unsigned long long o0 = __shfl_xor_sync(0xffffffffu, v0, j);
+                    const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, v1, j);
+                    const bool lower = (lane & j) == 0;
+                    const bool up0 = (lane & k) == 0;
+                    const bool up1 = ((lane + 32) & k) == 0;
+                    v0 = (lower == up0) ? (v0 < o0 ? v0 : o0) : (v0 < o0 ? o0 : v0);
+                    v1 = (lower == up1) ? (v1 < o1 ? v1 : o1) : (v1 < o1 ? o1 : v1);
+                }
+            }
+        }
+        tile_ent[b + lane] = (int)(unsigned)(v0 & 0xffffffffu);
+        if (lane + 32 < n) tile_ent[b + lane + 32] = (int)(unsigned)(v1 & 0xffffffffu);
+        return;
+    }
     unsigned long long* s = s_warp_keys + (size_t)w * kWarpSortCap;
     int N = 64;
     while (N < n) N <<= 1;
@@ -324,16 +437,39 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __rest
 }
 
 // Long lists: one CTA per tile (tiles with at most kWarpSortCap entries return at once).
-__global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr,
+__device__ void sort_long_list(const int* __restrict__ ent_tmp, const float* __restrict__ key,
+                               int* __restrict__ tile_ent, int b, int n, unsigned long long* s);
+
+// Blocks stride over the tiles 256 at a time: each thread checks one list
+// length, the long lists found are sorted one after the other by the block.
+__global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr, int n_tiles,
                                                const int* __restrict__ ent_tmp,
                                                const float* __restrict__ key,
                                                int* __restrict__ tile_ent)
 {
     __shared__ unsigned long long s[kSortCap];
-    const int t = blockIdx.x;
-    const int b = tile_ptr[t], e = tile_ptr[t + 1];
-    const int n = e - b;
-    if (n <= kWarpSortCap) return;
+    __shared__ int s_list[256];
+    __shared__ int s_cnt;
+    for (int t0 = blockIdx.x * 256; t0 < n_tiles; t0 += gridDim.x * 256) {
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const int t = t0 + threadIdx.x;
+        if (t < n_tiles && tile_ptr[t + 1] - tile_ptr[t] > kWarpSortCap)
+            s_list[atomicAdd(&s_cnt, 1)] = t;
+        __syncthreads();
+        const int cnt = s_cnt;
+        for (int q = 0; q < cnt; ++q) {
+            const int tt = s_list[q];
+            const int b = tile_ptr[tt];
+            sort_long_list(ent_tmp, key, tile_ent, b, tile_ptr[tt + 1] - b, s);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void sort_long_list(const int* __restrict__ ent_tmp, const float* __restrict__ key,
+                               int* __restrict__ tile_ent, int b, int n, unsigned long long* s)
+{
     const int tid = threadIdx.x, NT = blockDim.x;
     if (n <= kSortCap) {
         int N = 2;
@@ -355,6 +491,7 @@ __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr,
             }
         }
         for (int i = tid; i < n; i += NT) tile_ent[b + i] = (int)(unsigned)(s[i] & 0xffffffffu);
+        __syncthreads();    // the block's next list reuses s
         return;
     }
     // rank of each element = number of smaller keys (keys are unique)
@@ -372,6 +509,7 @@ __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr,
         }
         if (i < n) tile_ent[b + rank] = (int)(unsigned)(ki & 0xffffffffu);
     }
+    __syncthreads();    // the block's next list reuses s
 }
 
 }  // namespace
@@ -429,7 +567,9 @@ extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, c
         k_sort_warp<<<(frame->n_tiles + kSortWarps - 1) / kSortWarps, kSortWarps * 32, dyn, st>>>(
             tile_ptr, frame->n_tiles, w.ent_tmp, key, tile_ent);
         PS_LAUNCH_CHECK();
-        k_sort<<<frame->n_tiles, 256, 0, st>>>(tile_ptr, w.ent_tmp, key, tile_ent);
+        const int sort_blocks = (frame->n_tiles + 255) / 256;
+        k_sort<<<sort_blocks < kSortBlocks ? sort_blocks : kSortBlocks, 256, 0, st>>>(
+            tile_ptr, frame->n_tiles, w.ent_tmp, key, tile_ent);
         PS_LAUNCH_CHECK();
     }
     return PS_OK;

@@ -425,6 +425,72 @@ def surface_init_nn(room: Room, n: int, seed: int, scale: float = 0.5) -> Planes
     return p
 
 
+def sphere_init(room: Room, n: int, seed: int, radius: float = 0.05) -> Planes:
+    """The sphere initialisation of the ablation in Sec. 4.3: n planes with all
+    radii = radius on the bounding sphere of the scene (centre of the room box,
+    radius half its diagonal), normals pointing to the centre, random rotation
+    about the normal."""
+    rng = np.random.default_rng(seed)
+    size = np.asarray(room.size, np.float64)
+    centre = size / 2.0
+    R = 0.5 * float(np.linalg.norm(size))
+    u = random_unit_vectors(rng, n)
+    centers = centre + R * u
+    nrm = -u
+    a = random_unit_vectors(rng, n)
+    vx = a - (a * nrm).sum(1, keepdims=True) * nrm
+    vx /= np.linalg.norm(vx, axis=1, keepdims=True)
+    vy = np.cross(nrm, vx)
+    quat = np.array([quat_from_frame(vx[k], vy[k], nrm[k]) for k in range(n)])
+    radii = np.full((n, 4), radius)
+    return Planes(centers.astype(np.float32), quat.astype(np.float32), radii.astype(np.float32))
+
+
+def mono_init(room: Room, depth: np.ndarray, normal: np.ndarray, n: int, seed: int,
+              scale_sigma: float = 0.03, depth_sigma: float = 0.01, normal_sigma_deg: float = 8.0,
+              radius_scale: float = 0.5) -> Planes:
+    """Stand-in for the monocular-depth initialisation of Sec. 3.1: the
+    ground-truth depth and camera-frame normal maps [V, H, W] / [V, H, W, 3] are
+    degraded like a monocular prediction (a per-view depth scale error
+    N(1, scale_sigma), per-pixel relative depth noise N(0, depth_sigma), normals
+    tilted by N(0, normal_sigma_deg) degrees about a random axis), n random
+    valid pixels are back-projected to plane centres, each plane's normal is the
+    degraded normal (so its rotation comes from the coarse geometry), its
+    in-plane rotation is random, and every radius is radius_scale x the distance
+    to the nearest other centre."""
+    rng = np.random.default_rng(seed)
+    cams = room.cams
+    V = depth.shape[0]
+    scale = rng.normal(1.0, scale_sigma, size=V)
+    valid = np.argwhere(depth > 0)
+    pick = valid[rng.integers(0, len(valid), size=n)]
+    v, j, i = pick[:, 0], pick[:, 1], pick[:, 2]
+    intr = cams.intr.astype(np.float64)[v]
+    z = depth[v, j, i].astype(np.float64) * scale[v] * (1.0 + rng.normal(0.0, depth_sigma, size=n))
+    pc = np.stack([(i + 0.5 - intr[:, 2]) / intr[:, 0] * z, (j + 0.5 - intr[:, 3]) / intr[:, 1] * z, z], 1)
+    Rt = cams.w2c.astype(np.float64)[v]
+    R, t = Rt[:, :, :3], Rt[:, :, 3]
+    centers = np.einsum("nji,nj->ni", R, pc - t)
+    nc = normal[v, j, i].astype(np.float64)
+    ax = random_unit_vectors(rng, n)
+    ang = np.deg2rad(rng.normal(0.0, normal_sigma_deg, size=n))
+    # Rodrigues rotation of the camera-frame normal about a random axis
+    cosa, sina = np.cos(ang)[:, None], np.sin(ang)[:, None]
+    nc = nc * cosa + np.cross(ax, nc) * sina + ax * (ax * nc).sum(1, keepdims=True) * (1.0 - cosa)
+    nw = np.einsum("nji,nj->ni", R, nc)
+    nw /= np.linalg.norm(nw, axis=1, keepdims=True)
+    a = random_unit_vectors(rng, n)
+    vx = a - (a * nw).sum(1, keepdims=True) * nw
+    vx /= np.linalg.norm(vx, axis=1, keepdims=True)
+    vy = np.cross(nw, vx)
+    quat = np.array([quat_from_frame(vx[k], vy[k], nw[k]) for k in range(n)])
+    from scipy.spatial import cKDTree
+    d, _ = cKDTree(centers).query(centers, k=2)
+    r = np.clip(radius_scale * d[:, 1], 0.02, 2.0)
+    radii = np.repeat(r[:, None], 4, axis=1)
+    return Planes(centers.astype(np.float32), quat.astype(np.float32), radii.astype(np.float32))
+
+
 def batch_rooms(n_rooms: int, seed0: int = 1000, planes=(200, 3000), views=(16, 96),
                 sizes=((240, 320), (360, 480), (480, 640)), n_rect: int = 2000) -> list:
     """n_rooms independent rooms as large_room, each with its own plane count
