@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--batched", type=int, default=32,
                     help="rooms in the batched-vs-plain time-to-2cm comparison (0: skip)")
     ap.add_argument("--batched-iters", type=int, default=5000)
+    ap.add_argument("--ablation", type=int, default=0,
+                    help="rooms of the Sec. 4.3 ablation (init variants, single radii); 0 = skip")
     ap.add_argument("--profile-case", action="store_true",
                     help="for ncu: set up, warm up 3 steps, run one step inside a profiler range, exit")
     return ap.parse_args()
@@ -416,6 +418,11 @@ def run_ours(args, rank, world, local_rank):
         del wl
         torch.cuda.empty_cache()
         result["time_to_2cm_vs_plain"] = run_batched(args, rank, device)
+    if args.ablation > 0:
+        from paper_2412_03451_gb300 import ablation
+        torch.cuda.empty_cache()
+        result["ablation_time_to_2cm"] = ablation.run(n_rooms=args.ablation, iters=args.batched_iters,
+                                                      seed0=7000 + 100 * rank, device=device)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         from paper_2412_03451_gb300 import scenes as S
         room = S.large_room(1000 + rank, n_rect=N_GT, n_views=N_VIEWS, H=H, W=W, f=F)

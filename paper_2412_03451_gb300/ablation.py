@@ -1,0 +1,72 @@
+"""Ablations of Sec. 4.3 on synthetic rooms, measured as time to a mean depth
+error of 2 cm (the paper's Tab. 3 measures reconstruction quality on ScanNetV2,
+which is not available here; the mechanisms are the same).
+
+Variants (each fits every room on its own, 64 views of 640x480, 8 views per
+step, Eq. 10 schedule from iteration 0):
+  plain         random surface points, random orientation, radii 0.5 x the
+                nearest-centre distance (the start used by the throughput runs);
+  mono          the Sec. 3.1 start: points and normals of a degraded (monocular-
+                like) depth/normal map, radii 0.5 x nearest-centre distance;
+  sphere        the Sec. 4.3 sphere start: radii 0.05 m on the scene's bounding
+                sphere, normals to its centre;
+  single_radii  the mono start with one radius per axis (Sec. 4.3, PS_SINGLE_RADII).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import batch as BT
+from . import binding as B
+from . import scenes as S
+
+VARIANTS = ("plain", "mono", "sphere", "single_radii")
+
+
+def _gt_maps(ss: BT.SceneSet, i: int):
+    c = ss.rooms[i].cams
+    off = int(ss.gt_off[i][0])
+    m = c.V * c.H * c.W
+    d = ss.gt_depth[off:off + m].view(c.V, c.H, c.W).cpu().numpy()
+    n = ss.gt_normal[off:off + m].view(c.V, c.H, c.W, 3).cpu().numpy()
+    return d, n
+
+
+def make_inits(name: str, rooms, ss_ref: BT.SceneSet, planes: int, seed0: int):
+    out = []
+    for i, room in enumerate(rooms):
+        seed = seed0 + 100 + i
+        if name == "plain":
+            out.append(S.surface_init_nn(room, planes, seed))
+        elif name in ("mono", "single_radii"):
+            d, n = _gt_maps(ss_ref, i)
+            out.append(S.mono_init(room, d, n, planes, seed))
+        elif name == "sphere":
+            out.append(S.sphere_init(room, planes, seed))
+        else:
+            raise ValueError(name)
+    return out
+
+
+def run(n_rooms: int = 4, planes: int = 2000, iters: int = 5000, seed0: int = 7000,
+        variants=VARIANTS, device="cuda", tile=(16, 16)) -> dict:
+    rooms = [S.large_room(seed0 + i, n_rect=2000, n_views=64) for i in range(n_rooms)]
+    ss_ref = BT.SceneSet(rooms, [S.surface_init_nn(r, planes, seed0 + 100 + i)
+                                 for i, r in enumerate(rooms)], device=device, tile=tile)
+    out = {"rooms": n_rooms, "planes": planes, "iteration_cap": iters,
+           "what": "per variant: rooms fitted one by one; GPU seconds, iterations to mean depth "
+                   "error <= 2 cm (None: not reached), error at the end"}
+    for name in variants:
+        inits = make_inits(name, rooms, ss_ref, planes, seed0)
+        flags = B.PS_SINGLE_RADII if name == "single_radii" else 0
+        ss = BT.SceneSet(rooms, inits, device=device, tile=tile, flags=flags)
+        res = [BT.fit_until(ss, [s], max_iters=iters) for s in range(n_rooms)]
+        its = [r["done_at"][0][0] if r["done_at"][0] is not None else None for r in res]
+        out[name] = {"gpu_s": round(sum(r["gpu_ms"] for r in res) / 1e3, 3),
+                     "iterations_to_2cm": its,
+                     "reached": sum(i is not None for i in its),
+                     "final_err_m": [round(float(r["err"][0]), 4) for r in res]}
+        del ss
+        torch.cuda.empty_cache()
+    return out
