@@ -98,6 +98,7 @@ def parse():
     ap.add_argument("--batched-iters", type=int, default=5000)
     ap.add_argument("--ablation", type=int, default=0,
                     help="rooms of the Sec. 4.3 ablation (init variants, single radii); 0 = skip")
+    ap.add_argument("--ablation-variants", default="plain,mono,sphere,single_radii,split,split_low")
     ap.add_argument("--profile-case", action="store_true",
                     help="for ncu: set up, warm up 3 steps, run one step inside a profiler range, exit")
     return ap.parse_args()
@@ -422,7 +423,8 @@ def run_ours(args, rank, world, local_rank):
         from paper_2412_03451_gb300 import ablation
         torch.cuda.empty_cache()
         result["ablation_time_to_2cm"] = ablation.run(n_rooms=args.ablation, iters=args.batched_iters,
-                                                      seed0=7000 + 100 * rank, device=device)
+                                                      seed0=7000 + 100 * rank, device=device,
+                                                      variants=tuple(args.ablation_variants.split(",")))
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         from paper_2412_03451_gb300 import scenes as S
         room = S.large_room(1000 + rank, n_rect=N_GT, n_views=N_VIEWS, H=H, W=W, f=F)

@@ -302,6 +302,41 @@ ps_status ps_count_pairs(const ps_frame* frame, const ps_settings* settings, con
 ps_status ps_step_advance(ps_step_state* d_state, const ps_step_state* d_sched, int n_sched,
                           int* d_iter, ps_stream stream);
 
+/* Plane splitting, part 1 (Sec. 3.3 "Plane Splitting", App. A.2): adds this
+   step's radius gradients to a running sum.  g_radii [P][4] (device, the
+   gradient of the loss with respect to r^x+, r^x-, r^y+, r^y-), acc [P][2]
+   (device, updated): acc[p][0] += s_p (|g[p][0]| + |g[p][1]|) / 2 and
+   acc[p][1] += s_p (|g[p][2]| + |g[p][3]|) / 2, with s_p = plane_scale[p]
+   (device [P]) or, if plane_scale is NULL, the value scale.  The scale turns the
+   summed loss of Eq. 14 into the per-pixel mean the split threshold refers to
+   (1 / supervised pixels of the plane's scene in this step).  PS_ERR_ARG on bad
+   sizes or NULL pointers. */
+ps_status ps_radii_grad_accum(const float* g_radii, const float* plane_scale, float scale,
+                              int n_planes, float* acc, ps_stream stream);
+
+/* Plane splitting, part 2: every plane p whose mean radius gradient on an axis,
+   acc[p][axis] / n_iter, exceeds tau is cut in two along the other axis (the
+   larger axis if both exceed it): X -> a +X half and a -X half (centres
+   p + r^x+/2 v^x and p - r^x-/2 v^x, X radii r^x+/2 and r^x-/2 on both sides,
+   Y radii kept), Y likewise with v^y; the rotation is kept.  Planes whose
+   quaternion is zero or non-finite are kept.
+   params, m, v: device flat buffers of P planes, [center P x 3 | quat P x 4 |
+   radii P x 4] (m, v: Adam moments in the same layout, may be NULL).
+   plane_ptr [S+1] (device): CSR of the planes of each scene.  Output: the same
+   layout for P' = P + splits planes in params_out (and m_out, v_out if not
+   NULL; capacity planes of room each): scene s occupies plane_ptr_out[s] ..
+   plane_ptr_out[s+1] - 1, its planes in their old order (a split plane's +half
+   in its slot) followed by the -halves in the order of their parents.  Moments
+   are copied for kept planes and zeroed for both halves.  split_rank [P+1]
+   (device, written): split planes before each plane, [P] = their number;
+   *d_count (device) = P'.  If P' > capacity only split_rank and *d_count are
+   written.  One CTA; deterministic.  Host-side PS_ERR_ARG on bad sizes. */
+ps_status ps_split_planes(const float* params, const float* m, const float* v, int n_scenes,
+                          const int* plane_ptr, int n_planes, const float* acc, int n_iter,
+                          float tau, float* params_out, float* m_out, float* v_out,
+                          int* plane_ptr_out, int capacity, int* split_rank, int* d_count,
+                          ps_stream stream);
+
 /* ps_adam_step with the step's bias corrections read from d_state (device). */
 ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v, long long n,
                              float lr, float b1, float b2, float eps,

@@ -51,6 +51,9 @@ class SceneSet:
             del r
         self.gt_depth = torch.cat(gd)
         self.gt_normal = torch.cat(gn)
+        # supervised pixels (ground-truth depth > 0) of every view of every scene
+        self.sup = [(d.view(room.cams.V, -1) > 0).sum(1).cpu().numpy()
+                    for d, room in zip(gd, rooms)]
         self.n_batches = max(int(math.ceil(room.cams.V / self.vps)) for room in rooms)
 
     def batch_views(self, b):
@@ -63,9 +66,22 @@ class SceneSet:
         r = np.concatenate([p.radii for p in self.inits])
         return SP.planes_to_flat(c, q, r, self.device)
 
-    def renderer(self, scenes=None, M=30, capacity=None):
+    def split_scales(self, scenes, Ks):
+        """Per camera batch, the per-plane factor [sum Ks] (device) that turns the
+        summed loss of a step into a sum of per-view pixel means over the step's
+        views of the plane's scene (views_per_step / supervised pixels of those
+        views): the loss one view contributes when each iteration fits one view."""
+        out = []
+        for b in range(self.n_batches):
+            vi = self.batch_views(b)
+            per = [self.vps / max(int(self.sup[s][vi[s]].sum()), 1) for s in scenes]
+            out.append(torch.tensor(np.repeat(per, Ks), dtype=torch.float32, device=self.device))
+        return out
+
+    def renderer(self, scenes=None, M=30, capacity=None, Ks=None):
         """A renderer for the step frame of the given scenes (all by default),
-        with every camera batch planned on the device."""
+        with every camera batch planned on the device.  Ks overrides the scenes'
+        plane counts (after splitting)."""
         scenes = list(range(self.S)) if scenes is None else list(scenes)
         H, W, sov = [], [], []
         for i, s in enumerate(scenes):
@@ -73,7 +89,7 @@ class SceneSet:
             H += [c.H] * self.vps
             W += [c.W] * self.vps
             sov += [i] * self.vps
-        K = [self.K[s] for s in scenes]
+        K = [self.K[s] for s in scenes] if Ks is None else list(Ks)
         pptr = np.concatenate([[0], np.cumsum(K)]).astype(np.int32)
         r = SP.Renderer(H, W, sov, pptr, tile=self.tile, M=M, capacity=capacity,
                         device=self.device, flags=self.flags)
@@ -113,18 +129,48 @@ def join_flat(flats, Ks):
     return torch.cat(cs + qs + rs).contiguous()
 
 
+def _split_round(ss, fit, active, Ks, n_iter, tau, params, moments):
+    """Sec. 3.3 plane splitting of the active scenes on the device; updates
+    params, moments and returns the new plane counts and the number of splits."""
+    P = int(sum(Ks))
+    dev = fit.flat.device
+    ptr = torch.tensor(np.concatenate([[0], np.cumsum(Ks)]), dtype=torch.int32, device=dev)
+    cap = 2 * P
+    out = torch.empty(11 * cap, device=dev)
+    mo, vo = torch.empty_like(out), torch.empty_like(out)
+    ptr_o = torch.empty_like(ptr)
+    rank = torch.empty(P + 1, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    B.ps_split_planes(fit.flat, fit.m, fit.v, ptr, fit.split_acc, n_iter, tau, out, mo, vo,
+                      ptr_o, cap, rank, cnt)
+    Pn = int(cnt.item())
+    new_ptr = ptr_o.cpu().numpy()
+    nK = [int(new_ptr[i + 1] - new_ptr[i]) for i in range(len(active))]
+    for s, f, m, v in zip(active, split_flat(out[:11 * Pn], nK), split_flat(mo[:11 * Pn], nK),
+                          split_flat(vo[:11 * Pn], nK)):
+        params[s] = f.clone()
+        moments[s] = (m.clone(), v.clone())
+    return nK, Pn - P
+
+
 def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_headroom=1.6,
-              use_graphs=True, compact=True, lam_offset=0):
+              use_graphs=True, compact=True, lam_offset=0, split_every=0, split_tau=0.2):
     """Fits the given scenes together (one launch per kernel per step) until
     every scene's mean depth error is <= threshold or max_iters.  With compact,
     scenes that reach the threshold leave the batch: the remaining scenes'
     parameters and Adam moments move to a smaller frame whose graphs are
-    captured again.  Returns per-scene iterations and errors and the GPU time
-    spent stepping (CUDA events; frame rebuilds and the per-rotation
-    convergence check are outside the timed region)."""
+    captured again.  With split_every > 0, planes are split every split_every
+    iterations (Sec. 3.3; threshold split_tau on the radius gradient of the
+    per-view mean loss) and the frame is rebuilt with the new plane counts.  Returns
+    per-scene iterations and errors and the GPU time spent stepping (CUDA
+    events; frame rebuilds, splitting and the per-rotation convergence check are
+    outside the timed region)."""
     scenes = list(scenes)
     S = len(scenes)
     nb = ss.n_batches
+    Kd = {s: ss.K[s] for s in scenes}
+    splits = 0
+    next_split = split_every if split_every > 0 else None
     params = {s: f for s, f in zip(scenes, split_flat(ss.flat_for(scenes), [ss.K[s] for s in scenes]))}
     moments = {s: (torch.zeros_like(params[s]), torch.zeros_like(params[s])) for s in scenes}
     latest = {}                     # (scene, view) -> (sum |D - D*|, count)
@@ -134,14 +180,17 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
     ite = 0
     active = list(scenes)
     while ite < max_iters and active:
-        Ks = [ss.K[s] for s in active]
-        r = ss.renderer(active)
+        Ks = [Kd[s] for s in active]
+        r = ss.renderer(active, Ks=Ks)
         flat = join_flat([params[s] for s in active], Ks)
         fit = SP.Fitter(r, flat)
         fit.m.copy_(join_flat([moments[s][0] for s in active], Ks))
         fit.v.copy_(join_flat([moments[s][1] for s in active], Ks))
         fit.ite = ite
         fit.lam_offset = lam_offset
+        acc_from = ite
+        if next_split is not None:
+            fit.enable_split(ss.split_scales(active, Ks))
         need = 0
         for b in range(nb):
             r.select(b)
@@ -164,7 +213,7 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
                     sums.append(fit.replay(b))
                 else:
                     r.select(b)
-                    sums.append(fit.step(ss.gt_depth, ss.gt_normal).clone())
+                    sums.append(fit.step(ss.gt_depth, ss.gt_normal, batch=b).clone())
                 ite += 1
             e1.record()
             torch.cuda.synchronize()
@@ -197,9 +246,18 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
                     params[s] = f.clone()
                 active = []
                 break
+            elif next_split is not None and ite >= next_split:
+                nK, n_split = _split_round(ss, fit, active, Ks, ite - acc_from, split_tau,
+                                           params, moments)
+                splits += n_split
+                for s, k in zip(active, nK):
+                    Kd[s] = k
+                next_split += split_every
+                rebuild = True
         if not rebuild and active:
             for s, f in zip(active, split_flat(fit.flat, Ks)):
                 params[s] = f.clone()
         del fit, r
     return {"iterations": ite, "gpu_ms": spent_ms, "done_at": [done_at[s] for s in scenes],
-            "err": [err[s] for s in scenes], "params": [params[s] for s in scenes]}
+            "err": [err[s] for s in scenes], "params": [params[s] for s in scenes],
+            "planes": [Kd[s] for s in scenes], "splits": splits}

@@ -28,7 +28,7 @@ EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin
            "ps_count_pairs", "ps_step_advance", "ps_adam_step_state", "ps_gemm_bf16",
            "ps_seed_im2col", "ps_seed_col2im", "ps_seed_relu_bwd", "ps_seed_transpose",
            "ps_seed_colsum", "ps_seed_pool", "ps_seed_pool_bwd", "ps_seed_loss", "ps_cast_bf16",
-           "ps_status_string", "ps_version")
+           "ps_radii_grad_accum", "ps_split_planes", "ps_status_string", "ps_version")
 
 
 class PsSettings(ctypes.Structure):
@@ -115,6 +115,8 @@ def load():
             "ps_seed_loss": ([P, P, I, I, P, P, P], I),
             "ps_cast_bf16": ([P, I, I, I, P, P], I),
             "ps_adam_step_state": ([P, P, P, P, LL, F, F, F, F, P, F, P], I),
+            "ps_radii_grad_accum": ([P, P, F, I, P, P], I),
+            "ps_split_planes": ([P, P, P, I, P, I, P, I, F, P, P, P, P, I, P, P, P], I),
             "ps_status_string": ([I], ctypes.c_char_p),
             "ps_version": ([], I),
         }
@@ -313,6 +315,24 @@ def ps_adam_step_state(param, grad, m, v, lr, b1, b2, eps, d_state, clamp_min=fl
     _check(load().ps_adam_step_state(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
                                      float(lr), float(b1), float(b2), float(eps), _ptr(d_state),
                                      float(clamp_min), _stream(stream)), "ps_adam_step_state")
+
+
+def ps_radii_grad_accum(g_radii, acc, scale=1.0, plane_scale=None, stream=None):
+    """acc [P, 2] += per-axis mean |dL/dr| of g_radii [P, 4] (times scale or plane_scale[P])."""
+    n = acc.numel() // 2
+    _check(load().ps_radii_grad_accum(_ptr(g_radii), _ptr(plane_scale), float(scale), int(n),
+                                      _ptr(acc), _stream(stream)), "ps_radii_grad_accum")
+
+
+def ps_split_planes(params, m, v, plane_ptr, acc, n_iter, tau, params_out, m_out, v_out,
+                    plane_ptr_out, capacity, split_rank, d_count, stream=None):
+    """Sec. 3.3 plane splitting on device buffers (see ps.h)."""
+    n_planes = acc.numel() // 2
+    _check(load().ps_split_planes(_ptr(params), _ptr(m), _ptr(v), int(plane_ptr.numel() - 1),
+                                  _ptr(plane_ptr), int(n_planes), _ptr(acc), int(n_iter), float(tau),
+                                  _ptr(params_out), _ptr(m_out), _ptr(v_out), _ptr(plane_ptr_out),
+                                  int(capacity), _ptr(split_rank), _ptr(d_count), _stream(stream)),
+           "ps_split_planes")
 
 
 def ps_gemm_bf16(A, B, bias, C32, C16, relu=False, accumulate=False, err=None, stream=None):

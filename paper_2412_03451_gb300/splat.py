@@ -247,6 +247,22 @@ class Fitter:
         # Eq. 10 is evaluated at ite + lam_offset: a fit from a good initialisation
         # may skip the schedule's blurry start (Adam's step count is unaffected)
         self.lam_offset = 0
+        # plane splitting (Sec. 3.3): running per-axis radius-gradient sums [P, 2] and, per
+        # camera batch, the per-plane scale to the per-pixel mean loss
+        self.split_acc = None
+        self.split_scale = None
+
+    def enable_split(self, plane_scales):
+        """Accumulates the radius gradients of every step for plane splitting;
+        plane_scales[b] ([P] device) is used at steps of camera batch b."""
+        self.split_acc = torch.zeros((self.r.P, 2), device=self.flat.device)
+        self.split_scale = list(plane_scales)
+
+    def _accumulate(self, batch):
+        if self.split_acc is not None:
+            P = self.r.P
+            B.ps_radii_grad_accum(self.grad[7 * P:], self.split_acc,
+                                  plane_scale=self.split_scale[batch or 0])
 
     # -- captured CUDA graphs ------------------------------------------------------
     def enable_graphs(self, n_iters: int, batches, gt_slices):
@@ -271,26 +287,30 @@ class Fitter:
         # warm the library's per-device launch caches outside capture
         with torch.cuda.stream(stream):
             r.select(batches[0])
-            saved = (self.flat.clone(), self.m.clone(), self.v.clone(), int(self.d_iter.item()))
-            self._graph_body(*gt_slices[0], self.graph_sums[0])
+            saved = (self.flat.clone(), self.m.clone(), self.v.clone(), int(self.d_iter.item()),
+                     None if self.split_acc is None else self.split_acc.clone())
+            self._graph_body(*gt_slices[0], self.graph_sums[0], batches[0])
             torch.cuda.synchronize()
             self.flat.copy_(saved[0]); self.m.copy_(saved[1]); self.v.copy_(saved[2])
             self.d_iter.fill_(saved[3])
+            if saved[4] is not None:
+                self.split_acc.copy_(saved[4])
         for i, (b, (gd, gn)) in enumerate(zip(batches, gt_slices)):
             r.select(b)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
-                self._graph_body(gd, gn, self.graph_sums[i])
+                self._graph_body(gd, gn, self.graph_sums[i], b)
             self.graphs.append(g)
         torch.cuda.synchronize()
 
-    def _graph_body(self, gt_depth, gt_normal, view_sums):
+    def _graph_body(self, gt_depth, gt_normal, view_sums, batch=0):
         r = self.r
         P = r.P
         B.ps_step_advance(self.d_state, self.d_sched, self.n_sched, self.d_iter)
         r.project_bin(self.flat, 1.0, d_state=self.d_state)
         self.grad.zero_()
         r.fused(self.flat, self.grad, gt_depth, gt_normal, view_sums=view_sums)
+        self._accumulate(batch)
         B.ps_adam_step_state(self.flat[:7 * P], self.grad[:7 * P], self.m[:7 * P], self.v[:7 * P],
                              self.lr, self.b1, self.b2, self.eps, self.d_state)
         B.ps_adam_step_state(self.flat[7 * P:], self.grad[7 * P:], self.m[7 * P:], self.v[7 * P:],
@@ -302,7 +322,7 @@ class Fitter:
         self.ite += 1
         return self.graph_sums[batch_index]
 
-    def step(self, gt_depth, gt_normal, lam=None, marks=None):
+    def step(self, gt_depth, gt_normal, lam=None, marks=None, batch=None):
         """One iteration.  If marks is a list, CUDA events are recorded on the
         current stream after each stage as (name, event) pairs."""
         def mark(tag):
@@ -327,6 +347,7 @@ class Fitter:
             mark("loss")
             r.backward(self.flat, self.grad)
             mark("splat_bwd")
+        self._accumulate(batch)
         P = r.P
         t = self.ite + 1
         B.ps_adam_step(self.flat[:7 * P], self.grad[:7 * P], self.m[:7 * P], self.v[:7 * P],
