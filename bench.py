@@ -98,7 +98,7 @@ def parse():
     ap.add_argument("--batched-iters", type=int, default=5000)
     ap.add_argument("--ablation", type=int, default=0,
                     help="rooms of the Sec. 4.3 ablation (init variants, single radii); 0 = skip")
-    ap.add_argument("--ablation-variants", default="plain,mono,sphere,single_radii,split,split_low")
+    ap.add_argument("--ablation-variants", default="plain,mono,sphere,single_radii,split,split_low,gaussian")
     ap.add_argument("--profile-case", action="store_true",
                     help="for ncu: set up, warm up 3 steps, run one step inside a profiler range, exit")
     return ap.parse_args()

@@ -70,6 +70,13 @@ typedef enum {
                               "w/o Double Radii" ablation, Sec. 4.3) */
 #define PS_HARD 2          /* hard rectangle: w = 1 inside (m >= 0), else filtered.
                               Used to ray-cast ground truth; no backward. */
+#define PS_GAUSSIAN 4      /* the Gaussian splatting weight of Eq. 5 instead of Eq. 7-9
+                              (the ablation of Sec. 3.2): w = exp(-(P_X^2 / s_X^2 +
+                              P_Y^2 / s_Y^2) / 2), s_X = r^x+ if P_X > 0 else r^x-
+                              (likewise Y); lambda is not used; delta must be
+                              sqrt(2 ln(1 / w_min)) and multiplies the radii in the
+                              binning (the margin of d_state is not used).  Not with
+                              PS_HARD. */
 
 #define PS_MAX_M 64        /* largest supported M (nearest intersections per ray) */
 
@@ -87,10 +94,11 @@ typedef struct ps_settings {
     float lambda;          /* Eq. 10 value for this iteration */
     float w_min;           /* filter threshold, 1e-4 (Sec. 3.2) */
     float z_near, z_far;   /* valid intersection depth range (0.01, 100 m) */
-    double delta;          /* binning margin: 2 sigmoid(-5 lambda delta) = w_min; 0 with PS_HARD */
+    double delta;          /* binning margin: 2 sigmoid(-5 lambda delta) = w_min; 0 with PS_HARD;
+                              the radius factor sqrt(2 ln(1 / w_min)) with PS_GAUSSIAN */
     int M;                 /* nearest intersections kept per ray, 30 (Sec. 3.2), <= PS_MAX_M */
     int tile_w, tile_h;    /* tile shape in pixels: 8x8, 16x16 or 32x8 */
-    int flags;             /* PS_SINGLE_RADII | PS_HARD */
+    int flags;             /* PS_SINGLE_RADII | PS_HARD | PS_GAUSSIAN */
     float a_cos, a_l1n, a_depth;  /* Eq. 14 weights: alpha_1 = 5, alpha_1 = 5, alpha_2 = 1 */
     int reserved;
     const ps_step_state* d_state; /* optional (device): if not NULL, lambda and delta are read

@@ -113,12 +113,23 @@ def filter_margin(lam: float, w_min: float = W_MIN) -> float:
     return math.log((1.0 - h) / h) / (5.0 * lam)
 
 
+def gauss_extent(w_min: float = W_MIN) -> float:
+    """kappa with exp(-kappa^2 / 2) = w_min: the Gaussian weight of Eq. 5 passes the
+    filter only within kappa sigma of the centre on each axis."""
+    return math.sqrt(2.0 * math.log(1.0 / w_min))
+
+
+def _flags(single_radii, gaussian) -> int:
+    return (1 if single_radii else 0) | (4 if gaussian else 0)
+
+
 # --------------------------------------------------------------------------
 # Binning (per-plane screen bounds) and tile lists.
 
 def bin_records(center, quat, radii, w2c, intr, H, W, tile_w, tile_h, delta,
-                z_near=Z_NEAR, z_far=Z_FAR, single_radii=False):
-    """Tile rectangle and depth key of every (view, plane); see ps_oracle.c."""
+                z_near=Z_NEAR, z_far=Z_FAR, single_radii=False, gaussian=False):
+    """Tile rectangle and depth key of every (view, plane); see ps_oracle.c.
+    With gaussian, delta multiplies the radii (gauss_extent) instead of widening them."""
     c, q, r = _f64(center), _f64(quat), _f64(radii)
     Rt, K_ = _f64(w2c).reshape(-1, 12), _f64(intr).reshape(-1, 4)
     K, V = c.shape[0], Rt.shape[0]
@@ -127,7 +138,7 @@ def bin_records(center, quat, radii, w2c, intr, H, W, tile_w, tile_h, delta,
     key32 = np.zeros((V, K), dtype=np.float32)
     _load().or_bin_records(K, V, _ptr(c), _ptr(q), _ptr(r), _ptr(Rt), _ptr(K_), H, W,
                            tile_w, tile_h, float(delta), float(z_near), float(z_far),
-                           int(bool(single_radii)), _ptr(rect), _ptr(key), _ptr(key32))
+                           _flags(single_radii, gaussian), _ptr(rect), _ptr(key), _ptr(key32))
     return rect, key, key32
 
 
@@ -165,7 +176,7 @@ def tile_lists(rect, key32, H, W, tile_w, tile_h):
 
 def render(center, quat, radii, w2c, intr, H, W, lam, M=M_DEFAULT, w_min=W_MIN,
            z_near=Z_NEAR, z_far=Z_FAR, single_radii=False, eta=1e-6, tol_d=1e-4,
-           tol_n=1e-5, rows=None):
+           tol_n=1e-5, rows=None, gaussian=False):
     """Brute-force forward of Eq. 11-13.  Returns a dict of per-pixel arrays:
     depth [V,H,W], normal [V,H,W,3], alpha, n_sel, n_cand, ill (see ps_oracle.c)."""
     c, q, r = _f64(center), _f64(quat), _f64(radii)
@@ -178,7 +189,7 @@ def render(center, quat, radii, w2c, intr, H, W, lam, M=M_DEFAULT, w_min=W_MIN,
     delta = filter_margin(lam, w_min)
     _load().or_render(K, V, _ptr(c), _ptr(q), _ptr(r), _ptr(Rt), _ptr(K_), H, W,
                       float(lam), float(w_min), float(z_near), float(z_far), int(M),
-                      int(bool(single_radii)), float(delta), float(eta), float(tol_d),
+                      _flags(single_radii, gaussian), float(delta), float(eta), float(tol_d),
                       float(tol_n), int(row0), int(row1),
                       _ptr(out["depth"]), _ptr(out["normal"]), _ptr(out["alpha"]),
                       _ptr(out["n_sel"]), _ptr(out["n_cand"]), _ptr(out["ill"]))
@@ -200,7 +211,7 @@ def loss(depth, normal, gt_depth, gt_normal, a_cos=ALPHA1, a_l1n=ALPHA1, a_depth
 
 
 def backward(center, quat, radii, w2c, intr, H, W, lam, dLdD, dLdN, M=M_DEFAULT,
-             w_min=W_MIN, z_near=Z_NEAR, z_far=Z_FAR, single_radii=False):
+             w_min=W_MIN, z_near=Z_NEAR, z_far=Z_FAR, single_radii=False, gaussian=False):
     """Analytic FP64 gradient of sum(dLdD * D + dLdN . N) with respect to the
     plane centers [K,3], quaternions [K,4] and radii [K,4]."""
     c, q, r = _f64(center), _f64(quat), _f64(radii)
@@ -210,7 +221,7 @@ def backward(center, quat, radii, w2c, intr, H, W, lam, dLdD, dLdN, M=M_DEFAULT,
     gc, gq, gr = np.zeros((K, 3)), np.zeros((K, 4)), np.zeros((K, 4))
     _load().or_backward(K, V, _ptr(c), _ptr(q), _ptr(r), _ptr(Rt), _ptr(K_), H, W,
                         float(lam), float(w_min), float(z_near), float(z_far), int(M),
-                        int(bool(single_radii)), _ptr(gD), _ptr(gN), _ptr(gc), _ptr(gq),
+                        _flags(single_radii, gaussian), _ptr(gD), _ptr(gN), _ptr(gc), _ptr(gq),
                         _ptr(gr))
     return gc, gq, gr
 

@@ -97,9 +97,14 @@ typedef struct {
     double pcn;                      /* |p_c|, scale of the FP32 noise model */
 } plane_cam;
 
+/* flags: bit 0 = single radii (Sec. 4.3), bit 2 = Gaussian weight (Eq. 5).   */
+#define OR_SINGLE 1
+#define OR_GAUSS 4
+
 static void plane_to_cam(const double* p, const double* q, const double* r,
-                         const double* Rt, int single_radii, plane_cam* o)
+                         const double* Rt, int flags, plane_cam* o)
 {
+    const int single_radii = flags & OR_SINGLE;
     o->ok = plane_axes(q, &o->qs, o->qhat, o->vx, o->vy, o->n);
     if (!o->ok) return;
     double tmp[3];
@@ -117,7 +122,10 @@ static void plane_to_cam(const double* p, const double* q, const double* r,
 /* Binning specification (screen bounds of the expanded rectangle).          */
 /* The rectangle is widened by delta on every side; delta is the margin at   */
 /* which 2 sigmoid(-5 lambda delta) = w_min, so every (pixel, plane) pair    */
-/* that survives the w >= w_min filter of Sec. 3.2 lies inside it.  The quad */
+/* that survives the w >= w_min filter of Sec. 3.2 lies inside it.  With the */
+/* Gaussian weight of Eq. 5 (flag bit 2) every radius is multiplied by delta */
+/* instead, delta = sqrt(2 ln(1 / w_min)): exp(-q/2) >= w_min needs          */
+/* |P_X| <= delta sigma_X and |P_Y| <= delta sigma_Y.  The quad */
 /* is clipped to z >= z_near, projected, and its pixel bbox, padded by one   */
 /* pixel and clamped to the image, is divided by the tile size.  The depth   */
 /* key is the smallest z of the clipped polygon: a lower bound on the depth  */
@@ -127,8 +135,9 @@ void or_bin_records(int K, int V,
                     const double* center, const double* quat, const double* radii,
                     const double* w2c, const double* intr, int H, int W,
                     int tile_w, int tile_h, double delta, double z_near, double z_far,
-                    int single_radii, int* rect, double* key, float* key_f32)
+                    int flags, int* rect, double* key, float* key_f32)
 {
+    const int gauss = flags & OR_GAUSS;
     for (int v = 0; v < V; ++v) {
         const double* Rt = w2c + 12 * v;
         double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
@@ -139,10 +148,12 @@ void or_bin_records(int K, int V,
             key[(long)v * K + k] = INFINITY;
             key_f32[(long)v * K + k] = INFINITY;
             plane_cam pc;
-            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, single_radii, &pc);
+            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, flags, &pc);
             if (!pc.ok) continue;
-            double exp_ = pc.r[0] + delta, exm = pc.r[1] + delta;
-            double eyp = pc.r[2] + delta, eym = pc.r[3] + delta;
+            double exp_ = gauss ? pc.r[0] * delta : pc.r[0] + delta;
+            double exm = gauss ? pc.r[1] * delta : pc.r[1] + delta;
+            double eyp = gauss ? pc.r[2] * delta : pc.r[2] + delta;
+            double eym = gauss ? pc.r[3] * delta : pc.r[3] + delta;
             /* corners in order (+x,+y), (-x,+y), (-x,-y), (+x,-y) */
             double ax[4] = {exp_, -exm, -exm, exp_};
             double ay[4] = {eyp, eyp, -eym, -eym};
@@ -210,6 +221,7 @@ typedef struct {
     double t, w;      /* depth and weight */
     double m, mX, mY; /* margins r - |P| */
     double PX, PY, den;
+    double sX, sY;    /* radius on the side of P_X, P_Y (Eq. 7-8; Eq. 5 scales) */
     int branchX;      /* 1 if w came from the X side (w_X < w_Y) */
 } cand;
 
@@ -223,9 +235,12 @@ static double side_weight(double lambda, double m)
 }
 
 /* Evaluates plane pc at ray d.  Returns 1 and fills c when t is in range and
-   the ray is not grazing; the weight filter is applied by the caller.       */
+   the ray is not grazing; the weight filter is applied by the caller.
+   With gauss, w is the Gaussian of Eq. 5 in the plane's frame, its scales
+   the one-sided radii: w = exp(-(P_X^2 / sigma_X^2 + P_Y^2 / sigma_Y^2) / 2)
+   with sigma_X = r^x+ if P_X > 0 else r^x- (likewise Y).                    */
 static int eval_pair(const plane_cam* pc, const double d[3], double lambda,
-                     double z_near, double z_far, cand* c)
+                     double z_near, double z_far, int gauss, cand* c)
 {
     double den = dot3(d, pc->nc);
     if (!(fabs(den) > 1e-6)) return 0;
@@ -236,8 +251,16 @@ static int eval_pair(const plane_cam* pc, const double d[3], double lambda,
     double rX = PX > 0.0 ? pc->r[0] : pc->r[1];
     double rY = PY > 0.0 ? pc->r[2] : pc->r[3];
     double mX = rX - fabs(PX), mY = rY - fabs(PY);
-    double wX = side_weight(lambda, mX), wY = side_weight(lambda, mY);
     c->t = t; c->den = den; c->PX = PX; c->PY = PY; c->mX = mX; c->mY = mY;
+    c->sX = rX; c->sY = rY;
+    if (gauss) {
+        double qf = (PX / rX) * (PX / rX) + (PY / rY) * (PY / rY);
+        c->w = exp(-0.5 * qf);
+        c->branchX = 0;
+        c->m = 0.0;
+        return 1;
+    }
+    double wX = side_weight(lambda, mX), wY = side_weight(lambda, mY);
     if (wX < wY) { c->w = wX; c->branchX = 1; c->m = mX; }
     else { c->w = wY; c->branchX = 0; c->m = mY; }
     return 1;
@@ -254,7 +277,7 @@ static int cand_cmp(const void* a, const void* b)
 
 typedef struct {
     double lambda, w_min, z_near, z_far;
-    int M, single_radii;
+    int M, flags;
 } or_set;
 
 /* Gathers, filters and sorts the candidates of one pixel.  Returns the
@@ -269,9 +292,13 @@ static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], cons
     for (int k = 0; k < K; ++k) {
         if (!pcs[k].ok) continue;
         cand c;
-        if (!eval_pair(&pcs[k], d, S->lambda, S->z_near, S->z_far, &c)) continue;
+        if (!eval_pair(&pcs[k], d, S->lambda, S->z_near, S->z_far, S->flags & OR_GAUSS, &c)) continue;
         double eps = eta * (1.0 + fabs(c.t) + pcs[k].pcn);
-        if (fabs(c.m + delta) < eps) *near_filter = 1;
+        if (S->flags & OR_GAUSS) {
+            /* w moves by about w (|P_X| / sigma_X^2 + |P_Y| / sigma_Y^2) eps */
+            double dw = c.w * (fabs(c.PX) / (c.sX * c.sX) + fabs(c.PY) / (c.sY * c.sY)) * eps;
+            if (fabs(c.w - S->w_min) < dw) *near_filter = 1;
+        } else if (fabs(c.m + delta) < eps) *near_filter = 1;
         if (fabs(c.t - S->z_near) < eps || fabs(c.t - S->z_far) < eps) *near_filter = 1;
         if (!(c.w >= S->w_min)) continue;
         c.k = k;
@@ -294,16 +321,17 @@ static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], cons
 /* Rows [row0, row1) of every view are rendered; others are left untouched.  */
 void or_render(int K, int V, const double* center, const double* quat, const double* radii,
                const double* w2c, const double* intr, int H, int W,
-               double lambda, double w_min, double z_near, double z_far, int M, int single_radii,
+               double lambda, double w_min, double z_near, double z_far, int M, int flags,
                double delta, double eta, double tol_d, double tol_n, int row0, int row1,
                double* depth, double* normal, double* alpha, int* n_sel, int* n_cand, int* ill)
 {
-    or_set S = {lambda, w_min, z_near, z_far, M, single_radii};
+    or_set S = {lambda, w_min, z_near, z_far, M, flags};
+    const int gauss = flags & OR_GAUSS;
     plane_cam* pcs = (plane_cam*)malloc(sizeof(plane_cam) * (size_t)(K > 0 ? K : 1));
     for (int v = 0; v < V; ++v) {
         const double* Rt = w2c + 12 * v;
         for (int k = 0; k < K; ++k)
-            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, single_radii, &pcs[k]);
+            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, flags, &pcs[k]);
         double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
         double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
 #pragma omp parallel
@@ -342,7 +370,10 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
                         double w = cs[s].w, t = cs[s].t, m = cs[s].m;
                         double e = eta * (1.0 + fabs(t) + p->pcn);
                         double slope;
-                        if (fabs(m) < e) slope = 2.5 * lambda;      /* max of dw/dm near the kink */
+                        if (gauss)                                  /* |dw/dP| summed over both axes */
+                            slope = w * (fabs(cs[s].PX) / (cs[s].sX * cs[s].sX) +
+                                         fabs(cs[s].PY) / (cs[s].sY * cs[s].sY));
+                        else if (fabs(m) < e) slope = 2.5 * lambda; /* max of dw/dm near the kink */
                         else if (m < 0.0) {
                             double sg = sigmoid(5.0 * lambda * m);
                             slope = 10.0 * lambda * sg * (1.0 - sg);
@@ -350,7 +381,10 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
                         double gD = Tj[s] * (t - Ab);
                         sD += fabs(gD) * slope * e;
                         for (int c = 0; c < 3; ++c) sN[c] += fabs(Tj[s] * (p->nc[c] - Bb[c])) * slope * e;
-                        if (Tj[s] > 0.0 && m < e) {
+                        if (gauss) {
+                            /* the side (sigma) choice of P_X or P_Y flips near 0 */
+                            if (Tj[s] > 0.0 && (fabs(cs[s].PX) < e || fabs(cs[s].PY) < e)) bad_grad = 1;
+                        } else if (Tj[s] > 0.0 && m < e) {
                             if (fabs(cs[s].mX - cs[s].mY) < e) bad_grad = 1;
                             double Pa = cs[s].branchX ? cs[s].PX : cs[s].PY;
                             if (fabs(Pa) < e) bad_grad = 1;
@@ -427,11 +461,12 @@ double or_loss(int V, int H, int W, const double* depth, const double* normal,
 /* the world parameters.  The clamp min(1, .) has derivative 0 at m >= 0.   */
 void or_backward(int K, int V, const double* center, const double* quat, const double* radii,
                  const double* w2c, const double* intr, int H, int W,
-                 double lambda, double w_min, double z_near, double z_far, int M, int single_radii,
+                 double lambda, double w_min, double z_near, double z_far, int M, int flags,
                  const double* dLdD, const double* dLdN,
                  double* g_center, double* g_quat, double* g_radii)
 {
-    or_set S = {lambda, w_min, z_near, z_far, M, single_radii};
+    or_set S = {lambda, w_min, z_near, z_far, M, flags};
+    const int single_radii = flags & OR_SINGLE, gauss = flags & OR_GAUSS;
     memset(g_center, 0, sizeof(double) * 3 * (size_t)K);
     memset(g_quat, 0, sizeof(double) * 4 * (size_t)K);
     memset(g_radii, 0, sizeof(double) * 4 * (size_t)K);
@@ -445,7 +480,7 @@ void or_backward(int K, int V, const double* center, const double* quat, const d
     for (int v = 0; v < V; ++v) {
         const double* Rt = w2c + 12 * v;
         for (int k = 0; k < K; ++k)
-            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, single_radii, &pcs[k]);
+            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, flags, &pcs[k]);
         double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
         double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
 #pragma omp parallel
@@ -489,7 +524,14 @@ void or_backward(int K, int V, const double* center, const double* quat, const d
                         }
                         double gr[4] = {0, 0, 0, 0};
                         double gPX = 0.0, gPY = 0.0;
-                        if (c->branchX) {
+                        if (gauss) {
+                            /* Eq. 5: w = exp(-(P_X^2 / s_X^2 + P_Y^2 / s_Y^2) / 2) */
+                            double sx2 = c->sX * c->sX, sy2 = c->sY * c->sY;
+                            gPX = -gw * w * c->PX / sx2;
+                            gPY = -gw * w * c->PY / sy2;
+                            gr[c->PX > 0.0 ? 0 : 1] += gw * w * c->PX * c->PX / (sx2 * c->sX);
+                            gr[c->PY > 0.0 ? 2 : 3] += gw * w * c->PY * c->PY / (sy2 * c->sY);
+                        } else if (c->branchX) {
                             /* m_X = r_X - |P_X| */
                             if (c->PX > 0.0) gr[0] += gm; else gr[1] += gm;
                             gPX = -gm * sgn(c->PX);

@@ -28,7 +28,8 @@ def rotation(q: np.ndarray) -> np.ndarray:
     """R(q / |q|) for quaternions [n, 4] in (w, x, y, z) order (Eq. 2-3);
     columns are v^x, v^y, n."""
     q = np.asarray(q, np.float64)
-    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    with np.errstate(invalid="ignore", divide="ignore"):    # zero rows give NaN axes
+        q = q / np.linalg.norm(q, axis=1, keepdims=True)
     w, x, y, z = q.T
     R = np.empty((len(q), 3, 3))
     R[:, 0, 0] = 1 - 2 * (y * y + z * z)

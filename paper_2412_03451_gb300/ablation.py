@@ -16,7 +16,9 @@ step, Eq. 10 schedule from iteration 0):
                 mean loss);
   split_low     the same with the threshold lowered to 0.005 (the printed 0.2
                 selects no plane on these rooms under this reading of the loss
-                scale; this variant exercises the mechanism).
+                scale; this variant exercises the mechanism);
+  gaussian      the mono start with the Gaussian weight of Eq. 5 instead of the
+                rectangle weight (Sec. 3.2, Fig. 4), the radii as its scales.
 """
 from __future__ import annotations
 
@@ -27,7 +29,7 @@ from . import batch as BT
 from . import binding as B
 from . import scenes as S
 
-VARIANTS = ("plain", "mono", "sphere", "single_radii", "split", "split_low")
+VARIANTS = ("plain", "mono", "sphere", "single_radii", "split", "split_low", "gaussian")
 
 
 def _gt_maps(ss: BT.SceneSet, i: int):
@@ -45,7 +47,7 @@ def make_inits(name: str, rooms, ss_ref: BT.SceneSet, planes: int, seed0: int):
         seed = seed0 + 100 + i
         if name == "plain":
             out.append(S.surface_init_nn(room, planes, seed))
-        elif name in ("mono", "single_radii", "split", "split_low"):
+        elif name in ("mono", "single_radii", "split", "split_low", "gaussian"):
             d, n = _gt_maps(ss_ref, i)
             out.append(S.mono_init(room, d, n, planes, seed))
         elif name == "sphere":
@@ -65,7 +67,7 @@ def run(n_rooms: int = 4, planes: int = 2000, iters: int = 5000, seed0: int = 70
                    "error <= 2 cm (None: not reached), error at the end"}
     for name in variants:
         inits = make_inits(name, rooms, ss_ref, planes, seed0)
-        flags = B.PS_SINGLE_RADII if name == "single_radii" else 0
+        flags = {"single_radii": B.PS_SINGLE_RADII, "gaussian": B.PS_GAUSSIAN}.get(name, 0)
         ss = BT.SceneSet(rooms, inits, device=device, tile=tile, flags=flags)
         split = 1000 if name in ("split", "split_low") else 0
         tau = 0.005 if name == "split_low" else 0.2

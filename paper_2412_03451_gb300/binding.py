@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libps.so")
 PS_OK, PS_ERR_ARG, PS_ERR_CUDA, PS_ERR_CAPACITY, PS_ERR_TIMEOUT, PS_ERR_NONFINITE = range(6)
 PS_SINGLE_RADII = 1
 PS_HARD = 2
+PS_GAUSSIAN = 4
 PS_MAX_M = 64
 
 EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin_tiles",
@@ -210,6 +211,12 @@ def filter_margin(lam: float, w_min: float = 1e-4) -> float:
     """delta with 2 sigmoid(-5 lam delta) = w_min (Eq. 7-8 and the Sec. 3.2 filter)."""
     h = 0.5 * w_min
     return math.log((1.0 - h) / h) / (5.0 * lam)
+
+
+def gauss_extent(w_min: float = 1e-4) -> float:
+    """kappa with exp(-kappa^2 / 2) = w_min: with PS_GAUSSIAN the binning scales
+    every radius by kappa (the Eq. 5 weight passes the filter within kappa sigma)."""
+    return math.sqrt(2.0 * math.log(1.0 / w_min))
 
 
 def lambda_schedule(ite: int) -> float:

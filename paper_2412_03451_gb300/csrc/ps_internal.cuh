@@ -59,6 +59,10 @@ struct PairEval {
     float dv;          // d . v_c of the active side
     bool sideX;        // active side is X (m_X < m_Y); ties go to Y
     bool pos;          // P > 0 on the active side (selects r^+)
+    // both axes (used by the Gaussian weight of Eq. 5)
+    float X, Y;        // P_X, P_Y
+    float dvx, dvy;    // d . v^x_c, d . v^y_c
+    float sX, sY;      // radius on the side of P_X, P_Y
 };
 
 struct SplatConst {
@@ -67,6 +71,8 @@ struct SplatConst {
     float z_near, z_far;
     float reject;      // quick reject: margins below -reject cannot reach w_min
     int hard;          // PS_HARD
+    int gauss;         // PS_GAUSSIAN: the Eq. 5 weight
+    float kappa;       // Eq. 5: w >= w_min only within kappa radii of the centre on each axis
 };
 
 // Every operation is executed for every lane and the filter is applied at the
@@ -82,8 +88,18 @@ __device__ __forceinline__ bool eval_pair(const float4& n, const float4& vx, con
     const float dvy = fmaf(dx, vy.x, fmaf(dy, vy.y, vy.z));
     const float X = fmaf(t, dvx, -vx.w);
     const float Y = fmaf(t, dvy, -vy.w);
-    const float mX = (X > 0.f ? r.x : r.y) - fabsf(X);
-    const float mY = (Y > 0.f ? r.z : r.w) - fabsf(Y);
+    const float sXr = X > 0.f ? r.x : r.y, sYr = Y > 0.f ? r.z : r.w;
+    o.X = X; o.Y = Y; o.dvx = dvx; o.dvy = dvy; o.sX = sXr; o.sY = sYr;
+    if (c.gauss) {
+        // Eq. 5 in the plane's frame, the one-sided radii as the scales
+        const float ux = __fdividef(X, sXr), uy = __fdividef(Y, sYr);
+        const float w = __expf(-0.5f * (ux * ux + uy * uy));
+        o.t = t; o.w = w; o.m = 0.f; o.den = den;
+        o.sideX = false; o.P = Y; o.dv = dvy; o.pos = Y > 0.f;
+        return (fabsf(den) > 1e-6f) && (t > c.z_near && t < c.z_far) && (w >= c.w_min);
+    }
+    const float mX = sXr - fabsf(X);
+    const float mY = sYr - fabsf(Y);
     const bool sx = mX < mY;
     const float m = sx ? mX : mY;
     // w = min(1, 2 sigmoid(5 lambda m)); below the clamp 2 sigmoid(x) = 2 e^x / (1 + e^x)
@@ -135,10 +151,13 @@ __device__ __forceinline__ bool region_may_hit(const float4& n, const float4& vx
     }
     if (npos != 4 && nneg != 4) return true;       // d . n_c may vanish: no bound
     if (tmax < c.z_near * 0.99999f || tmin > c.z_far * 1.00001f) return false;
-    const float mx = c.reject + 1e-5f * (fabsf(xmin) + fabsf(xmax) + fabsf(tmax)) + 1e-6f;
-    const float my = c.reject + 1e-5f * (fabsf(ymin) + fabsf(ymax) + fabsf(tmax)) + 1e-6f;
-    if (xmax < -(r.y + mx) || xmin > r.x + mx) return false;
-    if (ymax < -(r.w + my) || ymin > r.z + my) return false;
+    // support: r + reject around the rectangle, or kappa r for the Eq. 5 weight
+    const float sc = c.gauss ? c.kappa : 1.f;
+    const float rej = c.gauss ? 0.f : c.reject;
+    const float mx = rej + 1e-5f * (fabsf(xmin) + fabsf(xmax) + fabsf(tmax)) + 1e-6f;
+    const float my = rej + 1e-5f * (fabsf(ymin) + fabsf(ymax) + fabsf(tmax)) + 1e-6f;
+    if (xmax < -(sc * r.y + mx) || xmin > sc * r.x + mx) return false;
+    if (ymax < -(sc * r.w + my) || ymin > sc * r.z + my) return false;
     return true;
 }
 

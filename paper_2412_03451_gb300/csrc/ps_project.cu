@@ -107,6 +107,7 @@ struct ProjArgs {
     double delta, z_near, z_far;
     const ps_step_state* d_state;
     int single_radii;
+    int gauss;              // PS_GAUSSIAN: radii scaled by delta instead of widened
     int tile_w, tile_h;
 };
 
@@ -171,8 +172,9 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
             vyc[i] = row3(R, i, vyw);
             nc[i] = row3(R, i, nw);
         }
-        const double delta = a.d_state ? __ldg(&a.d_state->delta) : a.delta;
-    const double r0 = rf[0], r1 = a.single_radii ? (double)rf[0] : (double)rf[1];
+        // the Gaussian extent does not depend on lambda: the schedule's margin is not used
+        const double delta = (a.d_state && !a.gauss) ? __ldg(&a.d_state->delta) : a.delta;
+        const double r0 = rf[0], r1 = a.single_radii ? (double)rf[0] : (double)rf[1];
         const double r2 = rf[2], r3 = a.single_radii ? (double)rf[2] : (double)rf[3];
 
         // record (rounded to f32)
@@ -184,9 +186,12 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
         out[11] = (float)ad(ad(ml(vyc[0], pc[0]), ml(vyc[1], pc[1])), ml(vyc[2], pc[2]));
         out[12] = (float)r0; out[13] = (float)r1; out[14] = (float)r2; out[15] = (float)r3;
 
-        // binning: widened quad, corners (+x,+y), (-x,+y), (-x,-y), (+x,-y)
-        const double exp_ = ad(r0, delta), exm = ad(r1, delta);
-        const double eyp = ad(r2, delta), eym = ad(r3, delta);
+        // binning: widened quad (Eq. 5 weight: scaled quad), corners (+x,+y), (-x,+y),
+        // (-x,-y), (+x,-y)
+        const double exp_ = a.gauss ? ml(r0, delta) : ad(r0, delta);
+        const double exm = a.gauss ? ml(r1, delta) : ad(r1, delta);
+        const double eyp = a.gauss ? ml(r2, delta) : ad(r2, delta);
+        const double eym = a.gauss ? ml(r3, delta) : ad(r3, delta);
         const double ax[4] = {exp_, -exm, -exm, exp_};
         const double ay[4] = {eyp, eyp, -eym, -eym};
         double C[4][3];
@@ -267,6 +272,7 @@ extern "C" ps_status ps_project_cull(const ps_planes* planes, const ps_frame* fr
     if (frame->n_views <= 0 || frame->max_K < 0) return PS_ERR_ARG;
     if (s->tile_w <= 0 || s->tile_h <= 0) return PS_ERR_ARG;
     if (!(s->delta >= 0.0) && !s->d_state) return PS_ERR_ARG;
+    if ((s->flags & PS_GAUSSIAN) && (!(s->delta > 0.0) || (s->flags & PS_HARD))) return PS_ERR_ARG;
     if (!(s->z_near > 0.f) || !(s->z_far > s->z_near)) return PS_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(rec) & 15) || (reinterpret_cast<uintptr_t>(rect) & 15))
         return PS_ERR_ARG;
@@ -279,6 +285,7 @@ extern "C" ps_status ps_project_cull(const ps_planes* planes, const ps_frame* fr
     a.delta = s->delta; a.z_near = (double)s->z_near; a.z_far = (double)s->z_far;
     a.d_state = s->d_state;
     a.single_radii = (s->flags & PS_SINGLE_RADII) ? 1 : 0;
+    a.gauss = (s->flags & PS_GAUSSIAN) ? 1 : 0;
     a.tile_w = s->tile_w; a.tile_h = s->tile_h;
     dim3 grid((frame->max_K + 127) / 128, frame->n_views);
     k_project<<<grid, 128, 0, st>>>(a);

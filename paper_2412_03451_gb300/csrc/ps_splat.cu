@@ -457,6 +457,29 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
                 B0 = fmaf(w, n.x, (1.f - w) * B0);
                 B1 = fmaf(w, n.y, (1.f - w) * B1);
                 B2 = fmaf(w, n.z, (1.f - w) * B2);
+                if (a.c.gauss) {
+                    // Eq. 5: w = exp(-(X^2 / sX^2 + Y^2 / sY^2) / 2):
+                    // dw/dX = -w X / sX^2, dw/dsX = w X^2 / sX^3 (likewise Y)
+                    const float ix = __fdividef(1.f, pe.sX), iy = __fdividef(1.f, pe.sY);
+                    const float gX = -gw * w * pe.X * ix * ix;
+                    const float gY = -gw * w * pe.Y * iy * iy;
+                    const float grX = -gX * pe.X * ix, grY = -gY * pe.Y * iy;
+                    // Eq. 6 in record form on both axes
+                    gt = fmaf(gX, pe.dvx, gt);
+                    gt = fmaf(gY, pe.dvy, gt);
+                    const float gvx = gX * t, gvy = gY * t;
+                    const float gs = gt / pe.den;
+                    const float gden = -gs * t;
+                    gnx = fmaf(gden, dx, gnx);
+                    gny = fmaf(gden, dy, gny);
+                    gnz = gnz + gden;
+                    gr[0] = gnx; gr[1] = gny; gr[2] = gnz; gr[3] = gs;
+                    gr[4] = gvx * dx; gr[5] = gvx * dy; gr[6] = gvx; gr[7] = -gX;
+                    gr[8] = gvy * dx; gr[9] = gvy * dy; gr[10] = gvy; gr[11] = -gY;
+                    const bool px = pe.X > 0.f, py = pe.Y > 0.f;
+                    gr[12] = px ? grX : 0.f; gr[13] = px ? 0.f : grX;
+                    gr[14] = py ? grY : 0.f; gr[15] = py ? 0.f : grY;
+                } else {
                 // Eq. 7-9: w = 2 sigmoid(5 lambda m) below the clamp, dw/dm = 5 lambda w (1 - w/2)
                 const float gm = (pe.m < 0.f) ? gw * lam5 * w * (1.f - 0.5f * w) : 0.f;
                 // m = r_side - |P|: the radius gets gm, P gets -gm sgn(P)
@@ -484,6 +507,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) gr[12 + c] = (c == ridx) ? gm : 0.f;
+                }
             }
             // warp aggregation: for each distinct record among the active lanes, the
             // 16 gradient floats are summed over its lanes by a transpose-reduction
@@ -543,7 +567,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
 // lambda and the quick-reject margin from the device state (graph replay)
 __device__ __forceinline__ void load_state(SplatArgs& a)
 {
-    if (a.d_state && !a.c.hard) {
+    if (a.d_state && !a.c.hard && !a.c.gauss) {
         a.c.lam5 = 5.f * __ldg(&a.d_state->lambda);
         a.c.reject = (float)(__ldg(&a.d_state->delta) * 1.02 + 1e-6);
     }
@@ -870,6 +894,7 @@ ps_status check_common(const ps_frame* f, const ps_settings* s, const float* rec
     if (!(s->w_min > 0.f) || !(s->w_min < 1.f)) return PS_ERR_ARG;
     if (!(s->z_near > 0.f) || !(s->z_far > s->z_near)) return PS_ERR_ARG;
     if (!s->d_state && !(s->delta >= 0.0)) return PS_ERR_ARG;
+    if ((s->flags & PS_GAUSSIAN) && (!(s->delta > 0.0) || (s->flags & PS_HARD))) return PS_ERR_ARG;
     const int tw = s->tile_w, th = s->tile_h;
     if (!((tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8))) return PS_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(rec) & 15) return PS_ERR_ARG;
@@ -884,7 +909,9 @@ SplatConst make_const(const ps_settings* s)
     c.z_near = s->z_near;
     c.z_far = s->z_far;
     c.hard = (s->flags & PS_HARD) ? 1 : 0;
-    c.reject = c.hard ? 0.f : (float)(s->delta * 1.02 + 1e-6);
+    c.gauss = (s->flags & PS_GAUSSIAN) ? 1 : 0;
+    c.kappa = c.gauss ? (float)s->delta : 0.f;
+    c.reject = (c.hard || c.gauss) ? 0.f : (float)(s->delta * 1.02 + 1e-6);
     return c;
 }
 

@@ -125,7 +125,12 @@ class Renderer:
 
     def make_settings(self, lam, flags=None, d_state=None):
         fl = self.flags if flags is None else flags
-        delta = 0.0 if (fl & B.PS_HARD) else B.filter_margin(float(np.float32(lam)))
+        if fl & B.PS_HARD:
+            delta = 0.0
+        elif fl & B.PS_GAUSSIAN:
+            delta = B.gauss_extent()
+        else:
+            delta = B.filter_margin(float(np.float32(lam)))
         self.settings = B.make_settings(lam, delta, M=self.M, tile_w=self.tile[0],
                                         tile_h=self.tile[1], flags=fl, d_state=d_state)
         return self.settings

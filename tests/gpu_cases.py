@@ -54,17 +54,17 @@ def gpu_run(planes: S.Planes, cams: S.Cameras, lam: float, tile=(16, 16), M=30, 
     return out
 
 
-def oracle_bins(planes, cams, delta, tile):
+def oracle_bins(planes, cams, delta, tile, gaussian=False):
     rect, key, key32 = O.bin_records(planes.center, planes.quat, planes.radii, cams.w2c, cams.intr,
                                      cams.H, cams.W, tile[0], tile[1], delta, z_near=Z_NEAR32,
-                                     z_far=Z_FAR32)
+                                     z_far=Z_FAR32, gaussian=gaussian)
     ptr, ent = O.tile_lists(rect, key32, cams.H, cams.W, tile[0], tile[1])
     return rect, key32, ptr, ent
 
 
-def oracle_render(planes, cams, lam, M=30, rows=None):
+def oracle_render(planes, cams, lam, M=30, rows=None, gaussian=False):
     return O.render(planes.center, planes.quat, planes.radii, cams.w2c, cams.intr, cams.H, cams.W,
-                    f32(lam), M=M, z_near=Z_NEAR32, z_far=Z_FAR32, rows=rows)
+                    f32(lam), M=M, z_near=Z_NEAR32, z_far=Z_FAR32, rows=rows, gaussian=gaussian)
 
 
 def compare_maps(g, o, rows=None, tol_d=1e-4, tol_n=1e-5):
