@@ -8,8 +8,9 @@ the X axis (r^x+ and r^x-) exceeds 0.2 is split along its Y axis, and one whose
 average radius gradient on the Y axis exceeds 0.2 is split along its X axis.
 Readings used here (the paper gives no more):
   * "average radius gradient on the X axis" = the mean over the interval's
-    iterations of (|dL/dr^x+| + |dL/dr^x-|) / 2, with L the per-pixel mean of
-    Eq. 14 (the summed loss times 1 / supervised pixels);
+    iterations of (|dL/dr^x+| + |dL/dr^x-|) / 2, with L the loss of the
+    iteration's views, each view's Eq. 14 taken as a per-pixel mean (the
+    caller's scale: views per step / supervised pixels of the step's views);
   * "split along the Y axis" = cut along the line through the centre parallel
     to v^y: a +X half covering [0, r^x+] and a -X half covering [-r^x-, 0] of
     the plane's X range, each with both X radii equal to half its width, the Y
