@@ -154,7 +154,8 @@ def _split_round(ss, fit, active, Ks, n_iter, tau, params, moments):
 
 
 def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_headroom=1.6,
-              use_graphs=True, compact=True, lam_offset=0, split_every=0, split_tau=0.2):
+              use_graphs=True, compact=True, lam_offset=0, split_every=0, split_tau=0.2,
+              grow_margin=1.1, capacity=None):
     """Fits the given scenes together (one launch per kernel per step) until
     every scene's mean depth error is <= threshold or max_iters.  With compact,
     scenes that reach the threshold leave the batch: the remaining scenes'
@@ -164,12 +165,17 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
     per-view mean loss) and the frame is rebuilt with the new plane counts.  Returns
     per-scene iterations and errors and the GPU time spent stepping (CUDA
     events; frame rebuilds, splitting and the per-rotation convergence check are
-    outside the timed region)."""
+    outside the timed region).  Tile-list capacity: the frame is rebuilt with
+    capacity_headroom x the current need when the last step's need x grow_margin
+    passes the capacity (None: never), and a rotation whose lists overflowed
+    is redone from the state before it in a rebuilt frame; capacity sets the
+    smallest capacity of a new frame (default: 64 entries per tile)."""
     scenes = list(scenes)
     S = len(scenes)
     nb = ss.n_batches
     Kd = {s: ss.K[s] for s in scenes}
     splits = 0
+    overflows = 0
     next_split = split_every if split_every > 0 else None
     params = {s: f for s, f in zip(scenes, split_flat(ss.flat_for(scenes), [ss.K[s] for s in scenes]))}
     moments = {s: (torch.zeros_like(params[s]), torch.zeros_like(params[s])) for s in scenes}
@@ -181,7 +187,7 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
     active = list(scenes)
     while ite < max_iters and active:
         Ks = [Kd[s] for s in active]
-        r = ss.renderer(active, Ks=Ks)
+        r = ss.renderer(active, Ks=Ks, capacity=capacity)
         flat = join_flat([params[s] for s in active], Ks)
         fit = SP.Fitter(r, flat)
         fit.m.copy_(join_flat([moments[s][0] for s in active], Ks))
@@ -204,6 +210,9 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
         view_scene = np.repeat(np.arange(len(active)), ss.vps)
         rebuild = False
         while ite < max_iters and not rebuild:
+            # state before the rotation: a rotation whose tile lists overflowed is redone
+            snap = (fit.flat.clone(), fit.m.clone(), fit.v.clone(), ite,
+                    None if fit.split_acc is None else fit.split_acc.clone())
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -219,7 +228,26 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
             torch.cuda.synchronize()
             spent_ms += e0.elapsed_time(e1)
             if int(r.status.item()) & (1 << B.PS_ERR_CAPACITY):
-                raise RuntimeError("tile-list capacity overflow during the fit; raise the headroom")
+                # planes grew past the tile-list capacity: back to the state before the
+                # rotation, then a frame with capacity for the current planes
+                overflows += 1
+                if overflows > 8:
+                    raise RuntimeError("tile-list capacity overflow persists during the fit")
+                fit.flat.copy_(snap[0]); fit.m.copy_(snap[1]); fit.v.copy_(snap[2])
+                ite = snap[3]
+                for s, f, m, v in zip(active, split_flat(fit.flat, Ks), split_flat(fit.m, Ks),
+                                      split_flat(fit.v, Ks)):
+                    params[s] = f.clone()
+                    moments[s] = (m.clone(), v.clone())
+                rebuild = True
+                break
+            if grow_margin is not None and int(r.required.item()) * grow_margin > r.capacity:
+                # close to the capacity: rebuild with headroom before it overflows
+                for s, f, m, v in zip(active, split_flat(fit.flat, Ks), split_flat(fit.m, Ks),
+                                      split_flat(fit.v, Ks)):
+                    params[s] = f.clone()
+                    moments[s] = (m.clone(), v.clone())
+                rebuild = True
             vs = torch.stack(sums).cpu().numpy()          # [nb, V, 4]
             for b in range(nb):
                 vi = ss.batch_views(b)
@@ -260,4 +288,4 @@ def fit_until(ss: SceneSet, scenes, threshold=0.02, max_iters=3000, capacity_hea
         del fit, r
     return {"iterations": ite, "gpu_ms": spent_ms, "done_at": [done_at[s] for s in scenes],
             "err": [err[s] for s in scenes], "params": [params[s] for s in scenes],
-            "planes": [Kd[s] for s in scenes], "splits": splits}
+            "planes": [Kd[s] for s in scenes], "splits": splits, "overflows": overflows}
