@@ -57,12 +57,12 @@ FLOP_CAND, FLOP_COMP_FWD, FLOP_COMP_BWD = 27, 12, 66
 SM_COUNT, FP32_LANES = 152, 128
 # kernels of one step: schedule advance 1 (graphs); project 1; bin: record counts 1,
 # record scan, pair count 1, tile scan, scatter 1, sorts 2 (a scan is one launch up to
-# 65,536 elements, three beyond); fused splat 1 + chain 1 (split: fwd 1, loss 1, bwd 1 +
+# 49,152 elements, three beyond); fused splat 1 + chain 1 (split: fwd 1, loss 1, bwd 1 +
 # chain 1); Adam 2
 
 
 def scan_launches(n: int) -> int:
-    return 1 if n <= 65536 else 3  # one launch up to 8 scan tiles of 8,192
+    return 1 if n <= 48 * 1024 else 3
 
 
 def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:

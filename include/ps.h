@@ -345,6 +345,20 @@ ps_status ps_split_planes(const float* params, const float* m, const float* v, i
                           int* plane_ptr_out, int capacity, int* split_rank, int* d_count,
                           ps_stream stream);
 
+/* Plane merging (Sec. 3.3 "Plane Merge"): groups fitted planes into plane
+   instances.  Planes are taken by decreasing area (r^x+ + r^x-)(r^y+ + r^y-)
+   (ties: lower index first); each joins the first existing group whose first
+   plane has a normal within max_angle_deg of its own, up to sign (planes are
+   two-sided), and an offset within max_offset, or starts a new group.  Offset
+   = n . (p - scene_center) with n oriented like the group's normal.
+   params: device flat [center P x 3 | quat P x 4 | radii P x 4], n_planes <= 8192;
+   scene_center: host float[3].  Output (device): group_of[P] (group index, -1 for
+   a zero or non-finite quaternion), rep_of_group[P] (first plane of each group),
+   *d_groups = number of groups.  One CTA; deterministic. */
+ps_status ps_merge_planes(const float* params, int n_planes, const float* scene_center,
+                          float max_angle_deg, float max_offset, int* group_of, int* rep_of_group,
+                          int* d_groups, ps_stream stream);
+
 /* ps_adam_step with the step's bias corrections read from d_state (device). */
 ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v, long long n,
                              float lr, float b1, float b2, float eps,

@@ -1,4 +1,5 @@
-"""Plane splitting (Sec. 3.3 "Plane Splitting", App. A.2) in FP64.
+"""Plane splitting (Sec. 3.3 "Plane Splitting", App. A.2) and plane merging
+(Sec. 3.3 "Plane Merge") in FP64.
 
 TEST INFRASTRUCTURE ONLY: imported by tests; shares no code with the CUDA
 path.
@@ -21,6 +22,8 @@ Readings used here (the paper gives no more):
     in parent order; Adam moments of both halves restart at zero.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -115,3 +118,38 @@ def split_planes(center, quat, radii, plane_ptr, acc, n_iter, tau, m=None, v=Non
                 nc[j], nq[j], nr[j] = mc[i], mq[i], mr[i]
         out[name] = np.concatenate([nc.ravel(), nq.ravel(), nr.ravel()])
     return out
+
+
+def merge_planes(center, quat, radii, scene_center, max_angle_deg=25.0, max_offset=0.001):
+    """Plane merge (Sec. 3.3 "Plane Merge") read as a greedy grouping: planes by
+    decreasing area (ties: lower index), each joining the first group whose
+    first plane's normal is within max_angle_deg up to sign and whose offset
+    (distance from scene_center along the normal oriented like the group's) is
+    within max_offset.  Returns (group_of [P], first plane of each group)."""
+    c = np.asarray(center, np.float64)
+    r = np.asarray(radii, np.float64)
+    q = np.asarray(quat, np.float64)
+    P = len(c)
+    area = (r[:, 0] + r[:, 1]) * (r[:, 2] + r[:, 3])
+    area = np.where(area > 0, area, 0.0)
+    order = sorted(range(P), key=lambda i: (-area[i], i))
+    nq = (q * q).sum(1)
+    R = rotation(q)
+    cos_max = math.cos(math.radians(max_angle_deg))
+    group_of = np.full(P, -1, np.int64)
+    reps, rep_n, rep_o = [], [], []
+    for i in order:
+        if not (np.isfinite(nq[i]) and nq[i] > 0):
+            continue
+        n = R[i][:, 2]
+        off = float(n @ (c[i] - np.asarray(scene_center, np.float64)))
+        for g, (m, o) in enumerate(zip(rep_n, rep_o)):
+            d = float(n @ m)
+            s = 1.0 if d >= 0 else -1.0
+            if abs(d) >= cos_max and abs(s * off - o) < max_offset:
+                group_of[i] = g
+                break
+        else:
+            group_of[i] = len(reps)
+            reps.append(i); rep_n.append(n); rep_o.append(off)
+    return group_of, np.asarray(reps, np.int64)

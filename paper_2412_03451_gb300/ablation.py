@@ -2,6 +2,10 @@
 error of 2 cm (the paper's Tab. 3 measures reconstruction quality on ScanNetV2,
 which is not available here; the mechanisms are the same).
 
+Each fitted room is also scored like Sec. 4.1 (evaluate.py: Chamfer distance
+and F-score at 5 cm against the ground truth over every 8th view, and the plane
+instances after the merge of Sec. 3.3).
+
 Variants (each fits every room on its own, 64 views of 640x480, 8 views per
 step, Eq. 10 schedule from iteration 0):
   plain         random surface points, random orientation, radii 0.5 x the
@@ -26,6 +30,7 @@ import numpy as np
 import torch
 
 from . import batch as BT
+from . import evaluate as EV
 from . import binding as B
 from . import scenes as S
 
@@ -58,7 +63,7 @@ def make_inits(name: str, rooms, ss_ref: BT.SceneSet, planes: int, seed0: int):
 
 
 def run(n_rooms: int = 4, planes: int = 2000, iters: int = 5000, seed0: int = 7000,
-        variants=VARIANTS, device="cuda", tile=(16, 16)) -> dict:
+        variants=VARIANTS, device="cuda", tile=(16, 16), evaluate: bool = True) -> dict:
     rooms = [S.large_room(seed0 + i, n_rect=2000, n_views=64) for i in range(n_rooms)]
     ss_ref = BT.SceneSet(rooms, [S.surface_init_nn(r, planes, seed0 + 100 + i)
                                  for i, r in enumerate(rooms)], device=device, tile=tile)
@@ -74,11 +79,16 @@ def run(n_rooms: int = 4, planes: int = 2000, iters: int = 5000, seed0: int = 70
         res = [BT.fit_until(ss, [s], max_iters=iters, split_every=split, split_tau=tau)
                for s in range(n_rooms)]
         its = [r["done_at"][0][0] if r["done_at"][0] is not None else None for r in res]
+        ev = [EV.evaluate_fit(rooms[s], res[s]["params"][0], res[s]["planes"][0], flags=flags,
+                              seed=seed0 + s) for s in range(n_rooms)] if evaluate else []
         out[name] = {"gpu_s": round(sum(r["gpu_ms"] for r in res) / 1e3, 3),
                      "iterations_to_2cm": its,
                      "reached": sum(i is not None for i in its),
                      "final_err_m": [round(float(r["err"][0]), 4) for r in res],
                      "planes_at_end": [r["planes"][0] for r in res]}
+        if ev:
+            for key in ("chamfer_m", "fscore", "instances_0.1cm", "instances_0.1m", "gt_instances"):
+                out[name][key] = [e[key] for e in ev]
         del ss
         torch.cuda.empty_cache()
     return out

@@ -29,7 +29,8 @@ EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin
            "ps_count_pairs", "ps_step_advance", "ps_adam_step_state", "ps_gemm_bf16",
            "ps_seed_im2col", "ps_seed_col2im", "ps_seed_relu_bwd", "ps_seed_transpose",
            "ps_seed_colsum", "ps_seed_pool", "ps_seed_pool_bwd", "ps_seed_loss", "ps_cast_bf16",
-           "ps_radii_grad_accum", "ps_split_planes", "ps_status_string", "ps_version")
+           "ps_radii_grad_accum", "ps_split_planes", "ps_merge_planes", "ps_status_string",
+           "ps_version")
 
 
 class PsSettings(ctypes.Structure):
@@ -118,6 +119,7 @@ def load():
             "ps_adam_step_state": ([P, P, P, P, LL, F, F, F, F, P, F, P], I),
             "ps_radii_grad_accum": ([P, P, F, I, P, P], I),
             "ps_split_planes": ([P, P, P, I, P, I, P, I, F, P, P, P, P, I, P, P, P], I),
+            "ps_merge_planes": ([P, I, P, F, F, P, P, P, P], I),
             "ps_status_string": ([I], ctypes.c_char_p),
             "ps_version": ([], I),
         }
@@ -340,6 +342,15 @@ def ps_split_planes(params, m, v, plane_ptr, acc, n_iter, tau, params_out, m_out
                                   _ptr(params_out), _ptr(m_out), _ptr(v_out), _ptr(plane_ptr_out),
                                   int(capacity), _ptr(split_rank), _ptr(d_count), _stream(stream)),
            "ps_split_planes")
+
+
+def ps_merge_planes(params, n_planes, scene_center, max_angle_deg, max_offset, group_of,
+                    rep_of_group, d_groups, stream=None):
+    """Sec. 3.3 plane merge on device buffers (see ps.h); scene_center is 3 host floats."""
+    c = (ctypes.c_float * 3)(*[float(x) for x in scene_center])
+    _check(load().ps_merge_planes(_ptr(params), int(n_planes), c, float(max_angle_deg),
+                                  float(max_offset), _ptr(group_of), _ptr(rep_of_group),
+                                  _ptr(d_groups), _stream(stream)), "ps_merge_planes")
 
 
 def ps_gemm_bf16(A, B, bias, C32, C16, relu=False, accumulate=False, err=None, stream=None):

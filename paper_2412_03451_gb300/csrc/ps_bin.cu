@@ -208,11 +208,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
     }
 }
 
-// Arrays of up to kScanOneMax elements: one CTA walks the array in tiles of
-// kScanTile elements (coalesced loads into shared memory, kScanItems
-// consecutive elements per thread, a block scan, a running carry): one launch
-// instead of three.
-constexpr int kScanOneMax = 8 * kScanTile;
+// Arrays of up to kScanOneMax elements: one CTA holds the whole array in
+// shared memory (one coalesced load pass with every load in flight), each
+// thread scans a contiguous run, a block scan joins the runs, one coalesced
+// store pass: one launch instead of three.
+constexpr int kScanOneMax = 48 * 1024;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_one(const int* __restrict__ in, int n,
                                                            int* __restrict__ out,
@@ -221,48 +221,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_one(const int* __restrict
                                                            long long* __restrict__ d_total,
                                                            int* status)
 {
+    extern __shared__ int s_all[];
     __shared__ long long s_warp[32];
-    __shared__ int s_in[kScanTile];
-    long long carry = 0;
-    for (int base = 0; base < n; base += kScanTile) {
-#pragma unroll
-        for (int i = 0; i < kScanItems; ++i) {
-            const int j = base + i * kScanThreads + threadIdx.x;
-            s_in[i * kScanThreads + threadIdx.x] = j < n ? in[j] : 0;
-        }
-        __syncthreads();
-        long long loc[kScanItems];
-        long long sum = 0;
-#pragma unroll
-        for (int i = 0; i < kScanItems; ++i) {
-            loc[i] = sum;
-            sum += s_in[threadIdx.x * kScanItems + i];
-        }
-        long long total;
-        const long long e = block_scan_excl(sum, s_warp, total) + carry;
-        // results back through shared memory for coalesced stores (values clamped to int)
-#pragma unroll
-        for (int i = 0; i < kScanItems; ++i) {
-            const long long v = e + loc[i];
-            s_in[threadIdx.x * kScanItems + i] = (int)(v < capacity ? v : capacity);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < kScanItems; ++i) {
-            const int j = base + i * kScanThreads + threadIdx.x;
-            if (j < n) {
-                const int v = s_in[i * kScanThreads + threadIdx.x];
-                out[j] = v;
-                if (cursor) cursor[j] = v;
-            }
-        }
-        carry += total;
-        __syncthreads();
+    for (int j = threadIdx.x; j < n; j += kScanThreads) s_all[j] = in[j];
+    __syncthreads();
+    const int per = (n + kScanThreads - 1) / kScanThreads;
+    const int b = min((int)threadIdx.x * per, n), e = min(b + per, n);
+    long long sum = 0;
+    for (int j = b; j < e; ++j) sum += s_all[j];
+    long long total;
+    long long v = block_scan_excl(sum, s_warp, total);
+    for (int j = b; j < e; ++j) {
+        const int x = s_all[j];
+        s_all[j] = (int)(v < capacity ? v : capacity);
+        v += x;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += kScanThreads) {
+        const int x = s_all[j];
+        out[j] = x;
+        if (cursor) cursor[j] = x;
     }
     if (threadIdx.x == 0) {
-        out[n] = (int)(carry < capacity ? carry : capacity);
-        if (d_total) *d_total = carry;
-        if (status && carry > capacity) set_status(status, PS_ERR_CAPACITY);
+        out[n] = (int)(total < capacity ? total : capacity);
+        if (d_total) *d_total = total;
+        if (status && total > capacity) set_status(status, PS_ERR_CAPACITY);
     }
 }
 
@@ -270,7 +253,18 @@ cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long lon
                            long long* part, long long* d_total, int* status, cudaStream_t st)
 {
     if (n <= kScanOneMax) {
-        k_scan_one<<<1, kScanThreads, 0, st>>>(in, n, out, cursor, capacity, d_total, status);
+        static int configured[64] = {0};   // dynamic shared memory attribute, per device
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64 || !configured[dev]) {
+            e = cudaFuncSetAttribute(k_scan_one, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(int) * kScanOneMax));
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) configured[dev] = 1;
+        }
+        k_scan_one<<<1, kScanThreads, sizeof(int) * (size_t)(n > 0 ? n : 1), st>>>(
+            in, n, out, cursor, capacity, d_total, status);
         return cudaGetLastError();
     }
     const int nparts = scan_tiles(n > 0 ? n : 1);

@@ -1,4 +1,5 @@
-// ps_split.cu -- plane splitting (Sec. 3.3, "Plane Splitting"; App. A.2).
+// ps_split.cu -- plane splitting (Sec. 3.3, "Plane Splitting"; App. A.2) and
+// plane merging (Sec. 3.3, "Plane Merge").
 //
 // During the fit, every fixed number of iterations, a plane whose mean radius
 // gradient on one axis exceeds a threshold is cut in two along the other axis:
@@ -14,6 +15,12 @@
 //     scenes), the -half is appended after the scene's planes in plane order,
 //     so every scene's planes stay contiguous and the result is deterministic.
 //     Adam moments are copied for unsplit planes and zeroed for both halves.
+//   * k_merge_planes (one CTA) groups the fitted planes into plane instances:
+//     planes are taken by decreasing area; each joins the first existing group
+//     whose first (largest) plane has a normal within the angle threshold (up
+//     to sign: planes are two-sided) and an offset -- the distance from the
+//     scene centre to the plane along the normal oriented like the group's --
+//     within the offset threshold, or starts a new group.
 #include "ps_internal.cuh"
 
 using namespace ps;
@@ -200,7 +207,127 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_planes(SplitArgs a)
     }
 }
 
+constexpr int kMergeThreads = 1024;
+constexpr int kMergeMax = 8192;           // planes per call (one CTA, keys in shared memory)
+
+// normal (column 2 of R(q / |q|)) and offset of plane i; false for a degenerate quaternion
+__device__ __forceinline__ bool plane_normal_offset(const float* __restrict__ params, int P, int i,
+                                                    float3 c0, float3& n, float& off)
+{
+    const float* c = params + 3 * (size_t)i;
+    const float4 q = load_quat(params + 3 * (size_t)P, i);
+    const float nq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    if (!(nq > 0.f) || !(nq < INFINITY)) return false;
+    const float inv = rsqrtf(nq);
+    const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+    n = make_float3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+    off = n.x * (c[0] - c0.x) + n.y * (c[1] - c0.y) + n.z * (c[2] - c0.z);
+    return true;
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge_planes(const float* __restrict__ params,
+                                                               int P, float3 c0, float cos_max,
+                                                               float off_max, int* __restrict__ group_of,
+                                                               int* __restrict__ rep_of_group,
+                                                               int* __restrict__ d_groups)
+{
+    // dynamic shared memory: keys [N] (area bits, ~index; larger area first),
+    // per group its first plane's normal and offset [P], its first plane [P]
+    extern __shared__ unsigned long long s_dyn[];
+    __shared__ int s_groups, s_hit;
+    const int tid = threadIdx.x;
+    const float* radii = params + 7 * (size_t)P;
+    int N = 2;                    // keeps the float4 block 16-byte aligned
+    while (N < P) N <<= 1;
+    unsigned long long* s_key = s_dyn;
+    float4* s_n = reinterpret_cast<float4*>(s_dyn + N);
+    int* s_rep = reinterpret_cast<int*>(s_n + P);
+    for (int i = tid; i < N; i += kMergeThreads) {
+        unsigned long long k = 0ull;                   // padding sorts last
+        if (i < P) {
+            const float* r = radii + 4 * (size_t)i;
+            const float area = (r[0] + r[1]) * (r[2] + r[3]);
+            const float a = area > 0.f ? area : 0.f;   // NaN and negative areas last among planes
+            k = ((unsigned long long)__float_as_uint(a) << 32) | (unsigned)(0xffffffffu - (unsigned)i);
+        }
+        s_key[i] = k;
+    }
+    __syncthreads();
+    // bitonic sort, descending
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < N; i += kMergeThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long x = s_key[i], y = s_key[ixj];
+                    const bool desc = (i & k) == 0;
+                    if ((x < y) == desc) { s_key[i] = y; s_key[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) s_groups = 0;
+    __syncthreads();
+    for (int o = 0; o < P; ++o) {
+        const int i = (int)(0xffffffffu - (unsigned)(s_key[o] & 0xffffffffu));
+        float3 n;
+        float off;
+        const bool ok = plane_normal_offset(params, P, i, c0, n, off);
+        if (!ok) {                                     // degenerate: a group of its own
+            if (tid == 0) { group_of[i] = -1; }
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0) s_hit = 0x7fffffff;
+        __syncthreads();
+        const int G = s_groups;
+        for (int g = tid; g < G; g += kMergeThreads) {
+            const float4 m = s_n[g];
+            const float d = n.x * m.x + n.y * m.y + n.z * m.z;
+            const float sgn = d >= 0.f ? 1.f : -1.f;
+            if (fabsf(d) >= cos_max && fabsf(sgn * off - m.w) < off_max) atomicMin(&s_hit, g);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int g = s_hit;
+            if (g == 0x7fffffff) {
+                g = s_groups;
+                s_rep[g] = i;
+                s_n[g] = make_float4(n.x, n.y, n.z, off);
+                s_groups = g + 1;
+            }
+            group_of[i] = g;
+        }
+        __syncthreads();
+    }
+    const int G = s_groups;
+    for (int g = tid; g < G; g += kMergeThreads) rep_of_group[g] = s_rep[g];
+    if (tid == 0) *d_groups = G;
+}
+
 }  // namespace
+
+extern "C" ps_status ps_merge_planes(const float* params, int n_planes, const float* scene_center,
+                                     float max_angle_deg, float max_offset, int* group_of,
+                                     int* rep_of_group, int* d_groups, ps_stream stream)
+{
+    if (n_planes < 0 || n_planes > kMergeMax || !scene_center || !d_groups) return PS_ERR_ARG;
+    if (n_planes > 0 && (!params || !group_of || !rep_of_group)) return PS_ERR_ARG;
+    if (!(max_angle_deg >= 0.f && max_angle_deg <= 90.f) || !(max_offset >= 0.f)) return PS_ERR_ARG;
+    const float3 c0 = make_float3(scene_center[0], scene_center[1], scene_center[2]);
+    const float cos_max = cosf(max_angle_deg * 3.14159265358979f / 180.f);
+    int N = 2;
+    while (N < n_planes) N <<= 1;
+    const size_t dyn = sizeof(unsigned long long) * (size_t)N + (sizeof(float4) + sizeof(int)) * (size_t)n_planes;
+    if (dyn > 48 * 1024)
+        PS_CUDA_CHECK(cudaFuncSetAttribute(k_merge_planes, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)dyn));
+    k_merge_planes<<<1, kMergeThreads, dyn, reinterpret_cast<cudaStream_t>(stream)>>>(
+        params, n_planes, c0, cos_max, max_offset, group_of, rep_of_group, d_groups);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
 
 extern "C" ps_status ps_radii_grad_accum(const float* g_radii, const float* plane_scale, float scale,
                                          int n_planes, float* acc, ps_stream stream)

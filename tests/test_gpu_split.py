@@ -103,3 +103,36 @@ def test_accumulation_matches_oracle(torch):
     torch.cuda.synchronize()
     ref = SO.radii_grad_accum(SO.radii_grad_accum(np.zeros((P, 2)), g, 0.25), g, scale)
     assert np.allclose(acc.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
+
+
+def _partition(g):
+    out = {}
+    for i, x in enumerate(g):
+        out.setdefault(int(x), []).append(i)
+    return sorted(tuple(v) for k, v in out.items() if k >= 0)
+
+
+@pytest.mark.parametrize("max_offset", [0.001, 0.1])
+def test_merge_matches_oracle_on_room_rectangles(torch, max_offset):
+    from paper_2412_03451_gb300 import binding as B
+    from paper_2412_03451_gb300 import scenes as S
+    room = S.large_room(1000, n_rect=2000, n_views=4)
+    gt = room.gt
+    P = gt.K
+    q = gt.quat.copy()
+    q[5] = 0.0                                  # degenerate: no group
+    flat = torch.from_numpy(np.concatenate([gt.center.ravel(), q.ravel(), gt.radii.ravel()])).cuda()
+    c0 = np.asarray(room.size, np.float64) / 2
+    g = torch.full((P,), -7, dtype=torch.int32, device="cuda")
+    reps = torch.full((P,), -7, dtype=torch.int32, device="cuda")
+    ng = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.ps_merge_planes(flat, P, c0, 25.0, max_offset, g, reps, ng)
+    torch.cuda.synchronize()
+    g_ref, reps_ref = SO.merge_planes(gt.center, q, gt.radii, c0, 25.0, max_offset)
+    n = int(ng.item())
+    assert n == len(reps_ref)
+    gg = g.cpu().numpy()
+    assert gg[5] == -1 and g_ref[5] == -1
+    assert _partition(gg) == _partition(g_ref)
+    # the rooms' faces lie on a few dozen planes: most rectangles merge
+    assert n < 0.1 * P

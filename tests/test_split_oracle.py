@@ -3,6 +3,8 @@
 The geometry is checked against rectangles built from scipy's rotation of the
 same quaternions (an independent implementation of R(q)): the two halves of a
 split plane tile the parent rectangle exactly."""
+import math
+
 import numpy as np
 import pytest
 
@@ -121,3 +123,49 @@ def test_accumulation_is_the_mean_of_the_two_sides():
     assert np.allclose(acc, [[1.0, 0.25], [0.0, 0.5]])
     acc = SO.radii_grad_accum(acc, g, np.array([1.0, 2.0]))
     assert np.allclose(acc, [[3.0, 0.75], [0.0, 2.5]])
+
+
+# ---------------------------------------------------------------------------
+# Plane merge (Sec. 3.3 "Plane Merge"): 25 degrees and 0.1 cm as printed.
+
+def _frame_quat(n, rng):
+    """Quaternion (w, x, y, z) of a frame whose third column is n (scipy)."""
+    a = rng.normal(size=3)
+    vx = a - (a @ n) * n
+    vx /= np.linalg.norm(vx)
+    vy = np.cross(n, vx)
+    R = np.stack([vx, vy, n], 1)
+    x, y, z, w = Rotation.from_matrix(R).as_quat()
+    return np.array([w, x, y, z])
+
+
+def test_merge_groups_coplanar_pieces_and_splits_the_rest():
+    rng = np.random.default_rng(8)
+    c0 = np.array([1.0, 2.0, 0.5])
+    n1 = np.array([0.0, 0.0, 1.0])
+    n2 = np.array([1.0, 0.0, 0.0])
+    # five pieces of the plane z = 0.5 + 1 (offset 1 from c0), one flipped, one tilted 20 deg,
+    # one tilted 30 deg, one shifted 2 mm, and two pieces of x = 1 + 3
+    tilt20 = np.array([math.sin(math.radians(20)), 0, math.cos(math.radians(20))])
+    tilt30 = np.array([math.sin(math.radians(30)), 0, math.cos(math.radians(30))])
+    centers = [c0 + [0, 0, 1], c0 + [2, 1, 1], c0 + [-1, 3, 1], c0 + [0.5, 0.5, 1], c0 + [3, 3, 1],
+               c0 + [0, 0, 1.002], c0 + [3, 0, 0], c0 + [3, 2, 1]]
+    normals = [n1, n1, -n1, tilt20, tilt30, n1, n2, n2]
+    q = np.array([_frame_quat(n, rng) for n in normals])
+    r = np.array([[1.0, 1, 1, 1], [0.5, 0.5, 0.5, 0.5], [0.2, 0.2, 0.2, 0.2], [0.3, 0.3, 0.3, 0.3],
+                  [0.4, 0.4, 0.4, 0.4], [0.6, 0.6, 0.6, 0.6], [0.9, 0.9, 0.9, 0.9], [0.1, 0.1, 0.1, 0.1]])
+    # the tilted planes pass through the point at offset 1 along their own normals
+    centers[3] = c0 + tilt20 * 1.0
+    centers[4] = c0 + tilt30 * 1.0
+    centers[7] = c0 + n2 * 3.0 + [0, 2, 1]
+    g, reps = SO.merge_planes(np.array(centers), q, r, c0, 25.0, 0.001)
+    # groups by decreasing area: plane 0 (area 4), then 6, 5, 1, 4, 3, 2, 7
+    assert g[0] == g[1] == g[2] == g[3] == 0        # coplanar, flipped and 20 deg pieces join
+    assert g[4] != 0                                # 30 deg is beyond 25
+    assert g[5] != 0                                # 2 mm is beyond 0.1 cm
+    assert g[6] == g[7] != 0                        # the other wall
+    assert reps[g[6]] == 6 and reps[0] == 0
+    assert len(reps) == 4
+    # with 0.1 m the shifted piece joins the first group
+    g2, _ = SO.merge_planes(np.array(centers), q, r, c0, 25.0, 0.1)
+    assert g2[5] == 0
