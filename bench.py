@@ -72,7 +72,7 @@ def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:
 # DRAM bytes (read + write) per launch of the fused splat kernel from the ncu
 # capture summarised in profiles/k_splat_fused_room640_8x8.md; reported only while
 # the kernel source is the one it was taken on.
-TRAFFIC = {"splat_fused": 45935104 + 398592, "src_sha": "75432b19998e4ea0"}
+TRAFFIC = {"splat_fused": 45935616 + 300288, "src_sha": "8421d99de6fb8d57"}
 
 
 def src_hash() -> str:
@@ -619,8 +619,12 @@ def cpu_baseline(room, init, ite, target_s=20.0):
     lam = O.lambda_schedule(ite)
     views = list(range(VIEWS_PER_STEP))
     r0 = H // 2
-    t, npx = oracle_sample_step(room, init, views, (r0, r0 + 2), lam)
-    rows = max(2, min(H, int(2 * target_s / max(t, 1e-3))))
+    # two short samples give the per-row time apart from the fixed set-up cost
+    t2, _ = oracle_sample_step(room, init, views, (r0, r0 + 2), lam)
+    t6, _ = oracle_sample_step(room, init, views, (r0, r0 + 6), lam)
+    per_row = max((t6 - t2) / 4.0, 1e-4)
+    fixed = max(t2 - 2 * per_row, 0.0)
+    rows = max(2, min(H, int((target_s - fixed) / per_row)))
     r0 = max(0, H // 2 - rows // 2)
     t, npx = oracle_sample_step(room, init, views, (r0, r0 + rows), lam)
     return {"value": round(npx / t / 1e6, 6), "unit": UNIT, "cores": O.num_threads(),
