@@ -39,11 +39,13 @@
  *   {n_c, n_c.p_c, v^x_c, v^x_c.p_c, v^y_c, v^y_c.p_c, r^x+, r^x-, r^y+, r^y-},
  *   its tile rectangle (4 ints, inclusive, empty = (0,0,-1,-1)) and its depth
  *   key (1 float: smallest camera z of the plane widened by the filter margin,
- *   rounded down to f32).
+ *   rounded down to f32; a record whose key is >= z_far is culled).
  *
  * Tiles: each view is cut into tile_w x tile_h pixel tiles, numbered
  *   row-major within a view and concatenated over views.  A tile list holds the
- *   record ids whose tile rectangle covers the tile, sorted by (key, record id).
+ *   record ids whose tile rectangle covers the tile, each with an entry key (a
+ *   lower bound of the plane's depth on every ray of the tile, see
+ *   ps_bin_tiles), sorted by (entry key, record id).
  */
 #ifndef PS_H_
 #define PS_H_
@@ -171,17 +173,27 @@ ps_status ps_project_cull(const ps_planes* planes, const ps_frame* frame,
 size_t ps_bin_workspace_bytes(const ps_frame* frame, long long capacity);
 
 /* Binning and depth ordering (the near-to-far sort of Sec. 3.2, "Blending
-   Composition", applied per tile to the conservative depth key).
-   Writes tile_ptr [n_tiles + 1] (device, CSR offsets) and tile_ent [capacity]
-   (device, record ids sorted by (key, record id) within each tile).  The
-   total number of entries goes to *d_required (device, 1 long long).  If it
-   exceeds capacity, PS_ERR_CAPACITY is set in *d_status, tile_ptr is still
-   complete, and the splat calls read only the first `capacity` entries.
-   ws (device, ws_bytes >= ps_bin_workspace_bytes) is scratch. */
-ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* settings, const int* rect,
-                       const float* key, int* tile_ptr, int* tile_ent, long long capacity,
-                       long long* d_required, void* ws, size_t ws_bytes, int* d_status,
-                       ps_stream stream);
+   Composition", applied per tile to a conservative depth key).
+   Inputs: rec [R][16], rect [R][4] and key [R] from ps_project_cull (device).
+   Writes tile_ptr [n_tiles + 1] (device, CSR offsets), tile_ent [capacity]
+   (device, record ids) and tile_key [capacity] (device, their entry keys),
+   sorted by (entry key, record id) within each tile.  Entry key (computed
+   bit-reproducibly in FP32 with correctly rounded + - * / only): for the rays
+   d of the pixel centres at the tile's four corner pixels, den = (n_x d_x +
+   n_y d_y) + n_z and t = s / den from the record's n_c and s; if den has one
+   sign at all four and |den| > 0.01 (|n_x d_x| + |n_y d_y| + |n_z|) at each,
+   c = max(min t, z_near), or +inf if max t <= z_near; otherwise c = z_near;
+   the entry key is max(c, key[record]).
+   The plane's depth on any ray of the tile is >= the key (up to FP32 rounding,
+   which the splat kernels absorb with a relative margin of 1/4096).  The total
+   number of entries goes to *d_required (device, 1 long long).  If it exceeds
+   capacity, PS_ERR_CAPACITY is set in *d_status, tile_ptr is still complete,
+   and the splat calls read only the first `capacity` entries.  ws (device,
+   ws_bytes >= ps_bin_workspace_bytes) is scratch. */
+ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* settings, const float* rec,
+                       const int* rect, const float* key, int* tile_ptr, int* tile_ent,
+                       float* tile_key, long long capacity, long long* d_required, void* ws,
+                       size_t ws_bytes, int* d_status, ps_stream stream);
 
 /* Bytes of scratch that ps_splat_fwd needs (its work counter). */
 size_t ps_fwd_workspace_bytes(const ps_frame* frame);
@@ -196,7 +208,7 @@ size_t ps_fwd_workspace_bytes(const ps_frame* frame);
    alpha may be NULL).  ws (device, 16-byte aligned, >= ps_fwd_workspace_bytes)
    is scratch (a work counter reset by the call). */
 ps_status ps_splat_fwd(const ps_frame* frame, const ps_settings* settings, const float* rec,
-                       const float* key, const int* tile_ptr, const int* tile_ent,
+                       const float* tile_key, const int* tile_ptr, const int* tile_ent,
                        long long capacity, float* depth, float* normal, float* alpha,
                        void* ws, size_t ws_bytes, int* d_status, ps_stream stream);
 
@@ -206,7 +218,7 @@ ps_status ps_splat_fwd(const ps_frame* frame, const ps_settings* settings, const
    [n_pixels] (device, written), depth (device, optional) as in ps_splat_fwd;
    ws as in ps_splat_fwd.  Used to cut training patches into planes. */
 ps_status ps_splat_ids(const ps_frame* frame, const ps_settings* settings, const float* rec,
-                       const float* key, const int* tile_ptr, const int* tile_ent,
+                       const float* tile_key, const int* tile_ptr, const int* tile_ent,
                        long long capacity, int* ids, float* depth, void* ws, size_t ws_bytes,
                        int* d_status, ps_stream stream);
 
@@ -238,7 +250,7 @@ size_t ps_bwd_workspace_bytes(const ps_frame* frame);
    scratch.  Float atomics make the summation order, and so the last bits,
    vary from run to run. */
 ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* frame,
-                       const ps_settings* settings, const float* rec, const float* key,
+                       const ps_settings* settings, const float* rec, const float* tile_key,
                        const int* tile_ptr, const int* tile_ent, long long capacity,
                        const float* dL_dD, const float* dL_dN, float* g_center, float* g_quat,
                        float* g_radii, void* ws, size_t ws_bytes, int* d_status,
@@ -260,7 +272,7 @@ ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* frame,
    calls that may overlap on the GPU (different streams, or different host
    threads on the same device) race and must be serialised by the caller. */
 ps_status ps_splat_bwd_noalloc(const ps_planes* planes, const ps_frame* frame,
-                               const ps_settings* settings, const float* rec, const float* key,
+                               const ps_settings* settings, const float* rec, const float* tile_key,
                                const int* tile_ptr, const int* tile_ent, long long capacity,
                                const float* dL_dD, const float* dL_dN, float* g_center,
                                float* g_quat, float* g_radii, int* d_status, ps_stream stream);
@@ -277,7 +289,7 @@ ps_status ps_splat_bwd_noalloc(const ps_planes* planes, const ps_frame* frame,
    accumulated (the caller zeroes them).  ws (device, 16-byte aligned,
    >= ps_bwd_workspace_bytes) is scratch. */
 ps_status ps_splat_fused(const ps_planes* planes, const ps_frame* frame,
-                         const ps_settings* settings, const float* rec, const float* key,
+                         const ps_settings* settings, const float* rec, const float* tile_key,
                          const int* tile_ptr, const int* tile_ent, long long capacity,
                          const float* gt_depth, const float* gt_normal, float* depth,
                          float* normal, float* dL_dD, float* dL_dN, double* view_sums,
@@ -300,7 +312,7 @@ ps_status ps_adam_step(float* param, const float* grad, float* m, float* v, long
    including the nearest one with w = 1)).  d_counts (device, 3 long long) is
    overwritten.  Walks every tile list completely; slower than ps_splat_fwd. */
 ps_status ps_count_pairs(const ps_frame* frame, const ps_settings* settings, const float* rec,
-                         const float* key, const int* tile_ptr, const int* tile_ent,
+                         const float* tile_key, const int* tile_ptr, const int* tile_ent,
                          long long capacity, long long* d_counts, ps_stream stream);
 
 /* Graph replay support: copies d_sched[min(*d_iter, n_sched - 1)] into *d_state

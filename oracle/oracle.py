@@ -75,6 +75,7 @@ def _load():
             D = ctypes.c_double
             L = ctypes.c_long
             lib.or_bin_records.argtypes = [I, I, P, P, P, P, P, I, I, I, I, D, D, D, I, P, P, P]
+            lib.or_records_ns.argtypes = [I, I, P, P, P, P, P]
             lib.or_render.argtypes = [I, I, P, P, P, P, P, I, I, D, D, D, D, I, I, D, D, D, D,
                                       I, I, P, P, P, P, P, P]
             lib.or_loss.argtypes = [I, I, I, P, P, P, P, D, D, D, P, P, P]
@@ -142,15 +143,73 @@ def bin_records(center, quat, radii, w2c, intr, H, W, tile_w, tile_h, delta,
     return rect, key, key32
 
 
-def tile_lists(rect, key32, H, W, tile_w, tile_h):
+def records_ns(center, quat, radii, w2c):
+    """f32 (n_c, n_c . p_c) of every (view, plane) record [V, K, 4], from the same
+    FP64 operations as the bins (see ps_oracle.c)."""
+    c, q, r = _f64(center), _f64(quat), _f64(radii)
+    Rt = _f64(w2c).reshape(-1, 12)
+    K, V = c.shape[0], Rt.shape[0]
+    ns = np.zeros((V, K, 4), dtype=np.float32)
+    _load().or_records_ns(K, V, _ptr(c), _ptr(q), _ptr(r), _ptr(Rt), _ptr(ns))
+    return ns
+
+
+def entry_keys(ns, intr, tx, ty, tile_w, tile_h, z_near=Z_NEAR, rec_key=None):
+    """Entry keys of tile-list entries (records with f32 normal/offset ns [E, 4],
+    intrinsics [E, 4], tile coordinates tx, ty [E]): the depth of the plane on
+    the rays through the pixel centres at the tile's four corner pixels, all
+    in f32 with correctly rounded + - * / (numpy float32, no contraction).  If
+    the denominators d . n_c share one sign and are each > 0.01 of the sum of
+    the magnitudes of their terms, c = max(min t, z_near), or +inf if
+    max t <= z_near; otherwise c = z_near.  The key is max(c, rec_key) (the
+    record's f32 quad key, if given): a lower bound of every depth the plane
+    takes on a ray of the tile."""
+    f32 = np.float32
+    ns = np.asarray(ns, f32)
+    intr = np.asarray(intr, f32)
+    fx, fy, cx, cy = intr[:, 0], intr[:, 1], intr[:, 2], intr[:, 3]
+    tx = np.asarray(tx, np.int64)
+    ty = np.asarray(ty, np.int64)
+    xs = [(tx * tile_w).astype(f32), (tx * tile_w + tile_w - 1).astype(f32)]
+    ys = [(ty * tile_h).astype(f32), (ty * tile_h + tile_h - 1).astype(f32)]
+    zn = f32(z_near)
+    tmin = np.full(len(tx), np.inf, f32)
+    tmax = np.full(len(tx), -np.inf, f32)
+    npos = np.zeros(len(tx), np.int64)
+    nneg = np.zeros(len(tx), np.int64)
+    weak = np.zeros(len(tx), bool)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for xa in xs:
+            dx = ((xa + f32(0.5)) - cx) / fx
+            for yb in ys:
+                dy = ((yb + f32(0.5)) - cy) / fy
+                p1 = ns[:, 0] * dx
+                p2 = ns[:, 1] * dy
+                den = (p1 + p2) + ns[:, 2]
+                mag = (np.abs(p1) + np.abs(p2)) + np.abs(ns[:, 2])
+                weak |= ~(np.abs(den) > f32(0.01) * mag)
+                npos += den > 0
+                nneg += den < 0
+                t = ns[:, 3] / den
+                tmin = np.fmin(tmin, t)
+                tmax = np.fmax(tmax, t)
+    key = np.where(tmax > zn, np.maximum(tmin, zn), f32(np.inf)).astype(f32)
+    key = np.where(weak | ((npos != 4) & (nneg != 4)), zn, key).astype(f32)
+    if rec_key is not None:
+        key = np.maximum(key, np.asarray(rec_key, f32))
+    return key
+
+
+def tile_lists(rect, key32, ns, intr, H, W, tile_w, tile_h, z_near=Z_NEAR):
     """CSR tile lists: tiles numbered v*T + ty*tiles_x + tx, entries are record
-    ids v*K + k, each list sorted by (float key, record id)."""
-    V, K = key32.shape
-    tx = (W + tile_w - 1) // tile_w
-    ty = (H + tile_h - 1) // tile_h
-    T = tx * ty
-    tiles, keys, recs = [], [], []
-    kb = key32.view(np.uint32)
+    ids v*K + k with their entry keys (entry_keys with the record keys key32
+    [V, K]), each list sorted by (key, record id).  ns [V, K, 4] from
+    records_ns, intr [V, 4].  Returns (ptr, ent, key)."""
+    V, K = rect.shape[0], rect.shape[1]
+    tx_n = (W + tile_w - 1) // tile_w
+    ty_n = (H + tile_h - 1) // tile_h
+    T = tx_n * ty_n
+    tiles, recs, txs, tys, vs = [], [], [], [], []
     for v in range(V):
         for k in range(K):
             x0, y0, x1, y1 = (int(a) for a in rect[v, k])
@@ -158,17 +217,23 @@ def tile_lists(rect, key32, H, W, tile_w, tile_h):
                 continue
             for yy in range(y0, y1 + 1):
                 for xx in range(x0, x1 + 1):
-                    tiles.append(v * T + yy * tx + xx)
-                    keys.append(int(kb[v, k]))
+                    tiles.append(v * T + yy * tx_n + xx)
                     recs.append(v * K + k)
+                    txs.append(xx); tys.append(yy); vs.append(v)
     tiles = np.asarray(tiles, dtype=np.int64)
-    keys = np.asarray(keys, dtype=np.int64)
     recs = np.asarray(recs, dtype=np.int64)
-    order = np.lexsort((recs, keys, tiles))
+    if tiles.size:
+        vs = np.asarray(vs)
+        keys = entry_keys(ns.reshape(-1, 4)[recs], np.asarray(intr, np.float32).reshape(-1, 4)[vs],
+                          np.asarray(txs), np.asarray(tys), tile_w, tile_h, z_near,
+                          rec_key=np.asarray(key32, np.float32).reshape(-1)[recs])
+    else:
+        keys = np.zeros(0, np.float32)
+    order = np.lexsort((recs, keys.view(np.uint32).astype(np.int64), tiles))
     counts = np.bincount(tiles, minlength=V * T) if tiles.size else np.zeros(V * T, np.int64)
     ptr = np.zeros(V * T + 1, dtype=np.int64)
     ptr[1:] = np.cumsum(counts)
-    return ptr.astype(np.int32), recs[order].astype(np.int32)
+    return ptr.astype(np.int32), recs[order].astype(np.int32), keys[order]
 
 
 # --------------------------------------------------------------------------

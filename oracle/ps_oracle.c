@@ -214,6 +214,26 @@ void or_bin_records(int K, int V,
     }
 }
 
+/* f32 camera-frame normal and offset of every (view, plane) record:         */
+/* ns[4 (v K + k) + (0..2)] = (float) n_c, ns[.. + 3] = (float) (n_c . p_c),   */
+/* from the same FP64 operations as the bins above (zeros for a degenerate    */
+/* quaternion).  The tile-list entry keys are computed from these.            */
+void or_records_ns(int K, int V, const double* center, const double* quat, const double* radii,
+                   const double* w2c, float* ns)
+{
+    for (int v = 0; v < V; ++v) {
+        const double* Rt = w2c + 12 * v;
+        for (int k = 0; k < K; ++k) {
+            float* o = ns + 4 * ((long)v * K + k);
+            plane_cam pc;
+            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, 0, &pc);
+            if (!pc.ok) { o[0] = o[1] = o[2] = o[3] = 0.0f; continue; }
+            o[0] = (float)pc.nc[0]; o[1] = (float)pc.nc[1]; o[2] = (float)pc.nc[2];
+            o[3] = (float)dot3(pc.nc, pc.pc);
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Per-(pixel, plane) evaluation of Eq. 4 and Eq. 6-9.                       */
 typedef struct {

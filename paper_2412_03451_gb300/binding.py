@@ -95,7 +95,7 @@ def load():
             "ps_plan_views": ([I, P, P, P, I, P, P, P, I, I, P, P], I),
             "ps_project_cull": ([P, P, P, P, P, P, P, P], I),
             "ps_bin_workspace_bytes": ([P, LL], SZ),
-            "ps_bin_tiles": ([P, P, P, P, P, P, LL, P, P, SZ, P, P], I),
+            "ps_bin_tiles": ([P, P, P, P, P, P, P, P, LL, P, P, SZ, P, P], I),
             "ps_fwd_workspace_bytes": ([P], SZ),
             "ps_splat_fwd": ([P, P, P, P, P, P, LL, P, P, P, P, SZ, P, P], I),
             "ps_splat_ids": ([P, P, P, P, P, P, LL, P, P, P, SZ, P, P], I),
@@ -240,12 +240,13 @@ def ps_bin_workspace_bytes(frame: PsFrame, capacity: int) -> int:
     return int(load().ps_bin_workspace_bytes(ctypes.byref(frame), int(capacity)))
 
 
-def ps_bin_tiles(frame, settings, rect, key, tile_ptr, tile_ent, capacity, required, ws, status,
-                 stream=None):
+def ps_bin_tiles(frame, settings, rec, rect, key, tile_ptr, tile_ent, tile_key, capacity, required,
+                 ws, status, stream=None):
     nbytes = ws.numel() * ws.element_size()
-    _check(load().ps_bin_tiles(ctypes.byref(frame), ctypes.byref(settings), _ptr(rect), _ptr(key),
-                               _ptr(tile_ptr), _ptr(tile_ent), int(capacity), _ptr(required),
-                               _ptr(ws), nbytes, _ptr(status), _stream(stream)), "ps_bin_tiles")
+    _check(load().ps_bin_tiles(ctypes.byref(frame), ctypes.byref(settings), _ptr(rec), _ptr(rect),
+                               _ptr(key), _ptr(tile_ptr), _ptr(tile_ent), _ptr(tile_key),
+                               int(capacity), _ptr(required), _ptr(ws), nbytes, _ptr(status),
+                               _stream(stream)), "ps_bin_tiles")
 
 
 def ps_fwd_workspace_bytes(frame: PsFrame) -> int:

@@ -2,19 +2,34 @@
 //
 // Sec. 3.2 ("Blending Composition") sorts the intersections of a ray near to
 // far.  The renderer gets there in two stages: here every tile receives the
-// records whose screen rectangle covers it, sorted by the record's depth key (a
-// lower bound of every depth the plane can produce in that tile); the splat
-// kernels then merge per pixel by exact depth.  Keys are unique per list as
-// (key bits, record id), so the output does not depend on the order in which
-// the atomics below land.
+// records whose screen rectangle covers it, each with a depth key that bounds
+// from below every depth the plane can produce in that tile, sorted by it;
+// the splat kernels then merge per pixel by exact depth.  Keys are unique per
+// list as (key bits, record id), so the output does not depend on the order in
+// which the atomics below land.
+//
+// Entry key (bit-exact specification, FP32 with correctly rounded + - * /
+// only, no contraction): the rays of the pixel centres at the tile's four
+// corner pixels, d = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1); per ray
+// den = (n_x d_x + n_y d_y) + n_z and t = s / den with the record's f32 n_c and
+// s = n_c . p_c.  Over the tile the depth s / (d . n_c) of the plane is
+// linear-fractional in the ray, so if den has one sign at all four corners (and
+// |den| > 0.01 (|n_x d_x| + |n_y d_y| + |n_z|) at each, which keeps FP32
+// cancellation small) its range over the tile is spanned by the corners:
+// c = max(min t, z_near), or +inf if max t <= z_near (no depth in range);
+// otherwise c = z_near.  The entry key is max(c, the record's key), both lower
+// bounds of every depth the plane produces in the tile.  Unlike the record key
+// alone (the smallest z of the whole widened quad), this bound is as tight as
+// the tile: entries of large or oblique planes no longer all sort to the front
+// of every list.
 //
 //   1. record counts: tiles covered by each record's rectangle (+ the record's
 //      first global tile and rectangle width), then an exclusive scan over
 //      records numbers every (record, tile) pair;
 //   2. pair count: one thread per pair adds 1 to its tile's counter;
 //   3. tile scan: tile_ptr = exclusive prefix sum, total -> d_required;
-//   4. scatter: one thread per pair writes its record id into a slot of its
-//      tile (unordered, via per-tile cursors);
+//   4. scatter: one thread per pair writes its record id and entry key into a
+//      slot of its tile (unordered, via per-tile cursors);
 //   5. sort: each tile's slots by (key, record id): one warp per tile sorts up
 //      to 64 entries in registers and up to kWarpSortCap in its slice of shared
 //      memory (bitonic networks); persistent CTAs take the longer lists
@@ -38,11 +53,12 @@ constexpr int kSortBlocks = 152 * 4;  // persistent blocks of the long-list sort
 
 struct BinWs {
     int* rec_cnt;       // [R + 1] tiles per record -> exclusive prefix (pair numbering)
-    int4* rec_info;     // [R] first global tile, rectangle width in tiles, tiles_x, 0
+    int4* rec_info;     // [R] first global tile, rectangle width in tiles, tiles_x, view
     int* tile_cnt;      // [n_tiles]
     int* cursor;        // [n_tiles]
     long long* part;    // [2 * max scan tiles] scan partial sums
     int* ent_tmp;       // [capacity] unordered entries
+    float* key_tmp;     // [capacity] their keys
 };
 
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -54,10 +70,10 @@ inline size_t ws_bytes(int R, int n_tiles, long long capacity)
     const int parts = 2 * (scan_tiles(R + 1) > scan_tiles(n_tiles) ? scan_tiles(R + 1) : scan_tiles(n_tiles)) + 2;
     return align_up(sizeof(int) * (size_t)(R + 1)) + align_up(sizeof(int4) * (size_t)(R > 0 ? R : 1)) +
            2 * align_up(sizeof(int) * (size_t)n_tiles) + align_up(sizeof(long long) * (size_t)parts) +
-           align_up(sizeof(int) * (size_t)(capacity > 0 ? capacity : 1));
+           2 * align_up(sizeof(int) * (size_t)(capacity > 0 ? capacity : 1));
 }
 
-inline BinWs carve(void* ws, int R, int n_tiles)
+inline BinWs carve(void* ws, int R, int n_tiles, long long capacity)
 {
     char* p = static_cast<char*>(ws);
     BinWs w;
@@ -68,6 +84,8 @@ inline BinWs carve(void* ws, int R, int n_tiles)
     const int parts = 2 * (scan_tiles(R + 1) > scan_tiles(n_tiles) ? scan_tiles(R + 1) : scan_tiles(n_tiles)) + 2;
     w.part = reinterpret_cast<long long*>(p); p += align_up(sizeof(long long) * (size_t)parts);
     w.ent_tmp = reinterpret_cast<int*>(p);
+    p += align_up(sizeof(int) * (size_t)(capacity > 0 ? capacity : 1));
+    w.key_tmp = reinterpret_cast<float*>(p);
     return w;
 }
 
@@ -86,11 +104,11 @@ __global__ void __launch_bounds__(128) k_rec_count(const int4* __restrict__ rect
     const int4 rc = __ldg(&rect[r]);
     const int tx = __ldg(&vw->tiles_x);
     int c = 0;
-    int4 info = make_int4(0, 1, tx, 0);
+    int4 info = make_int4(0, 1, tx, v);
     if (rc.z >= rc.x && rc.w >= rc.y) {
         const int w = rc.z - rc.x + 1;
         c = w * (rc.w - rc.y + 1);
-        info = make_int4(__ldg(&vw->tile_off) + rc.y * tx + rc.x, w, tx, 0);
+        info = make_int4(__ldg(&vw->tile_off) + rc.y * tx + rc.x, w, tx, v);
     }
     rec_cnt[r] = c;
     rec_info[r] = info;
@@ -319,11 +337,48 @@ __global__ void __launch_bounds__(256) k_pair_count(const int* __restrict__ rec_
     }
 }
 
+// The entry key of the specification above.
+__device__ __forceinline__ float entry_key(float4 ns, const ps_view* __restrict__ vw, int tx, int ty,
+                                           int tw, int th, float z_near)
+{
+    const float fx = __ldg(&vw->fx), fy = __ldg(&vw->fy), cx = __ldg(&vw->cx), cy = __ldg(&vw->cy);
+    const float xs[2] = {(float)(tx * tw), (float)(tx * tw + tw - 1)};
+    const float ys[2] = {(float)(ty * th), (float)(ty * th + th - 1)};
+    float tmin = INFINITY, tmax = -INFINITY;
+    int npos = 0, nneg = 0;
+    bool weak = false;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const float dx = __fdiv_rn(__fsub_rn(__fadd_rn(xs[a], 0.5f), cx), fx);
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float dy = __fdiv_rn(__fsub_rn(__fadd_rn(ys[b], 0.5f), cy), fy);
+            const float p1 = __fmul_rn(ns.x, dx), p2 = __fmul_rn(ns.y, dy);
+            const float den = __fadd_rn(__fadd_rn(p1, p2), ns.z);
+            const float mag = __fadd_rn(__fadd_rn(fabsf(p1), fabsf(p2)), fabsf(ns.z));
+            if (!(fabsf(den) > __fmul_rn(0.01f, mag))) weak = true;
+            npos += den > 0.f;
+            nneg += den < 0.f;
+            const float t = __fdiv_rn(ns.w, den);
+            tmin = fminf(tmin, t);
+            tmax = fmaxf(tmax, t);
+        }
+    }
+    if (weak || (npos != 4 && nneg != 4)) return z_near;
+    if (!(tmax > z_near)) return INFINITY;
+    return fmaxf(tmin, z_near);
+}
+
 __global__ void __launch_bounds__(256) k_pair_scatter(const int* __restrict__ rec_off, int R,
                                                        const int4* __restrict__ rec_info,
                                                        const int* __restrict__ tile_ptr,
                                                        int* __restrict__ cursor,
-                                                       int* __restrict__ ent_tmp)
+                                                       int* __restrict__ ent_tmp,
+                                                       float* __restrict__ key_tmp,
+                                                       const float4* __restrict__ rec,
+                                                       const float* __restrict__ rec_key,
+                                                       const ps_view* __restrict__ views,
+                                                       int tw, int th, float z_near)
 {
     __shared__ int s_rng[2];
     const int E = __ldg(&rec_off[R]);
@@ -338,24 +393,41 @@ __global__ void __launch_bounds__(256) k_pair_scatter(const int* __restrict__ re
             const int pos = atomicAdd(&cursor[t], 1);
             // tile_ptr is clamped to the capacity: positions past it belong to lists
             // that did not fit and are dropped (the status word says so)
-            if (pos < __ldg(&tile_ptr[t + 1])) ent_tmp[pos] = r;
+            if (pos < __ldg(&tile_ptr[t + 1])) {
+                const ps_view* vw = views + info.w;
+                const int lt = t - __ldg(&vw->tile_off);
+                ent_tmp[pos] = r;
+                key_tmp[pos] = fmaxf(entry_key(__ldg(&rec[4 * (size_t)r]), vw, lt % info.z,
+                                               lt / info.z, tw, th, z_near),
+                                     __ldg(&rec_key[r]));
+            }
         }
         __syncthreads();
     }
 }
 
 // 5. sort ----------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long sort_key(const float* __restrict__ key, int r)
+// (key bits, record id) of slot j: keys are positive or +inf, so their bits sort like the values
+__device__ __forceinline__ unsigned long long sort_key(const float* __restrict__ key_tmp,
+                                                       const int* __restrict__ ent_tmp, int j)
 {
-    return ((unsigned long long)__float_as_uint(__ldg(&key[r])) << 32) | (unsigned)r;
+    return ((unsigned long long)__float_as_uint(key_tmp[j]) << 32) | (unsigned)ent_tmp[j];
+}
+
+__device__ __forceinline__ void put(int* __restrict__ tile_ent, float* __restrict__ tile_key, int j,
+                                    unsigned long long v)
+{
+    tile_ent[j] = (int)(unsigned)(v & 0xffffffffu);
+    tile_key[j] = __uint_as_float((unsigned)(v >> 32));
 }
 
 // Short lists: one warp per tile.
 __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __restrict__ tile_ptr,
                                                                int n_tiles,
                                                                const int* __restrict__ ent_tmp,
-                                                               const float* __restrict__ key,
-                                                               int* __restrict__ tile_ent)
+                                                               const float* __restrict__ key_tmp,
+                                                               int* __restrict__ tile_ent,
+                                                               float* __restrict__ tile_key)
 {
     extern __shared__ unsigned long long s_warp_keys[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -365,11 +437,11 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __rest
     const int n = e - b;
     if (n <= 0 || n > kWarpSortCap) return;
     if (n == 1) {
-        if (lane == 0) tile_ent[b] = ent_tmp[b];
+        if (lane == 0) { tile_ent[b] = ent_tmp[b]; tile_key[b] = key_tmp[b]; }
         return;
     }
     if (n <= 32) {
-        unsigned long long v = lane < n ? sort_key(key, ent_tmp[b + lane]) : ~0ull;
+        unsigned long long v = lane < n ? sort_key(key_tmp, ent_tmp, b + lane) : ~0ull;
 #pragma unroll
         for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
@@ -380,13 +452,13 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __rest
                 v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
             }
         }
-        if (lane < n) tile_ent[b + lane] = (int)(unsigned)(v & 0xffffffffu);
+        if (lane < n) put(tile_ent, tile_key, b + lane, v);
         return;
     }
     if (n <= 64) {
         // element lane in v0, element lane + 32 in v1
-        unsigned long long v0 = sort_key(key, ent_tmp[b + lane]);
-        unsigned long long v1 = lane + 32 < n ? sort_key(key, ent_tmp[b + lane + 32]) : ~0ull;
+        unsigned long long v0 = sort_key(key_tmp, ent_tmp, b + lane);
+        unsigned long long v1 = lane + 32 < n ? sort_key(key_tmp, ent_tmp, b + lane + 32) : ~0ull;
 #pragma unroll
         for (int k = 2; k <= 64; k <<= 1) {
 #pragma unroll
@@ -405,14 +477,14 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __rest
                 }
             }
         }
-        tile_ent[b + lane] = (int)(unsigned)(v0 & 0xffffffffu);
-        if (lane + 32 < n) tile_ent[b + lane + 32] = (int)(unsigned)(v1 & 0xffffffffu);
+        put(tile_ent, tile_key, b + lane, v0);
+        if (lane + 32 < n) put(tile_ent, tile_key, b + lane + 32, v1);
         return;
     }
     unsigned long long* s = s_warp_keys + (size_t)w * kWarpSortCap;
     int N = 64;
     while (N < n) N <<= 1;
-    for (int i = lane; i < N; i += 32) s[i] = i < n ? sort_key(key, ent_tmp[b + i]) : ~0ull;
+    for (int i = lane; i < N; i += 32) s[i] = i < n ? sort_key(key_tmp, ent_tmp, b + i) : ~0ull;
     __syncwarp();
     for (int k = 2; k <= N; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -427,19 +499,21 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __rest
             __syncwarp();
         }
     }
-    for (int i = lane; i < n; i += 32) tile_ent[b + i] = (int)(unsigned)(s[i] & 0xffffffffu);
+    for (int i = lane; i < n; i += 32) put(tile_ent, tile_key, b + i, s[i]);
 }
 
 // Long lists: one CTA per tile (tiles with at most kWarpSortCap entries return at once).
-__device__ void sort_long_list(const int* __restrict__ ent_tmp, const float* __restrict__ key,
-                               int* __restrict__ tile_ent, int b, int n, unsigned long long* s);
+__device__ void sort_long_list(const int* __restrict__ ent_tmp, const float* __restrict__ key_tmp,
+                               int* __restrict__ tile_ent, float* __restrict__ tile_key, int b, int n,
+                               unsigned long long* s);
 
 // Blocks stride over the tiles 256 at a time: each thread checks one list
 // length, the long lists found are sorted one after the other by the block.
 __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr, int n_tiles,
                                                const int* __restrict__ ent_tmp,
-                                               const float* __restrict__ key,
-                                               int* __restrict__ tile_ent)
+                                               const float* __restrict__ key_tmp,
+                                               int* __restrict__ tile_ent,
+                                               float* __restrict__ tile_key)
 {
     __shared__ unsigned long long s[kSortCap];
     __shared__ int s_list[256];
@@ -455,21 +529,22 @@ __global__ void __launch_bounds__(256) k_sort(const int* __restrict__ tile_ptr, 
         for (int q = 0; q < cnt; ++q) {
             const int tt = s_list[q];
             const int b = tile_ptr[tt];
-            sort_long_list(ent_tmp, key, tile_ent, b, tile_ptr[tt + 1] - b, s);
+            sort_long_list(ent_tmp, key_tmp, tile_ent, tile_key, b, tile_ptr[tt + 1] - b, s);
         }
         __syncthreads();
     }
 }
 
-__device__ void sort_long_list(const int* __restrict__ ent_tmp, const float* __restrict__ key,
-                               int* __restrict__ tile_ent, int b, int n, unsigned long long* s)
+__device__ void sort_long_list(const int* __restrict__ ent_tmp, const float* __restrict__ key_tmp,
+                               int* __restrict__ tile_ent, float* __restrict__ tile_key, int b, int n,
+                               unsigned long long* s)
 {
     const int tid = threadIdx.x, NT = blockDim.x;
     if (n <= kSortCap) {
         int N = 2;
         while (N < n) N <<= 1;
         for (int i = tid; i < N; i += NT)
-            s[i] = i < n ? sort_key(key, ent_tmp[b + i]) : ~0ull;
+            s[i] = i < n ? sort_key(key_tmp, ent_tmp, b + i) : ~0ull;
         __syncthreads();
         for (int k = 2; k <= N; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
@@ -484,24 +559,24 @@ __device__ void sort_long_list(const int* __restrict__ ent_tmp, const float* __r
                 __syncthreads();
             }
         }
-        for (int i = tid; i < n; i += NT) tile_ent[b + i] = (int)(unsigned)(s[i] & 0xffffffffu);
+        for (int i = tid; i < n; i += NT) put(tile_ent, tile_key, b + i, s[i]);
         __syncthreads();    // the block's next list reuses s
         return;
     }
     // rank of each element = number of smaller keys (keys are unique)
     for (int i0 = 0; i0 < n; i0 += NT) {
         const int i = i0 + tid;
-        const unsigned long long ki = i < n ? sort_key(key, ent_tmp[b + i]) : 0ull;
+        const unsigned long long ki = i < n ? sort_key(key_tmp, ent_tmp, b + i) : 0ull;
         int rank = 0;
         for (int c0 = 0; c0 < n; c0 += kSortCap) {
             const int cn = min(kSortCap, n - c0);
             __syncthreads();
-            for (int j = tid; j < cn; j += NT) s[j] = sort_key(key, ent_tmp[b + c0 + j]);
+            for (int j = tid; j < cn; j += NT) s[j] = sort_key(key_tmp, ent_tmp, b + c0 + j);
             __syncthreads();
             if (i < n)
                 for (int j = 0; j < cn; ++j) rank += s[j] < ki;
         }
-        if (i < n) tile_ent[b + rank] = (int)(unsigned)(ki & 0xffffffffu);
+        if (i < n) put(tile_ent, tile_key, b + rank, ki);
     }
     __syncthreads();    // the block's next list reuses s
 }
@@ -514,22 +589,24 @@ extern "C" size_t ps_bin_workspace_bytes(const ps_frame* frame, long long capaci
     return ws_bytes(frame->n_records, frame->n_tiles, capacity);
 }
 
-extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, const int* rect,
-                                  const float* key, int* tile_ptr, int* tile_ent,
-                                  long long capacity, long long* d_required, void* ws,
-                                  size_t ws_bytes_, int* d_status, ps_stream stream)
+extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, const float* rec,
+                                  const int* rect, const float* key, int* tile_ptr, int* tile_ent,
+                                  float* tile_key, long long capacity, long long* d_required,
+                                  void* ws, size_t ws_bytes_, int* d_status, ps_stream stream)
 {
-    if (!frame || !s || !rect || !key || !tile_ptr || !d_required || !ws || !frame->views)
+    if (!frame || !s || !rec || !rect || !key || !tile_ptr || !d_required || !ws || !frame->views)
         return PS_ERR_ARG;
     if (capacity < 0 || capacity >= (1LL << 31) - 1) return PS_ERR_ARG;
-    if (capacity > 0 && !tile_ent) return PS_ERR_ARG;
+    if (capacity > 0 && (!tile_ent || !tile_key)) return PS_ERR_ARG;
+    if (s->tile_w <= 0 || s->tile_h <= 0 || !(s->z_near > 0.f)) return PS_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(rec) & 15) return PS_ERR_ARG;
     if (frame->n_tiles <= 0 || frame->n_records < 0) return PS_ERR_ARG;
     const int R = frame->n_records;
     if (ws_bytes_ < ws_bytes(R, frame->n_tiles, capacity)) return PS_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(ws) & 255) return PS_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(rect) & 15) return PS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    BinWs w = carve(ws, R, frame->n_tiles);
+    BinWs w = carve(ws, R, frame->n_tiles, capacity);
     PS_CUDA_CHECK(cudaMemsetAsync(w.tile_cnt, 0, sizeof(int) * (size_t)frame->n_tiles, st));
     const int4* rc = reinterpret_cast<const int4*>(rect);
     if (R > 0) {
@@ -548,7 +625,9 @@ extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, c
         return PS_ERR_CUDA;
     if (R > 0 && capacity > 0) {
         k_pair_scatter<<<kFlatBlocks, 256, 0, st>>>(w.rec_cnt, R, w.rec_info, tile_ptr, w.cursor,
-                                                    w.ent_tmp);
+                                                    w.ent_tmp, w.key_tmp,
+                                                    reinterpret_cast<const float4*>(rec), key, frame->views,
+                                                    s->tile_w, s->tile_h, s->z_near);
         PS_LAUNCH_CHECK();
         static int configured[64] = {0};   // dynamic shared memory attribute of k_sort_warp, per device
         const int dyn = (int)(sizeof(unsigned long long) * kWarpSortCap * kSortWarps);
@@ -559,11 +638,11 @@ extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, c
             if (dev >= 0 && dev < 64) configured[dev] = 1;
         }
         k_sort_warp<<<(frame->n_tiles + kSortWarps - 1) / kSortWarps, kSortWarps * 32, dyn, st>>>(
-            tile_ptr, frame->n_tiles, w.ent_tmp, key, tile_ent);
+            tile_ptr, frame->n_tiles, w.ent_tmp, w.key_tmp, tile_ent, tile_key);
         PS_LAUNCH_CHECK();
         const int sort_blocks = (frame->n_tiles + 255) / 256;
         k_sort<<<sort_blocks < kSortBlocks ? sort_blocks : kSortBlocks, 256, 0, st>>>(
-            tile_ptr, frame->n_tiles, w.ent_tmp, key, tile_ent);
+            tile_ptr, frame->n_tiles, w.ent_tmp, w.key_tmp, tile_ent, tile_key);
         PS_LAUNCH_CHECK();
     }
     return PS_OK;

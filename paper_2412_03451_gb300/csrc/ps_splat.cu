@@ -55,7 +55,7 @@ struct SplatArgs {
     const ps_view* views;
     int n_views;
     const float4* rec;        // [R][4]
-    const float* key;         // [R]
+    const float* key;         // [capacity] entry keys, parallel to tile_ent
     const int* tile_ptr;
     const int* tile_ent;
     long long capacity;
@@ -246,7 +246,7 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                 const float4* r = a.rec + (size_t)id * 4;
                 const float4 n = __ldg(r + 0), vx = __ldg(r + 1), vy = __ldg(r + 2), rr = __ldg(r + 3);
                 ok = region_may_hit(n, vx, vy, rr, g, a.c);
-                ws.key[lane] = __ldg(&a.key[id]);
+                ws.key[lane] = __ldg(&a.key[i]);
                 if (ok) {
                     ws.id[lane] = id;
                     ws.rec[lane][0] = n; ws.rec[lane][1] = vx; ws.rec[lane][2] = vy; ws.rec[lane][3] = rr;
@@ -255,7 +255,7 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                 ws.key[lane] = INFINITY;
             }
             if (lane == 0)
-                ws.key[32] = (base + 32 < end) ? __ldg(&a.key[__ldg(&a.tile_ent[base + 32])]) : INFINITY;
+                ws.key[32] = (base + 32 < end) ? __ldg(&a.key[base + 32]) : INFINITY;
             unsigned m = __ballot_sync(kFull, ok);
             __syncwarp();
             while (m) {

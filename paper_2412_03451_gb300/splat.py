@@ -92,6 +92,7 @@ class Renderer:
     def _alloc_lists(self, capacity: int):
         self.capacity = int(capacity)
         self.tile_ent = torch.zeros(max(self.capacity, 1), dtype=torch.int32, device=self.device)
+        self.tile_key = torch.zeros(max(self.capacity, 1), dtype=torch.float32, device=self.device)
         nbytes = B.ps_bin_workspace_bytes(self.frame, self.capacity)
         self.bin_ws = torch.zeros((nbytes + 255) // 256 * 64, dtype=torch.float32,
                                   device=self.device)
@@ -147,8 +148,8 @@ class Renderer:
         s = self.make_settings(lam, flags, d_state)
         pl = self.planes_struct(flat)
         B.ps_project_cull(pl, self.frame, s, self.rec, self.rect, self.key, self.status)
-        B.ps_bin_tiles(self.frame, s, self.rect, self.key, self.tile_ptr, self.tile_ent,
-                       self.capacity, self.required, self.bin_ws, self.status)
+        B.ps_bin_tiles(self.frame, s, self.rec, self.rect, self.key, self.tile_ptr, self.tile_ent,
+                       self.tile_key, self.capacity, self.required, self.bin_ws, self.status)
 
     def ensure_capacity(self, flat, lam, flags=None, headroom=1.5) -> bool:
         """Runs projection + binning once and grows the tile-list capacity if it
@@ -162,7 +163,7 @@ class Renderer:
         return False
 
     def splat_forward(self, alpha=True):
-        B.ps_splat_fwd(self.frame, self.settings, self.rec, self.key, self.tile_ptr, self.tile_ent,
+        B.ps_splat_fwd(self.frame, self.settings, self.rec, self.tile_key, self.tile_ptr, self.tile_ent,
                        self.capacity, self.depth, self.normal, self.alpha if alpha else None,
                        self.fwd_ws, self.status)
         return self.depth, self.normal
@@ -176,13 +177,13 @@ class Renderer:
         fl = B.PS_HARD if hard else 0
         self.project_bin(flat, lam, flags=fl)
         ids = torch.empty(int(self.frame.n_pixels), dtype=torch.int32, device=self.device)
-        B.ps_splat_ids(self.frame, self.settings, self.rec, self.key, self.tile_ptr, self.tile_ent,
+        B.ps_splat_ids(self.frame, self.settings, self.rec, self.tile_key, self.tile_ptr, self.tile_ent,
                        self.capacity, ids, self.depth, self.fwd_ws, self.status)
         return ids, self.depth
 
     def count_pairs(self, counts: torch.Tensor):
         """Work counts of the current tile lists (tested, candidate, composited pairs)."""
-        B.ps_count_pairs(self.frame, self.settings, self.rec, self.key, self.tile_ptr,
+        B.ps_count_pairs(self.frame, self.settings, self.rec, self.tile_key, self.tile_ptr,
                          self.tile_ent, self.capacity, counts)
 
     def loss(self, gt_depth, gt_normal):
@@ -198,7 +199,7 @@ class Renderer:
         pl = self.planes_struct(flat)
         gc, gq, gr = flat_views(grad_flat, self.P)
         m = write_maps
-        B.ps_splat_fused(pl, self.frame, self.settings, self.rec, self.key, self.tile_ptr,
+        B.ps_splat_fused(pl, self.frame, self.settings, self.rec, self.tile_key, self.tile_ptr,
                          self.tile_ent, self.capacity, gt_depth, gt_normal,
                          self.depth if m else None, self.normal if m else None,
                          self.dLdD if m else None, self.dLdN if m else None,
@@ -210,7 +211,7 @@ class Renderer:
         """Accumulates d(sum dLdD*D + dLdN.N)/dparams into grad_flat (same layout)."""
         pl = self.planes_struct(flat)
         gc, gq, gr = flat_views(grad_flat, self.P)
-        B.ps_splat_bwd(pl, self.frame, self.settings, self.rec, self.key, self.tile_ptr,
+        B.ps_splat_bwd(pl, self.frame, self.settings, self.rec, self.tile_key, self.tile_ptr,
                        self.tile_ent, self.capacity, self.dLdD if dLdD is None else dLdD,
                        self.dLdN if dLdN is None else dLdN, gc, gq, gr, self.bwd_ws, self.status)
 

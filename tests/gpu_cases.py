@@ -44,6 +44,7 @@ def gpu_run(planes: S.Planes, cams: S.Cameras, lam: float, tile=(16, 16), M=30, 
         key=r.key.cpu().numpy().reshape(V, planes.K),
         tile_ptr=r.tile_ptr.cpu().numpy(),
         tile_ent=r.tile_ent.cpu().numpy()[: int(r.tile_ptr[-1].item())],
+        tile_key=r.tile_key.cpu().numpy()[: int(r.tile_ptr[-1].item())],
         required=int(r.required.item()),
         status=int(r.status.item()),
         depth=r.depth.cpu().numpy().reshape(V, H, W),
@@ -58,8 +59,10 @@ def oracle_bins(planes, cams, delta, tile, gaussian=False):
     rect, key, key32 = O.bin_records(planes.center, planes.quat, planes.radii, cams.w2c, cams.intr,
                                      cams.H, cams.W, tile[0], tile[1], delta, z_near=Z_NEAR32,
                                      z_far=Z_FAR32, gaussian=gaussian)
-    ptr, ent = O.tile_lists(rect, key32, cams.H, cams.W, tile[0], tile[1])
-    return rect, key32, ptr, ent
+    ns = O.records_ns(planes.center, planes.quat, planes.radii, cams.w2c)
+    ptr, ent, ekey = O.tile_lists(rect, key32, ns, cams.intr, cams.H, cams.W, tile[0], tile[1],
+                                  z_near=Z_NEAR32)
+    return rect, key32, ptr, ent, ekey
 
 
 def oracle_render(planes, cams, lam, M=30, rows=None, gaussian=False):

@@ -37,11 +37,12 @@ def test_gauss_bins_bit_exact(tile):
     room, init = _scene()
     g = gpu_run(init, room.cams, 20.0, tile=tile, flags=_flags())
     assert g["delta"] == O.gauss_extent()
-    rect, key32, ptr, ent = oracle_bins(init, room.cams, g["delta"], tile, gaussian=True)
+    rect, key32, ptr, ent, ekey = oracle_bins(init, room.cams, g["delta"], tile, gaussian=True)
     assert np.array_equal(g["rect"], rect)
     assert np.array_equal(g["key"].view(np.uint32), key32.view(np.uint32))
     assert np.array_equal(g["tile_ptr"], ptr)
     assert np.array_equal(g["tile_ent"], ent)
+    assert np.array_equal(g["tile_key"].view(np.uint32), ekey.view(np.uint32))
 
 
 @pytest.mark.parametrize("lam", [7.36, 300.0])

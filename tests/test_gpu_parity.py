@@ -57,12 +57,13 @@ def tiny_init(seed=1):
 def test_bins_bit_exact_tiny_room(tile, lam):
     room, init = tiny_init()
     g = gpu_run(init, room.cams, lam, tile=tile)
-    rect, key32, ptr, ent = oracle_bins(init, room.cams, g["delta"], tile)
+    rect, key32, ptr, ent, ekey = oracle_bins(init, room.cams, g["delta"], tile)
     assert g["status"] == 0
     assert np.array_equal(g["rect"], rect)
     assert np.array_equal(g["key"].view(np.uint32), key32.view(np.uint32))
     assert np.array_equal(g["tile_ptr"], ptr)
     assert np.array_equal(g["tile_ent"], ent)
+    assert np.array_equal(g["tile_key"].view(np.uint32), ekey.view(np.uint32))
     assert g["required"] == len(ent)
     report("bins_tiny", tile=tile, lam=lam, entries=len(ent))
 
@@ -72,10 +73,11 @@ def test_bins_bit_exact_ragged_and_clipped():
     p = S.random_planes_in_view(21, 40, depth_range=(-0.5, 3.0), half=(0.1, 1.5))
     cams = S.identity_cameras(3, 50, 70, 40.0, seed=2, jitter=0.2)
     g = gpu_run(p, cams, 20.0, tile=(16, 16))
-    rect, key32, ptr, ent = oracle_bins(p, cams, g["delta"], (16, 16))
+    rect, key32, ptr, ent, ekey = oracle_bins(p, cams, g["delta"], (16, 16))
     assert np.array_equal(g["rect"], rect)
     assert np.array_equal(g["key"].view(np.uint32), key32.view(np.uint32))
     assert np.array_equal(g["tile_ptr"], ptr) and np.array_equal(g["tile_ent"], ent)
+    assert np.array_equal(g["tile_key"].view(np.uint32), ekey.view(np.uint32))
     culled = (rect[..., 2] < rect[..., 0]).sum()
     report("bins_ragged", culled=int(culled), entries=len(ent))
     assert culled > 0
@@ -84,7 +86,7 @@ def test_bins_bit_exact_ragged_and_clipped():
 def test_capacity_overflow_reports_required():
     room, init = tiny_init()
     g = gpu_run(init, room.cams, 20.0, capacity=100)
-    rect, key32, ptr, ent = oracle_bins(init, room.cams, g["delta"], (16, 16))
+    rect, key32, ptr, ent, ekey = oracle_bins(init, room.cams, g["delta"], (16, 16))
     assert g["status"] & (1 << 3)
     assert g["required"] == len(ent)
 
@@ -299,9 +301,10 @@ def test_paper_scale_forward_sampled_rows(big_case):
     report("fwd_big", **c)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
     # bit-exact bins at full size
-    rect, key32, ptr, ent = oracle_bins(init, cams, g["delta"], (16, 16))
+    rect, key32, ptr, ent, ekey = oracle_bins(init, cams, g["delta"], (16, 16))
     assert np.array_equal(g["rect"], rect)
     assert np.array_equal(g["tile_ptr"], ptr) and np.array_equal(g["tile_ent"], ent)
+    assert np.array_equal(g["tile_key"].view(np.uint32), ekey.view(np.uint32))
 
 
 def test_paper_scale_backward_sampled_rows(big_case):

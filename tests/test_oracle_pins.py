@@ -419,7 +419,8 @@ def test_tile_lists_brute_force():
     tw, th = 16, 8
     rect, key, key32 = O.bin_records(init.center, init.quat, init.radii, cams.w2c, cams.intr,
                                      cams.H, cams.W, tw, th, O.filter_margin(7.36))
-    ptr, ent = O.tile_lists(rect, key32, cams.H, cams.W, tw, th)
+    ns = O.records_ns(init.center, init.quat, init.radii, cams.w2c)
+    ptr, ent, ekey = O.tile_lists(rect, key32, ns, cams.intr, cams.H, cams.W, tw, th)
     txn, tyn = (cams.W + tw - 1) // tw, (cams.H + th - 1) // th
     K = init.K
     for v in range(cams.V):
@@ -428,8 +429,44 @@ def test_tile_lists_brute_force():
                 t = v * txn * tyn + ty * txn + tx
                 expect = [v * K + k for k in range(K)
                           if rect[v, k, 0] <= tx <= rect[v, k, 2] and rect[v, k, 1] <= ty <= rect[v, k, 3]]
-                expect.sort(key=lambda r: (float(key32[v, r - v * K]), r))
+                kk = {r: float(O.entry_keys(ns[v, r - v * K][None], cams.intr[v][None], [tx], [ty],
+                                            tw, th, rec_key=[key32[v, r - v * K]])[0])
+                      for r in expect}
+                expect.sort(key=lambda r: (kk[r], r))
                 assert list(ent[ptr[t]:ptr[t + 1]]) == expect
+                assert [kk[r] for r in expect] == list(ekey[ptr[t]:ptr[t + 1]])
+
+
+def test_entry_keys_bound_every_depth_of_the_tile():
+    # the entry key of a (plane, tile) pair is below the depth of every candidate pixel of
+    # the tile (single-plane brute-force renders); for most pairs it is well above the
+    # record's quad key (the tile sees only part of the plane)
+    room = S.tiny_room(0)
+    init = S.perturb_planes(room.gt, 3)
+    cams = room.cams
+    tw, th = 8, 8
+    lam = 7.36
+    rect, key, key32 = O.bin_records(init.center, init.quat, init.radii, cams.w2c, cams.intr,
+                                     cams.H, cams.W, tw, th, O.filter_margin(lam))
+    ns = O.records_ns(init.center, init.quat, init.radii, cams.w2c)
+    tighter, checked = 0, 0
+    for k in range(init.K):
+        o = O.render(init.center[k:k + 1], init.quat[k:k + 1], init.radii[k:k + 1], cams.w2c,
+                     cams.intr, cams.H, cams.W, lam)
+        for v in range(cams.V):
+            vj, vi = np.nonzero(o["alpha"][v] > 0)
+            if vj.size == 0:
+                continue
+            t = o["depth"][v][vj, vi] / o["alpha"][v][vj, vi]
+            tx, ty = vi // tw, vj // th
+            ek = O.entry_keys(np.repeat(ns[v, k][None], len(tx), 0),
+                              np.repeat(cams.intr[v][None], len(tx), 0), tx, ty, tw, th,
+                              rec_key=np.full(len(tx), key32[v, k]))
+            assert np.all(t >= ek.astype(np.float64) * (1 - 1e-6)), (k, v)
+            assert np.all(ek >= key32[v, k])
+            tighter += int((ek > key32[v, k] * 1.01).sum())
+            checked += len(t)
+    assert checked > 10000 and tighter > 0.3 * checked
 
 
 def test_binning_culls_plane_behind_camera():

@@ -61,7 +61,7 @@ def test_noalloc_backward_matches_workspace_backward():
         g = torch.zeros_like(flat)
         gc, gq, gr = SP.flat_views(g, K)
         code = fn(ctypes.byref(pl), ctypes.byref(r.frame), ctypes.byref(r.settings),
-                  r.rec.data_ptr(), r.key.data_ptr(), r.tile_ptr.data_ptr(), r.tile_ent.data_ptr(),
+                  r.rec.data_ptr(), r.tile_key.data_ptr(), r.tile_ptr.data_ptr(), r.tile_ent.data_ptr(),
                   r.capacity, r.dLdD.data_ptr(), r.dLdN.data_ptr(), gc.data_ptr(), gq.data_ptr(),
                   gr.data_ptr(), r.status.data_ptr(), stream)
         assert code == B.PS_OK, B.ps_status_string(code)
@@ -76,7 +76,7 @@ def test_noalloc_backward_matches_workspace_backward():
     big.n_views, big.n_records, big.n_tiles, big.max_K = 1, 65537, 1, 65537
     big.n_pixels, big.views = 1, r.frame.views
     code = fn(ctypes.byref(pl), ctypes.byref(big), ctypes.byref(r.settings), r.rec.data_ptr(),
-              r.key.data_ptr(), r.tile_ptr.data_ptr(), r.tile_ent.data_ptr(), r.capacity,
+              r.tile_key.data_ptr(), r.tile_ptr.data_ptr(), r.tile_ent.data_ptr(), r.capacity,
               r.dLdD.data_ptr(), r.dLdN.data_ptr(), gc.data_ptr(), gq.data_ptr(), gr.data_ptr(),
               r.status.data_ptr(), stream)
     assert code == B.PS_ERR_ARG
