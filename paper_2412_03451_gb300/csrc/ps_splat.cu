@@ -259,6 +259,11 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
             unsigned m = __ballot_sync(kFull, ok);
             __syncwarp();
             while (m) {
+                // every pixel of the strip is finished: the rest of the chunk cannot matter
+                // (forward only: measured slower in the modes with the backward)
+                if constexpr (MODE == kFwd) {
+                    if (__all_sync(kFull, s.done)) break;
+                }
                 const int e = __ffs(m) - 1;
                 m &= m - 1;
                 if (!s.done) {
