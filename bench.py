@@ -575,7 +575,8 @@ def run_e2e(wl, args, first, world):
     return {"value": round(value, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(n * 4 + n * 12), "d2h_bytes_per_step": VIEWS_PER_STEP * 4 * 8,
             "ms_per_step": round(t * 1e3 / K, 4),
-            "pipeline": "copies of step s+1 on a second stream overlap step s (two device buffers)"}
+            "pipeline": "copies of step s+1 on a second stream overlap step s (two device buffers)",
+            "l2": "not flushed: every step's supervision arrives from host memory"}
 
 
 def run_ttd(wl, max_iters):
