@@ -269,13 +269,21 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                 if (!s.done) {
                     PairEval pe;
                     const int id = ws.id[e];
+                    // keys are sorted: the next entry's key bounds every later depth
+                    const float bound = ws.key[e + 1] * kMargin;
                     if (eval_pair(ws.rec[e][0], ws.rec[e][1], ws.rec[e][2], ws.rec[e][3], dx, dy,
                                   a.c, pe)) {
-                        if (!s.have_floor || cand_less(s.ft, s.fid, pe.t, id))
-                            pend_insert(s, pe.t, pe.w, id, a.M);
+                        if (!s.have_floor || cand_less(s.ft, s.fid, pe.t, id)) {
+                            // nothing pending and nothing later can come before it: composite
+                            // at once (what inserting and flushing would do)
+                            if (s.nb == 0 && pe.t < bound && (!s.ovf || cand_less(pe.t, id, s.ot, s.oid)) &&
+                                !(s.has_cut && cand_less(s.ct, s.cid, pe.t, id)))
+                                composite<MODE>(s, k, a.rec, pe.t, pe.w, id, a.M);
+                            else
+                                pend_insert(s, pe.t, pe.w, id, a.M);
+                        }
                     }
-                    // keys are sorted: the next entry's key bounds every later depth
-                    if (s.nb > 0 || s.has_cut) flush<MODE>(s, k, a.rec, ws.key[e + 1] * kMargin, a.M);
+                    if (!s.done && (s.nb > 0 || s.has_cut)) flush<MODE>(s, k, a.rec, bound, a.M);
                 }
             }
             // entries without a relevant successor in this chunk: bound by the next chunk
