@@ -41,7 +41,7 @@ using namespace ps;
 namespace {
 
 #ifndef PS_KPEND
-#define PS_KPEND 6
+#define PS_KPEND 5
 #endif
 constexpr int kPend = PS_KPEND;           // pending-pair buffer per pixel
 constexpr unsigned kFull = 0xffffffffu;
