@@ -111,3 +111,37 @@ def test_settings_validation(lib):
         code = lib.ps_splat_fwd(ctypes.byref(frame), ctypes.byref(s), dummy, dummy, dummy, dummy,
                                 1, dummy, dummy, None, dummy, 256, None, None)
         assert code == B.PS_ERR_ARG, bad
+
+
+def test_plane_set_operations_reject_bad_arguments(lib):
+    # host-side checks of the splitting and merging entry points: nothing is launched
+    from paper_2412_03451_gb300 import binding as B
+    d = ctypes.c_void_p(256)
+    split = lib.ps_split_planes
+    # no scenes, negative planes, zero iterations, negative threshold, capacity below P
+    assert split(d, None, None, 0, d, 4, d, 10, 0.2, d, None, None, d, 8, d, d, None) == B.PS_ERR_ARG
+    assert split(d, None, None, 1, d, -1, d, 10, 0.2, d, None, None, d, 8, d, d, None) == B.PS_ERR_ARG
+    assert split(d, None, None, 1, d, 4, d, 0, 0.2, d, None, None, d, 8, d, d, None) == B.PS_ERR_ARG
+    assert split(d, None, None, 1, d, 4, d, 10, -1.0, d, None, None, d, 8, d, d, None) == B.PS_ERR_ARG
+    assert split(d, None, None, 1, d, 4, d, 10, 0.2, d, None, None, d, 3, d, d, None) == B.PS_ERR_ARG
+    assert split(d, None, None, 1, None, 4, d, 10, 0.2, d, None, None, d, 8, d, d, None) == B.PS_ERR_ARG
+    centre = (ctypes.c_float * 3)(0, 0, 0)
+    merge = lib.ps_merge_planes
+    assert merge(d, 8193, centre, 25.0, 0.001, d, d, d, None) == B.PS_ERR_ARG      # above 8,192
+    assert merge(d, 4, centre, 95.0, 0.001, d, d, d, None) == B.PS_ERR_ARG        # angle > 90
+    assert merge(d, 4, centre, 25.0, -1.0, d, d, d, None) == B.PS_ERR_ARG         # negative offset
+    assert merge(d, 4, None, 25.0, 0.001, d, d, d, None) == B.PS_ERR_ARG
+    assert lib.ps_radii_grad_accum(None, None, 1.0, 4, None, None) == B.PS_ERR_ARG
+
+
+def test_gaussian_flag_checks(lib):
+    from paper_2412_03451_gb300 import binding as B
+    views, frame = B.ps_plan_views([96], [128], [0], [0, 4], np.eye(3, 4, dtype=np.float32)[None],
+                                   np.array([[100, 100, 64, 48]], np.float32), 16, 16)
+    frame.views = 256
+    dummy = ctypes.c_void_p(256)
+    for flags, delta in ((B.PS_GAUSSIAN | B.PS_HARD, B.gauss_extent()), (B.PS_GAUSSIAN, 0.0)):
+        s = B.make_settings(20.0, delta, flags=flags)
+        code = lib.ps_splat_fwd(ctypes.byref(frame), ctypes.byref(s), dummy, dummy, dummy, dummy,
+                                1, dummy, dummy, None, dummy, 256, None, None)
+        assert code == B.PS_ERR_ARG, flags
