@@ -481,7 +481,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
                     gt = fmaf(gX, pe.dvx, gt);
                     gt = fmaf(gY, pe.dvy, gt);
                     const float gvx = gX * t, gvy = gY * t;
-                    const float gs = gt / pe.den;
+                    const float gs = __fdividef(gt, pe.den);
                     const float gden = -gs * t;
                     gnx = fmaf(gden, dx, gnx);
                     gny = fmaf(gden, dy, gny);
@@ -502,7 +502,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
                 gt = fmaf(gP, pe.dv, gt);
                 const float gv = gP * t;
                 // Eq. 4: t = s / (d . n_c)
-                const float gs = gt / pe.den;
+                const float gs = __fdividef(gt, pe.den);
                 const float gden = -gs * t;
                 gnx = fmaf(gden, dx, gnx);
                 gny = fmaf(gden, dy, gny);
