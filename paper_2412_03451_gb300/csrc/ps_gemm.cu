@@ -1,21 +1,28 @@
 // ps_gemm.cu -- BF16 GEMM on the 5th-generation tensor cores (tcgen05), FP32
-// accumulation in tensor memory, for the seed-proposal network's convolutions
-// (im2col form) and linear layer.
+// accumulation in tensor memory, operands brought in by the Tensor Memory
+// Accelerator, for the seed-proposal network's convolutions (im2col form) and
+// linear layer.
 //
 //   C[M, N] = A[M, K] . B[N, K]^T (+ bias[N]) (ReLU) , A and B bf16 row-major
 //   (K contiguous), C fp32 or bf16 row-major with leading dimension ldc.
 //
-// One CTA computes a 128 x 64 tile of C.  Per 64-wide slice of K, the four
-// warps copy the A (128 x 64) and B (64 x 64) slices into shared memory in the
-// canonical K-major, non-swizzled core-matrix layout (8 rows x 16 bytes per
-// core matrix, core matrices adjacent in K 128 bytes apart, adjacent in M/N
-// 1,024 bytes apart), one thread issues four tcgen05.mma (M = 128, N = 64,
-// K = 16 each) into a 64-column FP32 accumulator in tensor memory and commits
-// them to an mbarrier; after the last slice every warp reads its 32 rows of the
-// accumulator with tcgen05.ld and applies the epilogue.  Every mbarrier wait
-// is bounded: on time-out the kernel sets an error flag, frees its tensor
-// memory and returns.
+// One CTA computes a 128 x 64 tile of C over 64-wide slices of K, two slices
+// in flight: one thread issues, per slice, 8 + 8 TMA tile copies
+// (cp.async.bulk.tensor.2d) of 8-element-wide column blocks of A (128 rows)
+// and B (64 rows) into a shared-memory stage -- each copy lands as 8-row x
+// 16-byte core matrices stacked along M/N, which is the canonical K-major,
+// non-swizzled layout with core matrices 128 bytes apart along M/N and one
+// column block apart along K -- with an mbarrier counting the bytes; once a
+// stage is full it issues four tcgen05.mma (M = 128, N = 64, K = 16) into a
+// 64-column FP32 accumulator in tensor memory and commits them to the stage's
+// second mbarrier, which frees the stage for the slice after next.  Rows past
+// M or N are zero-filled by the copies.  After the last slice every warp reads
+// its 32 rows of the accumulator with tcgen05.ld and applies the epilogue.
+// Every mbarrier wait is bounded: on time-out the kernel sets an error flag,
+// waits (bounded) for the copies and MMAs it issued, frees its tensor memory
+// and returns.
 #include <stdint.h>
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "ps_internal.cuh"
@@ -28,6 +35,10 @@ constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int kThreads = 128;
 constexpr unsigned kTmemCols = 64;           // FP32 accumulator columns (= BN)
 constexpr long long kWaitPolls = 1LL << 24;  // bounded mbarrier wait
+constexpr int kStages = 2;
+constexpr int kABytes = BM * BK * 2, kBBytes = BN * BK * 2;
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kColA = BM * 16, kColB = BN * 16;   // bytes of one 8-element column block
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -70,8 +81,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
 }
 
 struct GemmArgs {
-    const __nv_bfloat16* A;   // [M, K]
-    const __nv_bfloat16* B;   // [N, K]
     const float* bias;        // [N] or null
     float* C32;               // [M, ldc] fp32 output, or null
     __nv_bfloat16* C16;       // [M, ldc] bf16 output, or null
@@ -81,16 +90,40 @@ struct GemmArgs {
     int* err;                 // error flag (device), set on a wait time-out
 };
 
-__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs a)
+// k-slice j of A and B into stage s: 8 column blocks each, bytes counted on full[s]
+__device__ __forceinline__ void issue_slice(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sa,
+                                            uint32_t sb, uint32_t full, int j, int m0, int n0)
 {
-    __shared__ __align__(1024) uint8_t sA[BM * BK * 2];
-    __shared__ __align__(1024) uint8_t sB[BN * BK * 2];
-    __shared__ __align__(8) uint64_t bar;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(full), "r"(kStageBytes) : "memory");
+#pragma unroll
+    for (int kh = 0; kh < BK / 8; ++kh) {
+        const int x = j * BK + kh * 8;
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];"
+            :: "r"(sa + kh * kColA), "l"(reinterpret_cast<uint64_t>(tmA)), "r"(x), "r"(m0), "r"(full)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];"
+            :: "r"(sb + kh * kColB), "l"(reinterpret_cast<uint64_t>(tmB)), "r"(x), "r"(n0), "r"(full)
+            : "memory");
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                        const __grid_constant__ CUtensorMap tmB,
+                                                        GemmArgs a)
+{
+    extern __shared__ uint8_t s_dyn[];               // kStages x (A, B) stages, 1024-aligned below
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
     __shared__ uint32_t tmem_base;
     __shared__ int failed;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const uint32_t base = (smem_u32(s_dyn) + 1023u) & ~1023u;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -98,43 +131,51 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[s])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         failed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = instr_desc(BM, BN);
     const int nk = a.K / BK;
-    uint32_t phase = 0;
+    int issued = 0, consumed = 0, committed = 0;    // slices, per thread 0
 
-    for (int kt = 0; kt < nk; ++kt) {
-        // A slice: 128 rows x 8 chunks of 16 bytes; B slice: 64 rows x 8 chunks
-        for (int c = tid; c < BM * 8; c += kThreads) {
-            const int r = c >> 3, k8 = c & 7;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (m0 + r < a.M)
-                v = *reinterpret_cast<const uint4*>(a.A + (size_t)(m0 + r) * a.K + kt * BK + k8 * 8);
-            *reinterpret_cast<uint4*>(sA + ((r >> 3) * 8 + k8) * 128 + (r & 7) * 16) = v;
-        }
-        for (int c = tid; c < BN * 8; c += kThreads) {
-            const int r = c >> 3, k8 = c & 7;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (n0 + r < a.N)
-                v = *reinterpret_cast<const uint4*>(a.B + (size_t)(n0 + r) * a.K + kt * BK + k8 * 8);
-            *reinterpret_cast<uint4*>(sB + ((r >> 3) * 8 + k8) * 128 + (r & 7) * 16) = v;
-        }
-        // make the generic-proxy stores visible to the tensor cores
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    if (tid == 0 && nk > 0) {
+        const uint32_t idesc = instr_desc(BM, BN);
+        issue_slice(&tmA, &tmB, base, base + kABytes, smem_u32(&full[0]), 0, m0, n0);
+        issued = 1;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt & 1;
+            if (kt + 1 < nk) {
+                const int s1 = (kt + 1) & 1;
+                // the stage of slice kt + 1 last held slice kt - 1: wait for its MMAs
+                if (kt >= 1 && !mbar_wait(smem_u32(&empty[s1]), (uint32_t)(((kt - 1) >> 1) & 1))) {
+                    failed = 1;
+                    break;
+                }
+                const uint32_t st = base + (uint32_t)s1 * kStageBytes;
+                issue_slice(&tmA, &tmB, st, st + kABytes, smem_u32(&full[s1]), kt + 1, m0, n0);
+                issued = kt + 2;
+            }
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((kt >> 1) & 1))) {
+                failed = 1;
+                break;
+            }
+            consumed = kt + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = base + (uint32_t)s * kStageBytes, sb = sa + kABytes;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t da = smem_desc(smem_u32(sA) + kk * 256, 128, 1024);
-                const uint64_t db = smem_desc(smem_u32(sB) + kk * 256, 128, 1024);
+                // K = 16 spans two column blocks: core matrices one block apart along K,
+                // 128 bytes apart along M/N
+                const uint64_t da = smem_desc(sa + kk * 2 * kColA, kColA, 128);
+                const uint64_t db = smem_desc(sb + kk * 2 * kColB, kColB, 128);
                 const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -144,22 +185,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs a)
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&bar)) : "memory");
+                         :: "r"(smem_u32(&empty[s])) : "memory");
+            committed = kt + 1;
         }
-        // every thread waits for the MMAs to finish reading shared memory
-        if (!mbar_wait(smem_u32(&bar), phase)) {
-            if (a.err) atomicExch(a.err, 1);
+        // the accumulator is complete once the last commit has arrived
+        if (!failed && !mbar_wait(smem_u32(&empty[(nk - 1) & 1]), (uint32_t)(((nk - 1) >> 1) & 1)))
             failed = 1;
+        if (failed) {
+            if (a.err) atomicExch(a.err, 1);
+            // give copies and MMAs in flight a bounded chance to finish before the
+            // shared and tensor memory they use is released
+            for (int j = consumed; j < issued; ++j) mbar_wait(smem_u32(&full[j & 1]), (uint32_t)((j >> 1) & 1));
+            if (committed > 0)
+                mbar_wait(smem_u32(&empty[(committed - 1) & 1]), (uint32_t)(((committed - 1) >> 1) & 1));
         }
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (failed) break;
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (!failed && nk > 0) {
-        // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
-        const int row = m0 + warp * 32 + lane;
+        // epilogue: warp w reads accumulator lanes (rows) 32w .. 32w + 31 and parks them, with
+        // bias and ReLU applied, in the (now free) stage memory, rows padded to 65 floats so
+        // that neither the parking nor the row-wise read-back conflicts on banks; the tile
+        // then leaves in coalesced row segments
+        float* tile = reinterpret_cast<float*>(s_dyn + (base - smem_u32(s_dyn)));
+        const int rl = warp * 32 + lane;
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
@@ -172,32 +223,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs a)
                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < a.M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col < a.N) {
-                        float x = __uint_as_float(r[j]);
-                        if (a.bias) x += a.bias[col];
-                        if (a.relu) x = fmaxf(x, 0.f);
-                        const size_t o = (size_t)row * a.ldc + col;
-                        if (a.C32) a.C32[o] = a.accumulate ? a.C32[o] + x : x;
-                        if (a.C16) a.C16[o] = __float2bfloat16(x);
-                    }
-                }
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + j;
+                float x = __uint_as_float(r[j]);
+                if (a.bias && col < a.N) x += a.bias[col];
+                if (a.relu) x = fmaxf(x, 0.f);
+                tile[rl * (BN + 1) + c0 + j] = x;
             }
         }
-    }
-    if (failed) {
-        // give MMAs still in flight a bounded chance to finish before the
-        // tensor memory they write is freed
-        mbar_wait(smem_u32(&bar), phase);
+        __syncthreads();
+        for (int i = tid; i < BM * BN; i += kThreads) {
+            const int rr = i / BN, cc = i - rr * BN;
+            const int row = m0 + rr, col = n0 + cc;
+            if (row < a.M && col < a.N) {
+                const float x = tile[rr * (BN + 1) + cc];
+                const size_t o = (size_t)row * a.ldc + col;
+                if (a.C32) a.C32[o] = a.accumulate ? a.C32[o] + x : x;
+                if (a.C16) a.C16[o] = __float2bfloat16(x);
+            }
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      :: "r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// 2D map of a row-major bf16 matrix [rows][K], boxes of 8 columns x box_rows rows
+bool make_map(CUtensorMap* m, const void* ptr, int rows, int K, int box_rows)
+{
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t stride[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dim, stride, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -210,14 +293,22 @@ extern "C" ps_status ps_gemm_bf16(const void* A, const void* B, const float* bia
     if (M <= 0 || N <= 0 || K <= 0 || (K % BK) != 0 || ldc < N) return PS_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return PS_ERR_ARG;
     if (accumulate && !C32) return PS_ERR_ARG;
+    CUtensorMap tmA, tmB;
+    if (!make_map(&tmA, A, M, K, BM) || !make_map(&tmB, B, N, K, BN)) return PS_ERR_CUDA;
     GemmArgs a;
-    a.A = static_cast<const __nv_bfloat16*>(A);
-    a.B = static_cast<const __nv_bfloat16*>(B);
     a.bias = bias; a.C32 = C32; a.C16 = static_cast<__nv_bfloat16*>(C16);
     a.M = M; a.N = N; a.K = K; a.ldc = ldc; a.relu = relu; a.accumulate = accumulate;
     a.err = d_err;
+    const int dyn = kStages * kStageBytes + 1024;
+    static int configured[64] = {0};   // dynamic shared memory attribute, per device
+    int dev = 0;
+    PS_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        PS_CUDA_CHECK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+        if (dev >= 0 && dev < 64) configured[dev] = 1;
+    }
     dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-    k_gemm_tc<<<grid, kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    k_gemm_tc<<<grid, kThreads, dyn, reinterpret_cast<cudaStream_t>(stream)>>>(tmA, tmB, a);
     PS_LAUNCH_CHECK();
     return PS_OK;
 }
