@@ -475,3 +475,32 @@ def test_plane_ids_match_ray_caster():
     same = ids.cpu().numpy().reshape(V, H, W) == pid
     report("plane_ids", frac_same=float(same.mean()))
     assert same.mean() > 0.995
+
+
+# ---------------------------------------------------------------------------
+# The extremes of M: the largest supported list (PS_MAX_M = 64, a 64 KB stack per
+# CTA in the backward) and a single composited pair, forward and backward.
+
+@pytest.mark.parametrize("M", [64, 1])
+def test_m_extremes_forward_backward(M):
+    p = S.random_planes_in_view(31, 90, depth_range=(1.0, 3.0), half=(0.3, 0.9), fov=0.4)
+    cams = S.identity_cameras(2, 40, 56, 30.0, seed=6, jitter=0.05)
+    lam = 20.0
+    o = oracle_render(p, cams, lam, M=M)
+    if M == 64:
+        assert (o["n_sel"] > 40).any()          # lists deeper than the default M
+    rng = np.random.default_rng(8)
+    dD = rng.normal(size=o["depth"].shape)
+    dN = rng.normal(size=o["normal"].shape)
+    ill = (o["ill"] & 2) != 0
+    dD[ill] = 0
+    dN[ill] = 0
+    dD, dN = dD.astype(np.float32), dN.astype(np.float32)
+    g = gpu_run(p, cams, lam, M=M, dLdD=dD, dLdN=dN, backward=True)
+    c = compare_maps(g, o)
+    assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    gc, gq, gr = O.backward(p.center, p.quat, p.radii, cams.w2c, cams.intr, cams.H, cams.W,
+                            f32(lam), dD, dN, M=M, z_near=f32(0.01))
+    for k, ref in (("g_center", gc), ("g_quat", gq), ("g_radii", gr)):
+        nbad, worst = grad_errors(g[k], ref)
+        assert nbad == 0, (M, k, nbad, worst)
