@@ -52,7 +52,8 @@ static int plane_axes(const double* q, double* qn_out, double qhat[4],
 {
     double s = sqrt(((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3]);
     if (!(s > 0.0) || !isfinite(s)) return 0;
-    double w = q[0] / s, x = q[1] / s, y = q[2] / s, z = q[3] / s;
+    double is = 1.0 / s;
+    double w = q[0] * is, x = q[1] * is, y = q[2] * is, z = q[3] * is;
     if (qn_out) *qn_out = s;
     if (qhat) { qhat[0] = w; qhat[1] = x; qhat[2] = y; qhat[3] = z; }
     /* R = [[1-2(y^2+z^2), 2(xy-wz), 2(xz+wy)],
@@ -184,8 +185,9 @@ void or_bin_records(int K, int V,
             double umin = 0, umax = 0, vmin = 0, vmax = 0;
             int bad = 0;
             for (int i = 0; i < np; ++i) {
-                double u = fx * (P[i][0] / P[i][2]) + cx;
-                double vv = fy * (P[i][1] / P[i][2]) + cy;
+                double iz = 1.0 / P[i][2];
+                double u = fx * (P[i][0] * iz) + cx;
+                double vv = fy * (P[i][1] * iz) + cy;
                 if (isnan(u) || isnan(vv)) bad = 1;
                 if (i == 0) { umin = umax = u; vmin = vmax = vv; }
                 else {

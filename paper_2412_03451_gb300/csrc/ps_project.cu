@@ -6,7 +6,7 @@
 // The tile rectangle and depth key are computed in FP64 with correctly rounded
 // __dadd_rn/__dsub_rn/__dmul_rn/__ddiv_rn/__dsqrt_rn only, in a fixed order, so
 // that they are reproducible bit for bit by any IEEE implementation of the same
-// formula.
+// formula (divisions by |q| and by a corner's z are one reciprocal and products).
 #include <math.h>
 #include <string.h>
 #include "ps_internal.cuh"
@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
     bool ok = (qs > 0.0) && isfinite(qs);
     if (!finite || !ok) set_status(a.status, PS_ERR_NONFINITE);
     if (ok) {
-        const double w = dv(q0, qs), x = dv(q1, qs), y = dv(q2, qs), z = dv(q3, qs);
+        const double iq = dv(1.0, qs);
+        const double w = ml(q0, iq), x = ml(q1, iq), y = ml(q2, iq), z = ml(q3, iq);
         double vxw[3], vyw[3], nw[3];
         vxw[0] = sb(1.0, ml(2.0, ad(ml(y, y), ml(z, z))));
         vxw[1] = ml(2.0, ad(ml(x, y), ml(w, z)));
@@ -224,8 +225,9 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
                 double umin = 0, umax = 0, vmin = 0, vmax = 0;
                 bool bad = false;
                 for (int i = 0; i < np; ++i) {
-                    const double u = ad(ml(fx, dv(P[i][0], P[i][2])), cx);
-                    const double vv = ad(ml(fy, dv(P[i][1], P[i][2])), cy);
+                    const double iz = dv(1.0, P[i][2]);
+                    const double u = ad(ml(fx, ml(P[i][0], iz)), cx);
+                    const double vv = ad(ml(fy, ml(P[i][1], iz)), cy);
                     if (isnan(u) || isnan(vv)) bad = true;
                     if (i == 0) { umin = umax = u; vmin = vmax = vv; }
                     else {
