@@ -110,22 +110,33 @@ def patch_targets(ids, depth, intr, w2c, planes_q, y0, x0, z_ref, min_pix=64):
     return t
 
 
-def make_dataset(n_rooms=32, seed0=5000, views=16, iters=1500, device="cuda", log=print):
-    """Fits n_rooms rooms with the method and cuts their views into patches.
-    Returns (X [N, 64, 64, 4] float32, T [N, 8, 12] float32)."""
+def make_dataset(n_rooms=32, seed0=5000, views=16, iters=1500, device="cuda", log=print, chunk=48):
+    """Fits n_rooms rooms with the method (batched, chunk rooms at a time) and
+    cuts their views into patches.  Returns (X [N, 64, 64, 4] float32,
+    T [N, 8, 12] float32)."""
     t0 = time.time()
     rng = np.random.default_rng(seed0)
+    Ks = [int(rng.integers(500, 3001)) for _ in range(n_rooms)]
+    Xs, Ts = [], []
+    for c0 in range(0, n_rooms, chunk):
+        idx = list(range(c0, min(c0 + chunk, n_rooms)))
+        _cut_patches(idx, Ks, seed0, views, iters, device, Xs, Ts)
+        log("seed data: %d of %d rooms, %d patches, %.1f s" % (idx[-1] + 1, n_rooms, len(Xs),
+                                                             time.time() - t0))
+    X, T = np.stack(Xs), np.stack(Ts)
+    log("seed data: %d patches, %.2f targets per patch, %.1f s" %
+        (len(X), float(T[..., 0].sum(1).mean()), time.time() - t0))
+    return X, T
+
+
+def _cut_patches(idx, Ks, seed0, views, iters, device, Xs, Ts):
     rooms, inits = [], []
-    for i in range(n_rooms):
-        K = int(rng.integers(500, 3001))
+    for i in idx:
         room = S.large_room(seed0 + i, n_rect=2000, n_views=views)
         rooms.append(room)
-        inits.append(S.surface_init_nn(room, K, seed0 + 10000 + i))
+        inits.append(S.surface_init_nn(room, Ks[i], seed0 + 10000 + i))
     ss = BT.SceneSet(rooms, inits, device=device)
-    res = BT.fit_until(ss, list(range(n_rooms)), threshold=0.0, max_iters=iters)
-    log("seed data: fitted %d rooms x %d iterations in %.1f s (GPU %.1f s)" %
-        (n_rooms, iters, time.time() - t0, res["gpu_ms"] / 1e3))
-    Xs, Ts = [], []
+    res = BT.fit_until(ss, list(range(len(rooms))), threshold=0.0, max_iters=iters)
     for i, room in enumerate(rooms):
         c = room.cams
         flat = res["params"][i]
@@ -148,10 +159,8 @@ def make_dataset(n_rooms=32, seed0=5000, views=16, iters=1500, device="cuda", lo
                 Xs.append(x)
                 Ts.append(patch_targets(ids[v], gd[v], c.intr[v], c.w2c[v], q, y0, x0, z_ref))
         del r
-    X, T = np.stack(Xs), np.stack(Ts)
-    log("seed data: %d patches, %.2f targets per patch, %.1f s" %
-        (len(X), float(T[..., 0].sum(1).mean()), time.time() - t0))
-    return X, T
+    del ss
+    torch.cuda.empty_cache()
 
 
 def train(X, T, steps=3000, batch=256, lr=1e-3, seed=0, device="cuda", log=print):
