@@ -161,8 +161,10 @@ ps_status ps_plan_views(int n_views, const int* H, const int* W, const int* scen
    The tile rectangle and depth key come from the plane widened by
    settings->delta on every side (every pair that passes the w >= w_min filter
    lies inside), clipped to z >= z_near, projected, padded by one pixel and
-   clamped to the image; they are computed in FP64 with correctly rounded
-   + - * / sqrt only, so they are reproducible bit for bit.
+   clamped to the image.  Record, rectangle and key are computed in FP32 with
+   correctly rounded + - * / sqrt only, in a fixed order, from the float inputs
+   (delta rounded to float), so they are reproducible bit for bit; the key
+   bounds the plane's depths up to that rounding.
    rec [R][16] f32, rect [R][4] i32, key [R] f32 (device, written).
    Non-finite or zero-norm parameters cull the plane and set PS_ERR_NONFINITE. */
 ps_status ps_project_cull(const ps_planes* planes, const ps_frame* frame,

@@ -130,6 +130,8 @@ def _flags(single_radii, gaussian) -> int:
 def bin_records(center, quat, radii, w2c, intr, H, W, tile_w, tile_h, delta,
                 z_near=Z_NEAR, z_far=Z_FAR, single_radii=False, gaussian=False):
     """Tile rectangle and depth key of every (view, plane); see ps_oracle.c.
+    The binning formula runs in FP32 on inputs rounded to float (delta
+    included); key is the FP32 key as a double, key32 the same value.
     With gaussian, delta multiplies the radii (gauss_extent) instead of widening them."""
     c, q, r = _f64(center), _f64(quat), _f64(radii)
     Rt, K_ = _f64(w2c).reshape(-1, 12), _f64(intr).reshape(-1, 4)
@@ -145,7 +147,7 @@ def bin_records(center, quat, radii, w2c, intr, H, W, tile_w, tile_h, delta,
 
 def records_ns(center, quat, radii, w2c):
     """f32 (n_c, n_c . p_c) of every (view, plane) record [V, K, 4], from the same
-    FP64 operations as the bins (see ps_oracle.c)."""
+    FP32 operations as the bins (see ps_oracle.c)."""
     c, q, r = _f64(center), _f64(quat), _f64(radii)
     Rt = _f64(w2c).reshape(-1, 12)
     K, V = c.shape[0], Rt.shape[0]

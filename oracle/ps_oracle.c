@@ -126,52 +126,102 @@ static void plane_to_cam(const double* p, const double* q, const double* r,
 /* that survives the w >= w_min filter of Sec. 3.2 lies inside it.  With the */
 /* Gaussian weight of Eq. 5 (flag bit 2) every radius is multiplied by delta */
 /* instead, delta = sqrt(2 ln(1 / w_min)): exp(-q/2) >= w_min needs          */
-/* |P_X| <= delta sigma_X and |P_Y| <= delta sigma_Y.  The quad */
-/* is clipped to z >= z_near, projected, and its pixel bbox, padded by one   */
-/* pixel and clamped to the image, is divided by the tile size.  The depth   */
-/* key is the smallest z of the clipped polygon: a lower bound on the depth  */
-/* t of every surviving intersection.  Plain + - * / sqrt in FP64, no FMA.   */
+/* |P_X| <= delta sigma_X and |P_Y| <= delta sigma_Y.  The quad is clipped   */
+/* to z >= z_near, projected, and its pixel bbox, padded by one pixel and    */
+/* clamped to the image, is divided by the tile size.  The depth key is the  */
+/* smallest z of the clipped polygon, a lower bound on the depth t of every  */
+/* surviving intersection (up to the rounding of the formula).               */
+/* The formula is evaluated in FP32 (every input rounded to float, delta    */
+/* included) with plain + - * / sqrt, left to right as written, no FMA, so   */
+/* that any IEEE implementation of it gives the same integers.  It is a      */
+/* conservative bound, not part of the rendered value: the renderer below   */
+/* stays in FP64.                                                           */
 /* rect = (tx0, ty0, tx1, ty1) inclusive; culled planes get (0,0,-1,-1).     */
+
+/* The plane's camera frame in FP32, the same formulas as plane_axes and     */
+/* plane_to_cam in the same order.  Returns 0 for a zero or non-finite |q|.  */
+typedef struct {
+    float pc[3], vxc[3], vyc[3], nc[3], r[4];
+} frame_f32;
+
+static float rowf(const float* R, int i, const float a[3])
+{
+    return (R[4 * i + 0] * a[0] + R[4 * i + 1] * a[1]) + R[4 * i + 2] * a[2];
+}
+
+static int plane_frame_f32(const double* p, const double* q, const double* r,
+                           const double* Rt, int flags, frame_f32* o)
+{
+    float R[12], pf[3], vx[3], vy[3], n[3];
+    for (int i = 0; i < 12; ++i) R[i] = (float)Rt[i];
+    for (int i = 0; i < 3; ++i) pf[i] = (float)p[i];
+    float q0 = (float)q[0], q1 = (float)q[1], q2 = (float)q[2], q3 = (float)q[3];
+    float s = sqrtf(((q0 * q0 + q1 * q1) + q2 * q2) + q3 * q3);
+    if (!(s > 0.0f) || !isfinite(s)) return 0;
+    float is = 1.0f / s;
+    float w = q0 * is, x = q1 * is, y = q2 * is, z = q3 * is;
+    vx[0] = 1.0f - 2.0f * (y * y + z * z);
+    vx[1] = 2.0f * (x * y + w * z);
+    vx[2] = 2.0f * (x * z - w * y);
+    vy[0] = 2.0f * (x * y - w * z);
+    vy[1] = 1.0f - 2.0f * (x * x + z * z);
+    vy[2] = 2.0f * (y * z + w * x);
+    n[0] = 2.0f * (x * z + w * y);
+    n[1] = 2.0f * (y * z - w * x);
+    n[2] = 1.0f - 2.0f * (x * x + y * y);
+    for (int i = 0; i < 3; ++i) {
+        o->pc[i] = rowf(R, i, pf) + R[4 * i + 3];
+        o->vxc[i] = rowf(R, i, vx);
+        o->vyc[i] = rowf(R, i, vy);
+        o->nc[i] = rowf(R, i, n);
+    }
+    const int single_radii = flags & OR_SINGLE;
+    o->r[0] = (float)r[0]; o->r[1] = (float)(single_radii ? r[0] : r[1]);
+    o->r[2] = (float)r[2]; o->r[3] = (float)(single_radii ? r[2] : r[3]);
+    return 1;
+}
+
 void or_bin_records(int K, int V,
                     const double* center, const double* quat, const double* radii,
                     const double* w2c, const double* intr, int H, int W,
-                    int tile_w, int tile_h, double delta, double z_near, double z_far,
+                    int tile_w, int tile_h, double delta_d, double z_near_d, double z_far_d,
                     int flags, int* rect, double* key, float* key_f32)
 {
     const int gauss = flags & OR_GAUSS;
+    const float delta = (float)delta_d, z_near = (float)z_near_d, z_far = (float)z_far_d;
     for (int v = 0; v < V; ++v) {
         const double* Rt = w2c + 12 * v;
-        double fx = intr[4 * v + 0], fy = intr[4 * v + 1];
-        double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
+        float fx = (float)intr[4 * v + 0], fy = (float)intr[4 * v + 1];
+        float cx = (float)intr[4 * v + 2], cy = (float)intr[4 * v + 3];
         for (int k = 0; k < K; ++k) {
             int* rc = rect + 4 * ((long)v * K + k);
             rc[0] = 0; rc[1] = 0; rc[2] = -1; rc[3] = -1;
             key[(long)v * K + k] = INFINITY;
             key_f32[(long)v * K + k] = INFINITY;
-            plane_cam pc;
-            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, flags, &pc);
-            if (!pc.ok) continue;
-            double exp_ = gauss ? pc.r[0] * delta : pc.r[0] + delta;
-            double exm = gauss ? pc.r[1] * delta : pc.r[1] + delta;
-            double eyp = gauss ? pc.r[2] * delta : pc.r[2] + delta;
-            double eym = gauss ? pc.r[3] * delta : pc.r[3] + delta;
+            frame_f32 f;
+            if (!plane_frame_f32(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, flags, &f))
+                continue;
+            float exp_ = gauss ? f.r[0] * delta : f.r[0] + delta;
+            float exm = gauss ? f.r[1] * delta : f.r[1] + delta;
+            float eyp = gauss ? f.r[2] * delta : f.r[2] + delta;
+            float eym = gauss ? f.r[3] * delta : f.r[3] + delta;
             /* corners in order (+x,+y), (-x,+y), (-x,-y), (+x,-y) */
-            double ax[4] = {exp_, -exm, -exm, exp_};
-            double ay[4] = {eyp, eyp, -eym, -eym};
-            double C[4][3];
+            float ax[4] = {exp_, -exm, -exm, exp_};
+            float ay[4] = {eyp, eyp, -eym, -eym};
+            float C[4][3];
             for (int c = 0; c < 4; ++c)
                 for (int i = 0; i < 3; ++i)
-                    C[c][i] = (pc.pc[i] + ax[c] * pc.vxc[i]) + ay[c] * pc.vyc[i];
+                    C[c][i] = (f.pc[i] + ax[c] * f.vxc[i]) + ay[c] * f.vyc[i];
             /* Sutherland-Hodgman against the half space z >= z_near */
-            double P[8][3];
+            float P[8][3];
             int np = 0;
             for (int e = 0; e < 4; ++e) {
-                const double* a = C[e];
-                const double* b = C[(e + 1) & 3];
+                const float* a = C[e];
+                const float* b = C[(e + 1) & 3];
                 int ina = a[2] >= z_near, inb = b[2] >= z_near;
                 if (ina) { P[np][0] = a[0]; P[np][1] = a[1]; P[np][2] = a[2]; ++np; }
                 if (ina != inb) {
-                    double s = (z_near - a[2]) / (b[2] - a[2]);
+                    float s = (z_near - a[2]) / (b[2] - a[2]);
                     P[np][0] = a[0] + s * (b[0] - a[0]);
                     P[np][1] = a[1] + s * (b[1] - a[1]);
                     P[np][2] = z_near;
@@ -179,15 +229,15 @@ void or_bin_records(int K, int V,
                 }
             }
             if (np == 0) continue;
-            double kmin = P[0][2];
+            float kmin = P[0][2];
             for (int i = 1; i < np; ++i) if (P[i][2] < kmin) kmin = P[i][2];
             if (!(kmin < z_far)) continue;
-            double umin = 0, umax = 0, vmin = 0, vmax = 0;
+            float umin = 0, umax = 0, vmin = 0, vmax = 0;
             int bad = 0;
             for (int i = 0; i < np; ++i) {
-                double iz = 1.0 / P[i][2];
-                double u = fx * (P[i][0] * iz) + cx;
-                double vv = fy * (P[i][1] * iz) + cy;
+                float iz = 1.0f / P[i][2];
+                float u = fx * (P[i][0] * iz) + cx;
+                float vv = fy * (P[i][1] * iz) + cy;
                 if (isnan(u) || isnan(vv)) bad = 1;
                 if (i == 0) { umin = umax = u; vmin = vmax = vv; }
                 else {
@@ -198,27 +248,25 @@ void or_bin_records(int K, int V,
                 }
             }
             if (bad) continue;
-            double px0 = floor(umin) - 1.0, px1 = floor(umax) + 1.0;
-            double py0 = floor(vmin) - 1.0, py1 = floor(vmax) + 1.0;
-            if (px1 < 0.0 || px0 > (double)(W - 1) || py1 < 0.0 || py0 > (double)(H - 1)) continue;
-            if (px0 < 0.0) px0 = 0.0;
-            if (py0 < 0.0) py0 = 0.0;
-            if (px1 > (double)(W - 1)) px1 = (double)(W - 1);
-            if (py1 > (double)(H - 1)) py1 = (double)(H - 1);
+            float px0 = floorf(umin) - 1.0f, px1 = floorf(umax) + 1.0f;
+            float py0 = floorf(vmin) - 1.0f, py1 = floorf(vmax) + 1.0f;
+            const float Wm = (float)(W - 1), Hm = (float)(H - 1);
+            if (px1 < 0.0f || px0 > Wm || py1 < 0.0f || py0 > Hm) continue;
+            if (px0 < 0.0f) px0 = 0.0f;
+            if (py0 < 0.0f) py0 = 0.0f;
+            if (px1 > Wm) px1 = Wm;
+            if (py1 > Hm) py1 = Hm;
             rc[0] = (int)px0 / tile_w; rc[1] = (int)py0 / tile_h;
             rc[2] = (int)px1 / tile_w; rc[3] = (int)py1 / tile_h;
-            key[(long)v * K + k] = kmin;
-            /* largest float not above kmin (round toward -inf) */
-            float kf = (float)kmin;
-            if ((double)kf > kmin) kf = nextafterf(kf, -INFINITY);
-            key_f32[(long)v * K + k] = kf;
+            key[(long)v * K + k] = (double)kmin;
+            key_f32[(long)v * K + k] = kmin;
         }
     }
 }
 
 /* f32 camera-frame normal and offset of every (view, plane) record:         */
-/* ns[4 (v K + k) + (0..2)] = (float) n_c, ns[.. + 3] = (float) (n_c . p_c),   */
-/* from the same FP64 operations as the bins above (zeros for a degenerate    */
+/* ns[4 (v K + k) + (0..2)] = n_c, ns[.. + 3] = n_c . p_c, from the FP32     */
+/* frame of the binning specification above (zeros for a degenerate          */
 /* quaternion).  The tile-list entry keys are computed from these.            */
 void or_records_ns(int K, int V, const double* center, const double* quat, const double* radii,
                    const double* w2c, float* ns)
@@ -227,11 +275,13 @@ void or_records_ns(int K, int V, const double* center, const double* quat, const
         const double* Rt = w2c + 12 * v;
         for (int k = 0; k < K; ++k) {
             float* o = ns + 4 * ((long)v * K + k);
-            plane_cam pc;
-            plane_to_cam(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, 0, &pc);
-            if (!pc.ok) { o[0] = o[1] = o[2] = o[3] = 0.0f; continue; }
-            o[0] = (float)pc.nc[0]; o[1] = (float)pc.nc[1]; o[2] = (float)pc.nc[2];
-            o[3] = (float)dot3(pc.nc, pc.pc);
+            frame_f32 f;
+            if (!plane_frame_f32(center + 3 * k, quat + 4 * k, radii + 4 * k, Rt, 0, &f)) {
+                o[0] = o[1] = o[2] = o[3] = 0.0f;
+                continue;
+            }
+            o[0] = f.nc[0]; o[1] = f.nc[1]; o[2] = f.nc[2];
+            o[3] = (f.nc[0] * f.pc[0] + f.nc[1] * f.pc[1]) + f.nc[2] * f.pc[2];
         }
     }
 }

@@ -3,10 +3,14 @@
 // Projection follows Sec. 3.1 (Eq. 2-3: v^x, v^y, n are the columns of the
 // rotation matrix of the normalised quaternion) and Sec. 3.2 (Eq. 4: rays from
 // the camera centre, so planes are moved into the camera frame once per view).
-// The tile rectangle and depth key are computed in FP64 with correctly rounded
-// __dadd_rn/__dsub_rn/__dmul_rn/__ddiv_rn/__dsqrt_rn only, in a fixed order, so
-// that they are reproducible bit for bit by any IEEE implementation of the same
-// formula (divisions by |q| and by a corner's z are one reciprocal and products).
+// The record, the tile rectangle and the depth key are computed in FP32 with
+// correctly rounded __fadd_rn/__fsub_rn/__fmul_rn/__fdiv_rn/__fsqrt_rn only, in
+// a fixed order, so that they are reproducible bit for bit by any IEEE
+// implementation of the same formula (divisions by |q| and by a corner's z are
+// one reciprocal and products).  FP32 rather than FP64: this GPU's FP64 rate is
+// a small fraction of its FP32 rate, and the rectangle is a conservative bound
+// (widened by delta, padded by a pixel) whose exact value only has to agree
+// between implementations.
 #include <math.h>
 #include <string.h>
 #include "ps_internal.cuh"
@@ -84,13 +88,13 @@ extern "C" ps_status ps_plan_views(int n_views, const int* H, const int* W, cons
 
 namespace {
 
-__device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float ad(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sb(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ml(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float dv(float a, float b) { return __fdiv_rn(a, b); }
 
 // rows of [R|t] applied to a (left-to-right sums)
-__device__ __forceinline__ double row3(const double* R, int i, const double* a)
+__device__ __forceinline__ float row3(const float* R, int i, const float* a)
 {
     return ad(ad(ml(R[4 * i + 0], a[0]), ml(R[4 * i + 1], a[1])), ml(R[4 * i + 2], a[2]));
 }
@@ -104,7 +108,8 @@ struct ProjArgs {
     int4* rect;
     float* key;
     int* status;
-    double delta, z_near, z_far;
+    double delta;
+    float z_near, z_far;
     const ps_step_state* d_state;
     int single_radii;
     int gauss;              // PS_GAUSSIAN: radii scaled by delta instead of widened
@@ -121,11 +126,11 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
     const int p = __ldg(&vw->plane_off) + k;
     const long long r = (long long)__ldg(&vw->rec_off) + k;
 
-    double R[12];
+    float R[12];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) R[i] = (double)__ldg(&vw->w2c[i]);
-    const double fx = __ldg(&vw->fx), fy = __ldg(&vw->fy);
-    const double cx = __ldg(&vw->cx), cy = __ldg(&vw->cy);
+    for (int i = 0; i < 12; ++i) R[i] = __ldg(&vw->w2c[i]);
+    const float fx = __ldg(&vw->fx), fy = __ldg(&vw->fy);
+    const float cx = __ldg(&vw->cx), cy = __ldg(&vw->cy);
     const int H = __ldg(&vw->H), W = __ldg(&vw->W);
 
     float cf[3], qf[4], rf[4];
@@ -147,71 +152,69 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
 #pragma unroll
     for (int i = 0; i < kRecFloats; ++i) out[i] = 0.f;
 
-    const double q0 = qf[0], q1 = qf[1], q2 = qf[2], q3 = qf[3];
-    const double qs = __dsqrt_rn(ad(ad(ad(ml(q0, q0), ml(q1, q1)), ml(q2, q2)), ml(q3, q3)));
-    bool ok = (qs > 0.0) && isfinite(qs);
+    const float q0 = qf[0], q1 = qf[1], q2 = qf[2], q3 = qf[3];
+    const float qs = __fsqrt_rn(ad(ad(ad(ml(q0, q0), ml(q1, q1)), ml(q2, q2)), ml(q3, q3)));
+    bool ok = (qs > 0.f) && isfinite(qs);
     if (!finite || !ok) set_status(a.status, PS_ERR_NONFINITE);
     if (ok) {
-        const double iq = dv(1.0, qs);
-        const double w = ml(q0, iq), x = ml(q1, iq), y = ml(q2, iq), z = ml(q3, iq);
-        double vxw[3], vyw[3], nw[3];
-        vxw[0] = sb(1.0, ml(2.0, ad(ml(y, y), ml(z, z))));
-        vxw[1] = ml(2.0, ad(ml(x, y), ml(w, z)));
-        vxw[2] = ml(2.0, sb(ml(x, z), ml(w, y)));
-        vyw[0] = ml(2.0, sb(ml(x, y), ml(w, z)));
-        vyw[1] = sb(1.0, ml(2.0, ad(ml(x, x), ml(z, z))));
-        vyw[2] = ml(2.0, ad(ml(y, z), ml(w, x)));
-        nw[0] = ml(2.0, ad(ml(x, z), ml(w, y)));
-        nw[1] = ml(2.0, sb(ml(y, z), ml(w, x)));
-        nw[2] = sb(1.0, ml(2.0, ad(ml(x, x), ml(y, y))));
-        double pw[3] = {(double)cf[0], (double)cf[1], (double)cf[2]};
-        double pc[3], vxc[3], vyc[3], nc[3];
+        const float iq = dv(1.f, qs);
+        const float w = ml(q0, iq), x = ml(q1, iq), y = ml(q2, iq), z = ml(q3, iq);
+        float vxw[3], vyw[3], nw[3];
+        vxw[0] = sb(1.f, ml(2.f, ad(ml(y, y), ml(z, z))));
+        vxw[1] = ml(2.f, ad(ml(x, y), ml(w, z)));
+        vxw[2] = ml(2.f, sb(ml(x, z), ml(w, y)));
+        vyw[0] = ml(2.f, sb(ml(x, y), ml(w, z)));
+        vyw[1] = sb(1.f, ml(2.f, ad(ml(x, x), ml(z, z))));
+        vyw[2] = ml(2.f, ad(ml(y, z), ml(w, x)));
+        nw[0] = ml(2.f, ad(ml(x, z), ml(w, y)));
+        nw[1] = ml(2.f, sb(ml(y, z), ml(w, x)));
+        nw[2] = sb(1.f, ml(2.f, ad(ml(x, x), ml(y, y))));
+        float pc[3], vxc[3], vyc[3], nc[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            pc[i] = ad(row3(R, i, pw), R[4 * i + 3]);
+            pc[i] = ad(row3(R, i, cf), R[4 * i + 3]);
             vxc[i] = row3(R, i, vxw);
             vyc[i] = row3(R, i, vyw);
             nc[i] = row3(R, i, nw);
         }
         // the Gaussian extent does not depend on lambda: the schedule's margin is not used
-        const double delta = (a.d_state && !a.gauss) ? __ldg(&a.d_state->delta) : a.delta;
-        const double r0 = rf[0], r1 = a.single_radii ? (double)rf[0] : (double)rf[1];
-        const double r2 = rf[2], r3 = a.single_radii ? (double)rf[2] : (double)rf[3];
+        const float delta = (float)((a.d_state && !a.gauss) ? __ldg(&a.d_state->delta) : a.delta);
+        const float r0 = rf[0], r1 = a.single_radii ? rf[0] : rf[1];
+        const float r2 = rf[2], r3 = a.single_radii ? rf[2] : rf[3];
 
-        // record (rounded to f32)
-        out[0] = (float)nc[0]; out[1] = (float)nc[1]; out[2] = (float)nc[2];
-        out[3] = (float)ad(ad(ml(nc[0], pc[0]), ml(nc[1], pc[1])), ml(nc[2], pc[2]));
-        out[4] = (float)vxc[0]; out[5] = (float)vxc[1]; out[6] = (float)vxc[2];
-        out[7] = (float)ad(ad(ml(vxc[0], pc[0]), ml(vxc[1], pc[1])), ml(vxc[2], pc[2]));
-        out[8] = (float)vyc[0]; out[9] = (float)vyc[1]; out[10] = (float)vyc[2];
-        out[11] = (float)ad(ad(ml(vyc[0], pc[0]), ml(vyc[1], pc[1])), ml(vyc[2], pc[2]));
-        out[12] = (float)r0; out[13] = (float)r1; out[14] = (float)r2; out[15] = (float)r3;
+        out[0] = nc[0]; out[1] = nc[1]; out[2] = nc[2];
+        out[3] = ad(ad(ml(nc[0], pc[0]), ml(nc[1], pc[1])), ml(nc[2], pc[2]));
+        out[4] = vxc[0]; out[5] = vxc[1]; out[6] = vxc[2];
+        out[7] = ad(ad(ml(vxc[0], pc[0]), ml(vxc[1], pc[1])), ml(vxc[2], pc[2]));
+        out[8] = vyc[0]; out[9] = vyc[1]; out[10] = vyc[2];
+        out[11] = ad(ad(ml(vyc[0], pc[0]), ml(vyc[1], pc[1])), ml(vyc[2], pc[2]));
+        out[12] = r0; out[13] = r1; out[14] = r2; out[15] = r3;
 
         // binning: widened quad (Eq. 5 weight: scaled quad), corners (+x,+y), (-x,+y),
         // (-x,-y), (+x,-y)
-        const double exp_ = a.gauss ? ml(r0, delta) : ad(r0, delta);
-        const double exm = a.gauss ? ml(r1, delta) : ad(r1, delta);
-        const double eyp = a.gauss ? ml(r2, delta) : ad(r2, delta);
-        const double eym = a.gauss ? ml(r3, delta) : ad(r3, delta);
-        const double ax[4] = {exp_, -exm, -exm, exp_};
-        const double ay[4] = {eyp, eyp, -eym, -eym};
-        double C[4][3];
+        const float exp_ = a.gauss ? ml(r0, delta) : ad(r0, delta);
+        const float exm = a.gauss ? ml(r1, delta) : ad(r1, delta);
+        const float eyp = a.gauss ? ml(r2, delta) : ad(r2, delta);
+        const float eym = a.gauss ? ml(r3, delta) : ad(r3, delta);
+        const float ax[4] = {exp_, -exm, -exm, exp_};
+        const float ay[4] = {eyp, eyp, -eym, -eym};
+        float C[4][3];
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int i = 0; i < 3; ++i)
                 C[c][i] = ad(ad(pc[i], ml(ax[c], vxc[i])), ml(ay[c], vyc[i]));
         // clip against z >= z_near (Sutherland-Hodgman, one plane)
-        double P[8][3];
+        float P[8][3];
         int np = 0;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const double* A = C[e];
-            const double* B = C[(e + 1) & 3];
+            const float* A = C[e];
+            const float* B = C[(e + 1) & 3];
             const bool ina = A[2] >= a.z_near, inb = B[2] >= a.z_near;
             if (ina) { P[np][0] = A[0]; P[np][1] = A[1]; P[np][2] = A[2]; ++np; }
             if (ina != inb) {
-                const double s = dv(sb(a.z_near, A[2]), sb(B[2], A[2]));
+                const float s = dv(sb(a.z_near, A[2]), sb(B[2], A[2]));
                 P[np][0] = ad(A[0], ml(s, sb(B[0], A[0])));
                 P[np][1] = ad(A[1], ml(s, sb(B[1], A[1])));
                 P[np][2] = a.z_near;
@@ -219,15 +222,15 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
             }
         }
         if (np > 0) {
-            double kmin = P[0][2];
+            float kmin = P[0][2];
             for (int i = 1; i < np; ++i) if (P[i][2] < kmin) kmin = P[i][2];
             if (kmin < a.z_far) {
-                double umin = 0, umax = 0, vmin = 0, vmax = 0;
+                float umin = 0.f, umax = 0.f, vmin = 0.f, vmax = 0.f;
                 bool bad = false;
                 for (int i = 0; i < np; ++i) {
-                    const double iz = dv(1.0, P[i][2]);
-                    const double u = ad(ml(fx, ml(P[i][0], iz)), cx);
-                    const double vv = ad(ml(fy, ml(P[i][1], iz)), cy);
+                    const float iz = dv(1.f, P[i][2]);
+                    const float u = ad(ml(fx, ml(P[i][0], iz)), cx);
+                    const float vv = ad(ml(fy, ml(P[i][1], iz)), cy);
                     if (isnan(u) || isnan(vv)) bad = true;
                     if (i == 0) { umin = umax = u; vmin = vmax = vv; }
                     else {
@@ -238,17 +241,17 @@ __global__ void __launch_bounds__(128) k_project(ProjArgs a)
                     }
                 }
                 if (!bad) {
-                    double px0 = sb(floor(umin), 1.0), px1 = ad(floor(umax), 1.0);
-                    double py0 = sb(floor(vmin), 1.0), py1 = ad(floor(vmax), 1.0);
-                    const double Wm = (double)(W - 1), Hm = (double)(H - 1);
-                    if (!(px1 < 0.0 || px0 > Wm || py1 < 0.0 || py0 > Hm)) {
-                        if (px0 < 0.0) px0 = 0.0;
-                        if (py0 < 0.0) py0 = 0.0;
+                    float px0 = sb(floorf(umin), 1.f), px1 = ad(floorf(umax), 1.f);
+                    float py0 = sb(floorf(vmin), 1.f), py1 = ad(floorf(vmax), 1.f);
+                    const float Wm = (float)(W - 1), Hm = (float)(H - 1);
+                    if (!(px1 < 0.f || px0 > Wm || py1 < 0.f || py0 > Hm)) {
+                        if (px0 < 0.f) px0 = 0.f;
+                        if (py0 < 0.f) py0 = 0.f;
                         if (px1 > Wm) px1 = Wm;
                         if (py1 > Hm) py1 = Hm;
                         rc.x = (int)px0 / a.tile_w; rc.y = (int)py0 / a.tile_h;
                         rc.z = (int)px1 / a.tile_w; rc.w = (int)py1 / a.tile_h;
-                        kf = __double2float_rd(kmin);
+                        kf = kmin;
                     }
                 }
             }
@@ -284,7 +287,7 @@ extern "C" ps_status ps_project_cull(const ps_planes* planes, const ps_frame* fr
     a.center = planes->center; a.quat = planes->quat; a.radii = planes->radii;
     a.views = frame->views;
     a.rec = rec; a.rect = reinterpret_cast<int4*>(rect); a.key = key; a.status = d_status;
-    a.delta = s->delta; a.z_near = (double)s->z_near; a.z_far = (double)s->z_far;
+    a.delta = s->delta; a.z_near = s->z_near; a.z_far = s->z_far;
     a.d_state = s->d_state;
     a.single_radii = (s->flags & PS_SINGLE_RADII) ? 1 : 0;
     a.gauss = (s->flags & PS_GAUSSIAN) ? 1 : 0;

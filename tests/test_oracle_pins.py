@@ -406,8 +406,10 @@ def test_binning_covers_every_surviving_pair_and_key_bounds_depth():
             assert (vi // tw).min() >= x0 and (vi // tw).max() <= x1
             assert (vj // th).min() >= y0 and (vj // th).max() <= y1
             t = o["depth"][v][vj, vi] / o["alpha"][v][vj, vi]
-            assert t.min() >= key[v, k] * (1 - 1e-12)
-            assert float(key32[v, k]) <= key[v, k]
+            # the key is the FP32 formula's: a bound up to its few roundings (relative
+            # 1e-6 here; the splat kernels allow 1/4096)
+            assert t.min() >= key[v, k] * (1 - 1e-6)
+            assert float(key32[v, k]) == key[v, k]
             n_checked += vj.size
     assert n_checked > 10000
 
@@ -474,10 +476,10 @@ def test_binning_culls_plane_behind_camera():
     c, q, r = plane([0, 0, -2.0], [1, 0, 0, 0], [0.5, 0.5, 0.5, 0.5])
     rect, key, _ = O.bin_records(c, q, r, w2c, intr, 96, 128, 16, 16, 0.01)
     assert rect[0, 0, 2] < rect[0, 0, 0] and math.isinf(key[0, 0])
-    # a plane crossing z = 0 is clipped, not culled, and its key is z_near
+    # a plane crossing z = 0 is clipped, not culled, and its key is z_near (as a float)
     c, q, r = plane([0, 0, 0.5], [math.cos(math.pi / 4), math.sin(math.pi / 4), 0, 0], [1, 1, 1, 1])
     rect, key, _ = O.bin_records(c, q, r, w2c, intr, 96, 128, 16, 16, 0.01)
-    assert rect[0, 0, 2] >= rect[0, 0, 0] and key[0, 0] == O.Z_NEAR
+    assert rect[0, 0, 2] >= rect[0, 0, 0] and key[0, 0] == float(np.float32(O.Z_NEAR))
 
 
 # ---------------------------------------------------------------------------
