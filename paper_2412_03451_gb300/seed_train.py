@@ -15,7 +15,10 @@ new room; seeds with confidence >= 0.5 become planes in world coordinates;
 patches without a confident seed fall back to the plain initialisation (a
 random surface point of the patch with random orientation).
 
-python -m paper_2412_03451_gb300.seed_train writes the trained weights.
+python -m paper_2412_03451_gb300.seed_train writes the trained weights and
+scores them on held-out rooms.  The committed weights came from
+PS_SEED_ROOMS=200 PS_SEED_STEPS=8000 PS_SEED_EVAL_ROOMS=100 (about 11 minutes
+on one GB300); PS_SEED_EVAL_ONLY=1 scores the committed weights alone.
 """
 from __future__ import annotations
 
