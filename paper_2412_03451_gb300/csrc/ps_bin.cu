@@ -25,12 +25,16 @@
 //
 //   1. record counts: tiles covered by each record's rectangle (+ the record's
 //      first global tile and rectangle width), then an exclusive scan over
-//      records numbers every (record, tile) pair;
-//   2. pair count: one thread per pair adds 1 to its tile's counter;
-//   3. tile scan: tile_ptr = exclusive prefix sum, total -> d_required;
-//   4. scatter: one thread per pair writes its record id and entry key into a
+//      records numbers every (record, tile) pair.  The same thread marks its
+//      rectangle in a difference array over the flat (view-major, row-major)
+//      tile index: +1 where each row segment starts, -1 one past its end (the
+//      whole rectangle is one segment when it spans the full width);
+//   2. tile scan: the inclusive prefix of the difference array is the number
+//      of records covering each tile, and tile_ptr is the exclusive prefix of
+//      that, both in one pass; total -> d_required;
+//   3. scatter: one thread per pair writes its record id and entry key into a
 //      slot of its tile (unordered, via per-tile cursors);
-//   5. sort: each tile's slots by (key, record id): one warp per tile sorts up
+//   4. sort: each tile's slots by (key, record id): one warp per tile sorts up
 //      to 64 entries in registers and up to kWarpSortCap in its slice of shared
 //      memory (bitonic networks); persistent CTAs take the longer lists
 //      (bitonic up to kSortCap entries, an O(n^2) rank sort beyond).
@@ -43,19 +47,25 @@ using namespace ps;
 namespace {
 
 constexpr int kSortCap = 4096;     // entries sorted in shared memory by a CTA (32 KB of u64)
-constexpr int kWarpSortCap = 1024; // entries sorted by one warp (8 KB of u64 per warp)
+constexpr int kWarpSortCap = 256;  // entries sorted by one warp (2 KB of u64 per warp: 8 blocks per SM)
 constexpr int kSortWarps = 8;
 constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 8;      // elements per thread per scan tile
+constexpr int kScanItems = 9;      // elements per thread per scan tile (odd: a thread's run
+                                   // starts 9 words after its neighbour's, no bank conflicts)
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kFlatBlocks = 152 * 8;
 constexpr int kSortBlocks = 152 * 4;  // persistent blocks of the long-list sort
+constexpr int kPairBlock = 256;       // pairs per scatter block = pairs per chunk of the chunk table
+
+inline long long n_chunks(long long capacity) { return capacity / kPairBlock + 2; }
 
 struct BinWs {
     int* rec_cnt;       // [R + 1] tiles per record -> exclusive prefix (pair numbering)
     int4* rec_info;     // [R] first global tile, rectangle width in tiles, tiles_x, view
-    int* tile_cnt;      // [n_tiles]
+    int* tile_cnt;      // [n_tiles] difference array of the tile counts
     int* cursor;        // [n_tiles]
+    int* count;         // [n_tiles + 1] tile counts (arrays beyond one scan CTA)
+    int* chunk_first;   // [n_chunks] record holding pair c * kPairBlock
     long long* part;    // [2 * max scan tiles] scan partial sums
     int* ent_tmp;       // [capacity] unordered entries
     float* key_tmp;     // [capacity] their keys
@@ -69,7 +79,8 @@ inline size_t ws_bytes(int R, int n_tiles, long long capacity)
 {
     const int parts = 2 * (scan_tiles(R + 1) > scan_tiles(n_tiles) ? scan_tiles(R + 1) : scan_tiles(n_tiles)) + 2;
     return align_up(sizeof(int) * (size_t)(R + 1)) + align_up(sizeof(int4) * (size_t)(R > 0 ? R : 1)) +
-           2 * align_up(sizeof(int) * (size_t)n_tiles) + align_up(sizeof(long long) * (size_t)parts) +
+           2 * align_up(sizeof(int) * (size_t)n_tiles) + align_up(sizeof(int) * (size_t)(n_tiles + 1)) +
+           align_up(sizeof(long long) * (size_t)parts) + align_up(sizeof(int) * (size_t)n_chunks(capacity)) +
            2 * align_up(sizeof(int) * (size_t)(capacity > 0 ? capacity : 1));
 }
 
@@ -81,6 +92,8 @@ inline BinWs carve(void* ws, int R, int n_tiles, long long capacity)
     w.rec_info = reinterpret_cast<int4*>(p); p += align_up(sizeof(int4) * (size_t)(R > 0 ? R : 1));
     w.tile_cnt = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * (size_t)n_tiles);
     w.cursor = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * (size_t)n_tiles);
+    w.count = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * (size_t)(n_tiles + 1));
+    w.chunk_first = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * (size_t)n_chunks(capacity));
     const int parts = 2 * (scan_tiles(R + 1) > scan_tiles(n_tiles) ? scan_tiles(R + 1) : scan_tiles(n_tiles)) + 2;
     w.part = reinterpret_cast<long long*>(p); p += align_up(sizeof(long long) * (size_t)parts);
     w.ent_tmp = reinterpret_cast<int*>(p);
@@ -93,7 +106,8 @@ inline BinWs carve(void* ws, int R, int n_tiles, long long capacity)
 __global__ void __launch_bounds__(128) k_rec_count(const int4* __restrict__ rect,
                                                     const ps_view* __restrict__ views,
                                                     int* __restrict__ rec_cnt,
-                                                    int4* __restrict__ rec_info)
+                                                    int4* __restrict__ rec_info,
+                                                    int* __restrict__ diff, int n_tiles)
 {
     const int v = blockIdx.y;
     const ps_view* vw = views + v;
@@ -108,7 +122,19 @@ __global__ void __launch_bounds__(128) k_rec_count(const int4* __restrict__ rect
     if (rc.z >= rc.x && rc.w >= rc.y) {
         const int w = rc.z - rc.x + 1;
         c = w * (rc.w - rc.y + 1);
-        info = make_int4(__ldg(&vw->tile_off) + rc.y * tx + rc.x, w, tx, v);
+        const int first = __ldg(&vw->tile_off) + rc.y * tx + rc.x;
+        info = make_int4(first, w, tx, v);
+        if (w == tx) {
+            // full rows: one contiguous run of c tiles
+            atomicAdd(&diff[first], 1);
+            if (first + c < n_tiles) atomicAdd(&diff[first + c], -1);
+        } else {
+            const int last = first + (rc.w - rc.y) * tx;   // first tile of the last row
+            for (int a = first; a <= last; a += tx) {
+                atomicAdd(&diff[a], 1);
+                if (a + w < n_tiles) atomicAdd(&diff[a + w], -1);
+            }
+        }
     }
     rec_cnt[r] = c;
     rec_info[r] = info;
@@ -229,7 +255,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
 // Arrays of up to kScanOneMax elements: one CTA holds the whole array in
 // shared memory (one coalesced load pass with every load in flight), each
 // thread scans a contiguous run, a block scan joins the runs, one coalesced
-// store pass: one launch instead of three.
+// store pass: one launch instead of three.  With `twice`, the array is first
+// replaced by its inclusive prefix (a difference array becomes the counts).
 constexpr int kScanOneMax = 48 * 1024;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_one(const int* __restrict__ in, int n,
@@ -237,14 +264,28 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_one(const int* __restrict
                                                            int* __restrict__ cursor,
                                                            long long capacity,
                                                            long long* __restrict__ d_total,
-                                                           int* status)
+                                                           int* status, int twice)
 {
     extern __shared__ int s_all[];
     __shared__ long long s_warp[32];
+#pragma unroll 8
     for (int j = threadIdx.x; j < n; j += kScanThreads) s_all[j] = in[j];
     __syncthreads();
-    const int per = (n + kScanThreads - 1) / kScanThreads;
+    // contiguous runs of an odd length: the runs of a warp's threads start in 32
+    // different banks, so the strided shared-memory passes below are conflict-free
+    const int per = ((n + kScanThreads - 1) / kScanThreads) | 1;
     const int b = min((int)threadIdx.x * per, n), e = min(b + per, n);
+    if (twice) {
+        int run = 0;
+        for (int j = b; j < e; ++j) run += s_all[j];
+        long long tot;
+        long long c = block_scan_excl(run, s_warp, tot);
+        for (int j = b; j < e; ++j) {
+            c += s_all[j];
+            s_all[j] = (int)c;
+        }
+        __syncthreads();
+    }
     long long sum = 0;
     for (int j = b; j < e; ++j) sum += s_all[j];
     long long total;
@@ -268,7 +309,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_one(const int* __restrict
 }
 
 cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long long capacity,
-                           long long* part, long long* d_total, int* status, cudaStream_t st)
+                           long long* part, long long* d_total, int* status, cudaStream_t st,
+                           int* twice_tmp = nullptr)
 {
     if (n <= kScanOneMax) {
         static int configured[64] = {0};   // dynamic shared memory attribute, per device
@@ -282,8 +324,15 @@ cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long lon
             if (dev >= 0 && dev < 64) configured[dev] = 1;
         }
         k_scan_one<<<1, kScanThreads, sizeof(int) * (size_t)(n > 0 ? n : 1), st>>>(
-            in, n, out, cursor, capacity, d_total, status);
+            in, n, out, cursor, capacity, d_total, status, twice_tmp ? 1 : 0);
         return cudaGetLastError();
+    }
+    if (twice_tmp) {
+        // inclusive prefix of in = the exclusive one shifted by one (twice_tmp [n + 1])
+        cudaError_t e = scan_exclusive(in, n, twice_tmp, nullptr, (1LL << 31) - 1, part, nullptr,
+                                       nullptr, st);
+        if (e != cudaSuccess) return e;
+        in = twice_tmp + 1;
     }
     const int nparts = scan_tiles(n > 0 ? n : 1);
     k_scan_sums<<<nparts, kScanThreads, 0, st>>>(in, n, part);
@@ -293,7 +342,7 @@ cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long lon
     return cudaGetLastError();
 }
 
-// 2./4. one thread per (record, tile) pair ----------------------------------------
+// 3. one thread per (record, tile) pair ----------------------------------------
 __device__ __forceinline__ int pair_record(const int* __restrict__ off, int lo, int hi, int i)
 {
     // last r in [lo, hi] with off[r] <= i (off is non-decreasing, off[lo] <= i)
@@ -304,37 +353,33 @@ __device__ __forceinline__ int pair_record(const int* __restrict__ off, int lo, 
     return lo;
 }
 
-// Pairs base .. base + blockDim.x - 1 of a block belong to records s_rng[0] ..
-// s_rng[1]: two threads search the whole record range once, the others only
-// that narrow range.
-__device__ __forceinline__ void block_record_range(const int* __restrict__ off, int R, int E,
-                                                   int base, int* s_rng)
+// chunk_first[c] = the record holding pair c * kPairBlock, for every chunk
+// c < n_chunk that starts below the pair total (one thread per record).
+__global__ void __launch_bounds__(256) k_chunk_first(const int* __restrict__ off, int R,
+                                                      int* __restrict__ chunk_first, long long n_chunk)
 {
-    if (threadIdx.x < 2) {
-        const int i = threadIdx.x == 0 ? base : min(base + (int)blockDim.x, E) - 1;
-        s_rng[threadIdx.x] = pair_record(off, 0, R - 1, i);
-    }
-    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const long long lo = __ldg(&off[r]), hi = __ldg(&off[r + 1]);
+    for (long long c = (lo + kPairBlock - 1) / kPairBlock; c < n_chunk && c * kPairBlock < hi; ++c)
+        chunk_first[c] = r;
 }
 
-__global__ void __launch_bounds__(256) k_pair_count(const int* __restrict__ rec_off, int R,
-                                                     const int4* __restrict__ rec_info,
-                                                     int* __restrict__ tile_cnt)
+// Pairs base .. base + kPairBlock - 1 of a block belong to records s_rng[0] ..
+// s_rng[1]: the chunk table gives the records holding this chunk's first pair
+// and the next chunk's (an upper bound); beyond the table two threads search
+// the whole record range.  The other threads search only that narrow range.
+__device__ __forceinline__ void block_record_range(const int* __restrict__ off, int R, int E,
+                                                   int base, const int* __restrict__ chunk_first,
+                                                   long long n_chunk, int* s_rng)
 {
-    __shared__ int s_rng[2];
-    const int E = __ldg(&rec_off[R]);
-    for (int base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
-        block_record_range(rec_off, R, E, base, s_rng);
-        const int i = base + threadIdx.x;
-        if (i < E) {
-            const int r = pair_record(rec_off, s_rng[0], s_rng[1], i);
-            const int4 info = __ldg(&rec_info[r]);
-            const int j = i - __ldg(&rec_off[r]);
-            const int t = info.x + (j / info.y) * info.z + (j % info.y);
-            atomicAdd(&tile_cnt[t], 1);
-        }
-        __syncthreads();
+    if (threadIdx.x < 2) {
+        const long long c = base / kPairBlock + threadIdx.x;
+        const int i = threadIdx.x == 0 ? base : min(base + kPairBlock, E) - 1;
+        s_rng[threadIdx.x] = (c < n_chunk && c * kPairBlock < E) ? __ldg(&chunk_first[c])
+                                                                   : pair_record(off, 0, R - 1, i);
     }
+    __syncthreads();
 }
 
 // The entry key of the specification above.
@@ -344,32 +389,40 @@ __device__ __forceinline__ float entry_key(float4 ns, const ps_view* __restrict_
     const float fx = __ldg(&vw->fx), fy = __ldg(&vw->fy), cx = __ldg(&vw->cx), cy = __ldg(&vw->cy);
     const float xs[2] = {(float)(tx * tw), (float)(tx * tw + tw - 1)};
     const float ys[2] = {(float)(ty * th), (float)(ty * th + th - 1)};
-    float tmin = INFINITY, tmax = -INFINITY;
     int npos = 0, nneg = 0;
     bool weak = false;
+    // the corners' den of largest and of smallest magnitude
+    float dbig = 0.f, dsmall = INFINITY;
+    const float dys[2] = {__fdiv_rn(__fsub_rn(__fadd_rn(ys[0], 0.5f), cy), fy),
+                          __fdiv_rn(__fsub_rn(__fadd_rn(ys[1], 0.5f), cy), fy)};
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         const float dx = __fdiv_rn(__fsub_rn(__fadd_rn(xs[a], 0.5f), cx), fx);
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const float dy = __fdiv_rn(__fsub_rn(__fadd_rn(ys[b], 0.5f), cy), fy);
+            const float dy = dys[b];
             const float p1 = __fmul_rn(ns.x, dx), p2 = __fmul_rn(ns.y, dy);
             const float den = __fadd_rn(__fadd_rn(p1, p2), ns.z);
             const float mag = __fadd_rn(__fadd_rn(fabsf(p1), fabsf(p2)), fabsf(ns.z));
             if (!(fabsf(den) > __fmul_rn(0.01f, mag))) weak = true;
             npos += den > 0.f;
             nneg += den < 0.f;
-            const float t = __fdiv_rn(ns.w, den);
-            tmin = fminf(tmin, t);
-            tmax = fmaxf(tmax, t);
+            if (fabsf(den) > fabsf(dbig)) dbig = den;
+            if (fabsf(den) < fabsf(dsmall)) dsmall = den;
         }
     }
     if (weak || (npos != 4 && nneg != 4)) return z_near;
+    // With one sign of den at the four corners, t = s / den has one sign and its
+    // magnitude falls as |den| grows; correctly rounded division is monotone and
+    // odd, so the extremes of the four rounded quotients are the quotients by the
+    // extreme dens: the same bits as taking all four.
+    const float ta = __fdiv_rn(ns.w, dbig), tb = __fdiv_rn(ns.w, dsmall);
+    const float tmin = fminf(ta, tb), tmax = fmaxf(ta, tb);
     if (!(tmax > z_near)) return INFINITY;
     return fmaxf(tmin, z_near);
 }
 
-__global__ void __launch_bounds__(256) k_pair_scatter(const int* __restrict__ rec_off, int R,
+__global__ void __launch_bounds__(kPairBlock) k_pair_scatter(const int* __restrict__ rec_off, int R,
                                                        const int4* __restrict__ rec_info,
                                                        const int* __restrict__ tile_ptr,
                                                        int* __restrict__ cursor,
@@ -378,35 +431,40 @@ __global__ void __launch_bounds__(256) k_pair_scatter(const int* __restrict__ re
                                                        const float4* __restrict__ rec,
                                                        const float* __restrict__ rec_key,
                                                        const ps_view* __restrict__ views,
-                                                       int tw, int th, float z_near)
+                                                       int tw, int th, float z_near,
+                                                       const int* __restrict__ chunk_first,
+                                                       long long n_chunk)
 {
     __shared__ int s_rng[2];
     const int E = __ldg(&rec_off[R]);
-    for (int base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
-        block_record_range(rec_off, R, E, base, s_rng);
+    for (int base = blockIdx.x * kPairBlock; base < E; base += gridDim.x * kPairBlock) {
+        block_record_range(rec_off, R, E, base, chunk_first, n_chunk, s_rng);
         const int i = base + threadIdx.x;
         if (i < E) {
             const int r = pair_record(rec_off, s_rng[0], s_rng[1], i);
             const int4 info = __ldg(&rec_info[r]);
             const int j = i - __ldg(&rec_off[r]);
             const int t = info.x + (j / info.y) * info.z + (j % info.y);
+            // the key first, so that the slot atomic's latency overlaps nothing it waits on
+            const ps_view* vw = views + info.w;
+            const int lt = t - __ldg(&vw->tile_off);
+            const float k = fmaxf(entry_key(__ldg(&rec[4 * (size_t)r]), vw, lt % info.z, lt / info.z,
+                                            tw, th, z_near),
+                                  __ldg(&rec_key[r]));
+            const int lim = __ldg(&tile_ptr[t + 1]);
             const int pos = atomicAdd(&cursor[t], 1);
             // tile_ptr is clamped to the capacity: positions past it belong to lists
             // that did not fit and are dropped (the status word says so)
-            if (pos < __ldg(&tile_ptr[t + 1])) {
-                const ps_view* vw = views + info.w;
-                const int lt = t - __ldg(&vw->tile_off);
+            if (pos < lim) {
                 ent_tmp[pos] = r;
-                key_tmp[pos] = fmaxf(entry_key(__ldg(&rec[4 * (size_t)r]), vw, lt % info.z,
-                                               lt / info.z, tw, th, z_near),
-                                     __ldg(&rec_key[r]));
+                key_tmp[pos] = k;
             }
         }
         __syncthreads();
     }
 }
 
-// 5. sort ----------------------------------------------------------------------
+// 4. sort -----------------------------------------------------------------------
 // (key bits, record id) of slot j: keys are positive or +inf, so their bits sort like the values
 __device__ __forceinline__ unsigned long long sort_key(const float* __restrict__ key_tmp,
                                                        const int* __restrict__ ent_tmp, int j)
@@ -611,23 +669,25 @@ extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, c
     const int4* rc = reinterpret_cast<const int4*>(rect);
     if (R > 0) {
         dim3 grid((frame->max_K + 127) / 128, frame->n_views);
-        k_rec_count<<<grid, 128, 0, st>>>(rc, frame->views, w.rec_cnt, w.rec_info);
+        k_rec_count<<<grid, 128, 0, st>>>(rc, frame->views, w.rec_cnt, w.rec_info, w.tile_cnt,
+                                          frame->n_tiles);
         PS_LAUNCH_CHECK();
         // pair numbering; the total (<= n_tiles * R) is bounded by the int range check below
         if (scan_exclusive(w.rec_cnt, R, w.rec_cnt, nullptr, (1LL << 31) - 1, w.part, nullptr,
                            nullptr, st) != cudaSuccess)
             return PS_ERR_CUDA;
-        k_pair_count<<<kFlatBlocks, 256, 0, st>>>(w.rec_cnt, R, w.rec_info, w.tile_cnt);
-        PS_LAUNCH_CHECK();
     }
     if (scan_exclusive(w.tile_cnt, frame->n_tiles, tile_ptr, w.cursor, capacity, w.part,
-                       d_required, d_status, st) != cudaSuccess)
+                       d_required, d_status, st, w.count) != cudaSuccess)
         return PS_ERR_CUDA;
     if (R > 0 && capacity > 0) {
-        k_pair_scatter<<<kFlatBlocks, 256, 0, st>>>(w.rec_cnt, R, w.rec_info, tile_ptr, w.cursor,
-                                                    w.ent_tmp, w.key_tmp,
-                                                    reinterpret_cast<const float4*>(rec), key, frame->views,
-                                                    s->tile_w, s->tile_h, s->z_near);
+        k_chunk_first<<<(R + 255) / 256, 256, 0, st>>>(w.rec_cnt, R, w.chunk_first, n_chunks(capacity));
+        PS_LAUNCH_CHECK();
+        k_pair_scatter<<<kFlatBlocks, kPairBlock, 0, st>>>(w.rec_cnt, R, w.rec_info, tile_ptr, w.cursor,
+                                                           w.ent_tmp, w.key_tmp,
+                                                           reinterpret_cast<const float4*>(rec), key,
+                                                           frame->views, s->tile_w, s->tile_h, s->z_near,
+                                                           w.chunk_first, n_chunks(capacity));
         PS_LAUNCH_CHECK();
         static int configured[64] = {0};   // dynamic shared memory attribute of k_sort_warp, per device
         const int dyn = (int)(sizeof(unsigned long long) * kWarpSortCap * kSortWarps);

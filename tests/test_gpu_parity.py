@@ -83,6 +83,32 @@ def test_bins_bit_exact_ragged_and_clipped():
     assert culled > 0
 
 
+@pytest.mark.parametrize("case", ["many_tiles", "many_records"])
+def test_bins_bit_exact_beyond_one_scan_block(case):
+    # more than 49,152 tiles (the tile counts and offsets take the multi-CTA scans) or
+    # more than 49,152 records (so does the pair numbering)
+    if case == "many_tiles":
+        p = S.random_planes_in_view(31, 150, depth_range=(-0.5, 5.0), half=(0.05, 1.5))
+        cams = S.identity_cameras(11, 480, 640, 500.0, seed=4, jitter=0.2)
+        lam, n_min = 20.0 / np.e, ("tiles", 49152)
+    else:
+        p = S.random_planes_in_view(32, 5000, depth_range=(0.5, 6.0), half=(0.01, 0.08))
+        cams = S.identity_cameras(11, 96, 128, 100.0, seed=5, jitter=0.2)
+        lam, n_min = 300.0, ("records", 49152)
+    g = gpu_run(p, cams, lam, tile=(8, 8))
+    rect, key32, ptr, ent, ekey = oracle_bins(p, cams, g["delta"], (8, 8))
+    n = len(ptr) - 1 if n_min[0] == "tiles" else cams.V * p.K
+    assert n > n_min[1]
+    assert g["status"] == 0
+    assert np.array_equal(g["rect"], rect)
+    assert np.array_equal(g["key"].view(np.uint32), key32.view(np.uint32))
+    assert np.array_equal(g["tile_ptr"], ptr)
+    assert np.array_equal(g["tile_ent"], ent)
+    assert np.array_equal(g["tile_key"].view(np.uint32), ekey.view(np.uint32))
+    assert g["required"] == len(ent)
+    report("bins_large", case=case, n=n, entries=len(ent))
+
+
 def test_capacity_overflow_reports_required():
     room, init = tiny_init()
     g = gpu_run(init, room.cams, 20.0, capacity=100)
