@@ -74,7 +74,7 @@ def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:
 # DRAM bytes (read + write) per launch of the fused splat kernel from the ncu
 # capture summarised in profiles/k_splat_fused_room640_8x8.md; reported only while
 # the kernel source is the one it was taken on.
-TRAFFIC = {"splat_fused": 51588608, "src_sha": "f77561e633a1a3ef"}
+TRAFFIC = {"splat_fused": 51166976, "src_sha": "cb3f1bc62a83339a"}
 
 
 def src_hash() -> str:
@@ -432,6 +432,7 @@ def run_ours(args, rank, world, local_rank):
         room = S.large_room(1000 + rank, n_rect=N_GT, n_views=N_VIEWS, H=H, W=W, f=F)
         result["cpu_baseline"] = cpu_baseline(room, S.surface_init(room, N_INIT, 2000 + rank),
                                               args.start_ite)
+        result["cpu_baseline"]["tiny_room"] = tiny_room_timing(device)
     return result
 
 
@@ -662,6 +663,79 @@ def cpu_baseline(room, init, ite, target_s=20.0):
             "sample": "rows %d-%d of the first %d views (%d pixel-views), forward + loss + backward "
                       "of the FP64 brute-force oracle over all %d planes; %.1f s" %
                       (r0, r0 + rows, len(views), npx, N_INIT, t)}
+
+
+def tiny_room_timing(device, n_steps=50):
+    """The 64-plane room (8 views of 128x96) fitted for n_steps Adam steps, every
+    view in every step: on the GPU (eager steps, CUDA events, tile-list capacity
+    sized once at the first step's lambda, whose widening is the largest) and by
+    the FP64 oracle on the host cores (forward, loss, backward and Adam per step);
+    the oracle's step is also timed on one core."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2412_03451_gb300 import binding as B
+    from paper_2412_03451_gb300 import scenes as S
+    from paper_2412_03451_gb300 import splat as SP
+    room = S.tiny_room(0)
+    init = S.perturb_planes(room.gt, 1)
+    cams = room.cams
+    V, Ht, Wt, K = cams.V, cams.H, cams.W, init.K
+    z32 = float(np.float32(0.01))
+    D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, cams.w2c, cams.intr, Ht, Wt,
+                        z_near=z32)
+    r = SP.Renderer([Ht] * V, [Wt] * V, [0] * V, [0, K], device=device)
+    r.set_cameras(cams.w2c, cams.intr)
+    gd = torch.from_numpy(D.astype(np.float32).reshape(-1)).to(device)
+    gn = torch.from_numpy(N.astype(np.float32).reshape(-1, 3)).to(device)
+    r.ensure_capacity(SP.planes_to_flat(init.center, init.quat, init.radii, device),
+                      B.lambda_schedule(0), headroom=2.0)
+
+    def gpu_fit():
+        fit = SP.Fitter(r, SP.planes_to_flat(init.center, init.quat, init.radii, device))
+        for it in range(n_steps):
+            fit.step(gd, gn, lam=B.lambda_schedule(it))
+        return fit
+
+    gpu_fit()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r.status.zero_()
+    e0.record()
+    gpu_fit()
+    e1.record()
+    torch.cuda.synchronize()
+    gpu_s = e0.elapsed_time(e1) / 1e3
+    ok = int(r.status.item()) == 0
+
+    def oracle_steps(n):
+        p = np.concatenate([init.center.ravel(), init.quat.ravel(), init.radii.ravel()]).astype(np.float64)
+        m, v = np.zeros_like(p), np.zeros_like(p)
+        t0 = time.perf_counter()
+        for it in range(n):
+            lam = float(np.float32(O.lambda_schedule(it)))
+            c, q, rr = p[:3 * K].reshape(K, 3), p[3 * K:7 * K].reshape(K, 4), p[7 * K:].reshape(K, 4)
+            o = O.render(c, q, rr, cams.w2c, cams.intr, Ht, Wt, lam, z_near=z32)
+            _, dD, dN, _ = O.loss(o["depth"], o["normal"], D, N)
+            gc, gq, gr = O.backward(c, q, rr, cams.w2c, cams.intr, Ht, Wt, lam, dD, dN, z_near=z32)
+            g = np.concatenate([gc.ravel(), gq.ravel(), gr.ravel()])
+            a = O.adam(p[:7 * K], g[:7 * K], m[:7 * K], v[:7 * K], it + 1)
+            b = O.adam(p[7 * K:], g[7 * K:], m[7 * K:], v[7 * K:], it + 1, clamp_min=1e-3)
+            p, m, v = (np.concatenate([a[i], b[i]]) for i in range(3))
+        return time.perf_counter() - t0
+
+    cores = O.num_threads()
+    oracle_s = oracle_steps(n_steps)
+    O.set_num_threads(1)
+    try:
+        one_core = oracle_steps(2) / 2
+    finally:
+        O.set_num_threads(cores)
+    return {"workload": "64 planes, 8 views of 128x96, %d Adam steps over all views" % n_steps,
+            "gpu_s": round(gpu_s, 4), "gpu_launch": "eager steps", "gpu_status_ok": ok,
+            "oracle_s": round(oracle_s, 3), "oracle_cores": cores,
+            "oracle_single_core_s_per_step": round(one_core, 4),
+            "gpu_vs_oracle": round(oracle_s / gpu_s, 1)}
 
 
 def run_reference(args):

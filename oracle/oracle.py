@@ -84,6 +84,7 @@ def _load():
             lib.or_raycast.argtypes = [I, I, P, P, P, P, P, I, I, D, D, I, I, P, P, P]
             lib.or_adam.argtypes = [L, P, P, P, P, D, D, D, D, I, D]
             lib.or_num_threads.restype = I
+            lib.or_set_num_threads.argtypes = [I]
             _lib = lib
     return _lib
 
@@ -98,6 +99,11 @@ def _ptr(a: np.ndarray):
 
 def num_threads() -> int:
     return int(_load().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (OpenMP)."""
+    _load().or_set_num_threads(int(n))
 
 
 # --------------------------------------------------------------------------

@@ -755,3 +755,13 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the parallel regions that follow (timing on one core). */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
