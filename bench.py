@@ -55,20 +55,25 @@ N_VIEWS, VIEWS_PER_STEP, N_GT, N_INIT = 64, 8, 2000, 3000
 #     + record accumulation 16                                         = 66
 FLOP_CAND, FLOP_COMP_FWD, FLOP_COMP_BWD = 27, 12, 66
 SM_COUNT, FP32_LANES = 152, 128
-# kernels of one step: schedule advance 1 (graphs); project 1; bin: record counts 1,
-# record scan, tile scan (counts and offsets), chunk table 1, scatter 1, sorts 2 (a scan is one launch up
-# to 49,152 elements, three beyond; the tile scan six beyond); fused splat 1 + chain 1
-# (split: fwd 1, loss 1, bwd 1 + chain 1); Adam 2
+# kernels of one step: schedule advance 1 (graphs); project 1; bin: record counts 1, scans
+# (record and tile scans in one launch when both fit one CTA, 49,152 elements; beyond, the
+# record scan takes three launches plus the chunk table 1 and the tile scan six), scatter 1,
+# sorts 2; fused splat 1 + chain 1 (split: fwd 1, loss 1, bwd 1 + chain 1); Adam 2
+ONE_CTA_SCAN = 48 * 1024
 
 
 def scan_launches(n: int, twice: bool = False) -> int:
-    if n <= 48 * 1024:
+    if n <= ONE_CTA_SCAN:
         return 1
     return 6 if twice else 3
 
 
 def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:
-    binning = 5 + scan_launches(n_records) + scan_launches(n_tiles, twice=True)
+    if 0 < n_records <= ONE_CTA_SCAN and n_tiles <= ONE_CTA_SCAN:
+        scans = 1
+    else:
+        scans = (scan_launches(n_records) + 1 if n_records > 0 else 0) + scan_launches(n_tiles, True)
+    binning = 1 + scans + 3
     return (1 + 1 + binning + 2 + 2) if fused else (1 + binning + 4 + 2)
 
 # DRAM bytes (read + write) per launch of the fused splat kernel from the ncu

@@ -257,25 +257,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
 // thread scans a contiguous run, a block scan joins the runs, one coalesced
 // store pass: one launch instead of three.  With `twice`, the array is first
 // replaced by its inclusive prefix (a difference array becomes the counts).
+// With chunk_first, the store pass also writes the chunk table of the pair
+// numbering (see k_chunk_first).  One launch runs one such job per CTA.
 constexpr int kScanOneMax = 48 * 1024;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_one(const int* __restrict__ in, int n,
-                                                           int* __restrict__ out,
-                                                           int* __restrict__ cursor,
-                                                           long long capacity,
-                                                           long long* __restrict__ d_total,
-                                                           int* status, int twice)
+struct ScanJob {
+    const int* in;
+    int n;
+    int* out;             // [n + 1] exclusive prefix clamped to capacity, out[n] = total
+    int* cursor;          // optional copy of out[0 .. n)
+    long long capacity;
+    long long* d_total;   // optional
+    int* status;          // optional: PS_ERR_CAPACITY when the total exceeds capacity
+    int twice;
+    int* chunk_first;     // optional chunk table [n_chunk]
+    long long n_chunk;
+};
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_one(ScanJob j0, ScanJob j1)
 {
     extern __shared__ int s_all[];
     __shared__ long long s_warp[32];
+    const ScanJob& a = blockIdx.x == 0 ? j0 : j1;
+    const int n = a.n;
 #pragma unroll 8
-    for (int j = threadIdx.x; j < n; j += kScanThreads) s_all[j] = in[j];
+    for (int j = threadIdx.x; j < n; j += kScanThreads) s_all[j] = a.in[j];
     __syncthreads();
     // contiguous runs of an odd length: the runs of a warp's threads start in 32
     // different banks, so the strided shared-memory passes below are conflict-free
     const int per = ((n + kScanThreads - 1) / kScanThreads) | 1;
     const int b = min((int)threadIdx.x * per, n), e = min(b + per, n);
-    if (twice) {
+    if (a.twice) {
         int run = 0;
         for (int j = b; j < e; ++j) run += s_all[j];
         long long tot;
@@ -292,20 +304,46 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_one(const int* __restrict
     long long v = block_scan_excl(sum, s_warp, total);
     for (int j = b; j < e; ++j) {
         const int x = s_all[j];
-        s_all[j] = (int)(v < capacity ? v : capacity);
+        s_all[j] = (int)(v < a.capacity ? v : a.capacity);
         v += x;
     }
     __syncthreads();
+    const int last = (int)(total < a.capacity ? total : a.capacity);
     for (int j = threadIdx.x; j < n; j += kScanThreads) {
         const int x = s_all[j];
-        out[j] = x;
-        if (cursor) cursor[j] = x;
+        a.out[j] = x;
+        if (a.cursor) a.cursor[j] = x;
+        if (a.chunk_first) {
+            const long long hi = j + 1 < n ? s_all[j + 1] : last;
+            for (long long c = ((long long)x + kPairBlock - 1) / kPairBlock;
+                 c < a.n_chunk && c * kPairBlock < hi; ++c)
+                a.chunk_first[c] = j;
+        }
     }
     if (threadIdx.x == 0) {
-        out[n] = (int)(total < capacity ? total : capacity);
-        if (d_total) *d_total = total;
-        if (status && total > capacity) set_status(status, PS_ERR_CAPACITY);
+        a.out[n] = last;
+        if (a.d_total) *a.d_total = total;
+        if (a.status && total > a.capacity) set_status(a.status, PS_ERR_CAPACITY);
     }
+}
+
+// One or two single-CTA scans in one launch (both arrays <= kScanOneMax).
+cudaError_t scan_one(const ScanJob& j0, const ScanJob* j1, cudaStream_t st)
+{
+    static int configured[64] = {0};   // dynamic shared memory attribute, per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        e = cudaFuncSetAttribute(k_scan_one, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(int) * kScanOneMax));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) configured[dev] = 1;
+    }
+    int n = j0.n > 0 ? j0.n : 1;
+    if (j1 && j1->n > n) n = j1->n;
+    k_scan_one<<<j1 ? 2 : 1, kScanThreads, sizeof(int) * (size_t)n, st>>>(j0, j1 ? *j1 : j0);
+    return cudaGetLastError();
 }
 
 cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long long capacity,
@@ -313,19 +351,8 @@ cudaError_t scan_exclusive(const int* in, int n, int* out, int* cursor, long lon
                            int* twice_tmp = nullptr)
 {
     if (n <= kScanOneMax) {
-        static int configured[64] = {0};   // dynamic shared memory attribute, per device
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev < 0 || dev >= 64 || !configured[dev]) {
-            e = cudaFuncSetAttribute(k_scan_one, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(sizeof(int) * kScanOneMax));
-            if (e != cudaSuccess) return e;
-            if (dev >= 0 && dev < 64) configured[dev] = 1;
-        }
-        k_scan_one<<<1, kScanThreads, sizeof(int) * (size_t)(n > 0 ? n : 1), st>>>(
-            in, n, out, cursor, capacity, d_total, status, twice_tmp ? 1 : 0);
-        return cudaGetLastError();
+        const ScanJob j{in, n, out, cursor, capacity, d_total, status, twice_tmp ? 1 : 0, nullptr, 0};
+        return scan_one(j, nullptr, st);
     }
     if (twice_tmp) {
         // inclusive prefix of in = the exclusive one shifted by one (twice_tmp [n + 1])
@@ -667,27 +694,41 @@ extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, c
     BinWs w = carve(ws, R, frame->n_tiles, capacity);
     PS_CUDA_CHECK(cudaMemsetAsync(w.tile_cnt, 0, sizeof(int) * (size_t)frame->n_tiles, st));
     const int4* rc = reinterpret_cast<const int4*>(rect);
+    const long long nch = n_chunks(capacity);
     if (R > 0) {
         dim3 grid((frame->max_K + 127) / 128, frame->n_views);
         k_rec_count<<<grid, 128, 0, st>>>(rc, frame->views, w.rec_cnt, w.rec_info, w.tile_cnt,
                                           frame->n_tiles);
         PS_LAUNCH_CHECK();
-        // pair numbering; the total (<= n_tiles * R) is bounded by the int range check below
-        if (scan_exclusive(w.rec_cnt, R, w.rec_cnt, nullptr, (1LL << 31) - 1, w.part, nullptr,
-                           nullptr, st) != cudaSuccess)
+    }
+    // Pair numbering: offsets clamp at the int range (still non-decreasing), so pairs
+    // past it are never scattered, and the tile total then exceeds every capacity.
+    if (R > 0 && R <= kScanOneMax && frame->n_tiles <= kScanOneMax) {
+        // the pair numbering (and its chunk table) and the tile counts and offsets are
+        // independent: one launch, one CTA each
+        const ScanJob jr{w.rec_cnt, R, w.rec_cnt, nullptr, (1LL << 31) - 1, nullptr, nullptr, 0,
+                         w.chunk_first, nch};
+        const ScanJob jt{w.tile_cnt, frame->n_tiles, tile_ptr, w.cursor, capacity, d_required,
+                         d_status, 1, nullptr, 0};
+        if (scan_one(jr, &jt, st) != cudaSuccess) return PS_ERR_CUDA;
+    } else {
+        if (R > 0) {
+            if (scan_exclusive(w.rec_cnt, R, w.rec_cnt, nullptr, (1LL << 31) - 1, w.part, nullptr,
+                               nullptr, st) != cudaSuccess)
+                return PS_ERR_CUDA;
+            k_chunk_first<<<(R + 255) / 256, 256, 0, st>>>(w.rec_cnt, R, w.chunk_first, nch);
+            PS_LAUNCH_CHECK();
+        }
+        if (scan_exclusive(w.tile_cnt, frame->n_tiles, tile_ptr, w.cursor, capacity, w.part,
+                           d_required, d_status, st, w.count) != cudaSuccess)
             return PS_ERR_CUDA;
     }
-    if (scan_exclusive(w.tile_cnt, frame->n_tiles, tile_ptr, w.cursor, capacity, w.part,
-                       d_required, d_status, st, w.count) != cudaSuccess)
-        return PS_ERR_CUDA;
     if (R > 0 && capacity > 0) {
-        k_chunk_first<<<(R + 255) / 256, 256, 0, st>>>(w.rec_cnt, R, w.chunk_first, n_chunks(capacity));
-        PS_LAUNCH_CHECK();
         k_pair_scatter<<<kFlatBlocks, kPairBlock, 0, st>>>(w.rec_cnt, R, w.rec_info, tile_ptr, w.cursor,
                                                            w.ent_tmp, w.key_tmp,
                                                            reinterpret_cast<const float4*>(rec), key,
                                                            frame->views, s->tile_w, s->tile_h, s->z_near,
-                                                           w.chunk_first, n_chunks(capacity));
+                                                           w.chunk_first, nch);
         PS_LAUNCH_CHECK();
         static int configured[64] = {0};   // dynamic shared memory attribute of k_sort_warp, per device
         const int dyn = (int)(sizeof(unsigned long long) * kWarpSortCap * kSortWarps);

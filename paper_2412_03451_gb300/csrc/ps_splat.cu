@@ -862,7 +862,7 @@ struct LaunchCache {
 };
 
 template <int TW, int TH, int MODE>
-cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st)
+cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool counter_zeroed)
 {
     constexpr int NS = TW * TH / 32;
     a.n_items = n_tiles * NS;
@@ -892,8 +892,10 @@ cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st)
     const int need = (a.n_items + kWarps - 1) / kWarps;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
+    if (!counter_zeroed) {
+        e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
     k_splat<TW, TH, MODE><<<blocks, kWarps * 32, dyn, st>>>(a);
     return cudaGetLastError();
 }
@@ -931,11 +933,12 @@ SplatConst make_const(const ps_settings* s)
 }
 
 template <int MODE>
-cudaError_t dispatch(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st)
+cudaError_t dispatch(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
+                     bool counter_zeroed = false)
 {
-    if (s->tile_w == 16) return launch_splat<16, 16, MODE>(a, n_tiles, s->M, st);
-    if (s->tile_w == 8) return launch_splat<8, 8, MODE>(a, n_tiles, s->M, st);
-    return launch_splat<32, 8, MODE>(a, n_tiles, s->M, st);
+    if (s->tile_w == 16) return launch_splat<16, 16, MODE>(a, n_tiles, s->M, st, counter_zeroed);
+    if (s->tile_w == 8) return launch_splat<8, 8, MODE>(a, n_tiles, s->M, st, counter_zeroed);
+    return launch_splat<32, 8, MODE>(a, n_tiles, s->M, st, counter_zeroed);
 }
 
 template <int TW, int TH>
@@ -1023,7 +1026,8 @@ extern "C" ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* f, co
     if (f->n_records == 0) return PS_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t grec_bytes = sizeof(float4) * 4 * (size_t)f->n_records;
-    PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, grec_bytes, st));
+    // the record gradients and the work counter after them: one memset
+    PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, grec_bytes + sizeof(int), st));
     SplatArgs a{};
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
@@ -1031,7 +1035,7 @@ extern "C" ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* f, co
     a.c = make_const(s); a.M = s->M; a.d_state = s->d_state;
     a.dLdD = dLdD; a.dLdN = dLdN; a.g_rec = reinterpret_cast<float4*>(ws); a.status = d_status;
     a.counter = reinterpret_cast<int*>(static_cast<char*>(ws) + grec_bytes);
-    if (dispatch<kBwd>(a, s, f->n_tiles, st) != cudaSuccess) return PS_ERR_CUDA;
+    if (dispatch<kBwd>(a, s, f->n_tiles, st, true) != cudaSuccess) return PS_ERR_CUDA;
     ChainArgs c;
     c.views = f->views; c.center = planes->center; c.quat = planes->quat; c.radii = planes->radii;
     c.g_rec = a.g_rec; c.g_center = g_center; c.g_quat = g_quat; c.g_radii = g_radii;
@@ -1060,7 +1064,8 @@ extern "C" ps_status ps_splat_fused(const ps_planes* planes, const ps_frame* f,
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     PS_CUDA_CHECK(cudaMemsetAsync(view_sums, 0, sizeof(double) * 4 * (size_t)f->n_views, st));
     const size_t grec_bytes = sizeof(float4) * 4 * (size_t)f->n_records;
-    if (grec_bytes) PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, grec_bytes, st));
+    // the record gradients and the work counter after them: one memset
+    PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, grec_bytes + sizeof(int), st));
     SplatArgs a{};
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
@@ -1072,7 +1077,7 @@ extern "C" ps_status ps_splat_fused(const ps_planes* planes, const ps_frame* f,
     a.gt_depth = gt_depth; a.gt_normal = gt_normal;
     a.out_dLdD = dL_dD; a.out_dLdN = dL_dN; a.view_sums = view_sums;
     a.a_cos = s->a_cos; a.a_l1n = s->a_l1n; a.a_depth = s->a_depth;
-    if (dispatch<kFused>(a, s, f->n_tiles, st) != cudaSuccess) return PS_ERR_CUDA;
+    if (dispatch<kFused>(a, s, f->n_tiles, st, true) != cudaSuccess) return PS_ERR_CUDA;
     if (f->n_records == 0) return PS_OK;
     ChainArgs c;
     c.views = f->views; c.center = planes->center; c.quat = planes->quat; c.radii = planes->radii;
