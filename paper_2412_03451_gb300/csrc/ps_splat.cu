@@ -92,36 +92,42 @@ struct WarpStage {
 
 __device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
 
+// A candidate's place in the (t, id) order as one 64-bit key: t is positive
+// (t > z_near > 0), so its bits order like its value, and the record id breaks
+// ties.  kNoKey (all ones) is above every key.
+typedef unsigned long long CKey;
+constexpr CKey kNoKey = ~0ull;
+
+__device__ __forceinline__ CKey ckey(float t, int id)
+{
+    return ((CKey)__float_as_uint(t) << 32) | (unsigned)id;
+}
+__device__ __forceinline__ float key_t(CKey k) { return __uint_as_float((unsigned)(k >> 32)); }
+__device__ __forceinline__ int key_id(CKey k) { return (int)(unsigned)(k & 0xffffffffu); }
+
 // Per-pixel walk state.
 struct Walk {
     float T;
     int cnt;
     bool done;
     int nb;
-    float bt[kPend], bw[kPend];
-    int bid[kPend];
-    bool have_floor;
-    float ft;
-    int fid;
-    bool ovf;
-    float ot;
-    int oid;
-    bool has_cut;     // nearest opaque (w = 1) candidate, or the M-th candidate
-    float ct;
-    int cid;
+    CKey bk[kPend];   // pending candidates, ascending
+    float bw[kPend];
+    CKey floor_;      // last composited candidate (0: none yet)
+    CKey ovf;         // smallest candidate dropped from a full buffer (kNoKey: none)
+    CKey cut;         // nearest opaque (w = 1) candidate, or the M-th candidate (kNoKey: none)
 };
 
-__device__ __forceinline__ void drop_note(Walk& s, float t, int id)
+__device__ __forceinline__ void drop_note(Walk& s, CKey k)
 {
-    if (!s.ovf || cand_less(t, id, s.ot, s.oid)) { s.ot = t; s.oid = id; }
-    s.ovf = true;
+    if (k < s.ovf) s.ovf = k;
 }
 
-__device__ __forceinline__ void set_cut(Walk& s, float t, int id)
+__device__ __forceinline__ void set_cut(Walk& s, CKey k)
 {
-    if (!s.has_cut || cand_less(t, id, s.ct, s.cid)) { s.ct = t; s.cid = id; s.has_cut = true; }
+    if (k < s.cut) s.cut = k;
     // pairs dropped from a full buffer that lie strictly behind the cut can never count
-    if (s.ovf && cand_less(s.ct, s.cid, s.ot, s.oid)) s.ovf = false;
+    if (s.cut < s.ovf) s.ovf = kNoKey;
 }
 
 // Adds a candidate.  Candidates behind the cut are dropped: nothing behind an
@@ -129,39 +135,38 @@ __device__ __forceinline__ void set_cut(Walk& s, float t, int id)
 // opaque candidate becomes the cut and truncates the pending pairs behind it;
 // when composited + pending exceeds M the largest pending pair is beyond the
 // top M and goes, and the new M-th pair becomes the cut.
-__device__ __forceinline__ void pend_insert(Walk& s, float t, float w, int id, int M)
+__device__ __forceinline__ void pend_insert(Walk& s, CKey key, float w, int M)
 {
-    if (s.has_cut && cand_less(s.ct, s.cid, t, id)) return;     // strictly behind the cut
+    if (s.cut < key) return;     // strictly behind the cut
     if (s.nb == kPend) {
-        if (!cand_less(t, id, s.bt[kPend - 1], s.bid[kPend - 1])) { drop_note(s, t, id); return; }
-        drop_note(s, s.bt[kPend - 1], s.bid[kPend - 1]);
+        if (!(key < s.bk[kPend - 1])) { drop_note(s, key); return; }
+        drop_note(s, s.bk[kPend - 1]);
         s.nb = kPend - 1;
     }
     int pos = 0;
 #pragma unroll
     for (int i = kPend - 1; i >= 1; --i) {
         if (i <= s.nb) {
-            if (cand_less(t, id, s.bt[i - 1], s.bid[i - 1])) {
-                s.bt[i] = s.bt[i - 1]; s.bw[i] = s.bw[i - 1]; s.bid[i] = s.bid[i - 1];
+            if (key < s.bk[i - 1]) {
+                s.bk[i] = s.bk[i - 1]; s.bw[i] = s.bw[i - 1];
             } else if (pos == 0) {
-                s.bt[i] = t; s.bw[i] = w; s.bid[i] = id; pos = i;
+                s.bk[i] = key; s.bw[i] = w; pos = i;
             }
         }
     }
-    if (pos == 0) { s.bt[0] = t; s.bw[0] = w; s.bid[0] = id; }
+    if (pos == 0) { s.bk[0] = key; s.bw[0] = w; }
     ++s.nb;
     if (w == 1.f) {
-        set_cut(s, t, id);
+        set_cut(s, key);
         s.nb = pos + 1;          // pending pairs behind an opaque one can never count
     }
     if (s.cnt + s.nb > M) {      // the largest pending pair is beyond the top M
         s.nb = M - s.cnt;
-        float lt = s.bt[0];
-        int lid = s.bid[0];
+        CKey lk = s.bk[0];
 #pragma unroll
         for (int i = 1; i < kPend; ++i)
-            if (i < s.nb) { lt = s.bt[i]; lid = s.bid[i]; }
-        set_cut(s, lt, lid);
+            if (i < s.nb) lk = s.bk[i];
+        set_cut(s, lk);
     }
 }
 
@@ -169,7 +174,7 @@ __device__ __forceinline__ void pend_pop(Walk& s)
 {
 #pragma unroll
     for (int i = 0; i < kPend - 1; ++i) {
-        s.bt[i] = s.bt[i + 1]; s.bw[i] = s.bw[i + 1]; s.bid[i] = s.bid[i + 1];
+        s.bk[i] = s.bk[i + 1]; s.bw[i] = s.bw[i + 1];
     }
     --s.nb;
 }
@@ -203,9 +208,7 @@ __device__ __forceinline__ void composite(Walk& s, Sink& k, const float4* __rest
     }
     s.T = s.T * (1.f - w);
     ++s.cnt;
-    s.have_floor = true;
-    s.ft = t;
-    s.fid = id;
+    s.floor_ = ckey(t, id);
     if (s.cnt >= M || s.T == 0.f) s.done = true;
 }
 
@@ -213,18 +216,18 @@ template <int MODE>
 __device__ __forceinline__ void flush(Walk& s, Sink& k, const float4* __restrict__ rec,
                                       float bound, int M)
 {
-    // every later candidate lies behind the cut: nothing else can enter
-    const bool final_ = s.has_cut && bound > s.ct;
+    // every later candidate lies behind the cut: nothing else can enter (no cut: NaN, false)
+    const bool final_ = bound > key_t(s.cut);
     if (final_) bound = INFINITY;
     while (s.nb > 0 && !s.done) {
-        if (!(s.bt[0] < bound)) break;
-        if (s.ovf && !cand_less(s.bt[0], s.bid[0], s.ot, s.oid)) break;
-        const float t = s.bt[0], w = s.bw[0];
-        const int id = s.bid[0];
+        const CKey k0 = s.bk[0];
+        if (!(key_t(k0) < bound)) break;
+        if (!(k0 < s.ovf)) break;
+        const float w = s.bw[0];
         pend_pop(s);
-        composite<MODE>(s, k, rec, t, w, id, M);
+        composite<MODE>(s, k, rec, key_t(k0), w, key_id(k0), M);
     }
-    if (final_ && s.nb == 0 && !s.ovf) s.done = true;
+    if (final_ && s.nb == 0 && s.ovf == kNoKey) s.done = true;
 }
 
 // Walks one tile list for the warp's 32 pixels.
@@ -273,29 +276,29 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                     const float bound = ws.key[e + 1] * kMargin;
                     if (eval_pair(ws.rec[e][0], ws.rec[e][1], ws.rec[e][2], ws.rec[e][3], dx, dy,
                                   a.c, pe)) {
-                        if (!s.have_floor || cand_less(s.ft, s.fid, pe.t, id)) {
+                        const CKey key = ckey(pe.t, id);
+                        if (s.floor_ < key) {
                             // nothing pending and nothing later can come before it: composite
                             // at once (what inserting and flushing would do)
-                            if (s.nb == 0 && pe.t < bound && (!s.ovf || cand_less(pe.t, id, s.ot, s.oid)) &&
-                                !(s.has_cut && cand_less(s.ct, s.cid, pe.t, id)))
+                            if (s.nb == 0 && pe.t < bound && key < s.ovf && !(s.cut < key))
                                 composite<MODE>(s, k, a.rec, pe.t, pe.w, id, a.M);
                             else
-                                pend_insert(s, pe.t, pe.w, id, a.M);
+                                pend_insert(s, key, pe.w, a.M);
                         }
                     }
-                    if (!s.done && (s.nb > 0 || s.has_cut)) flush<MODE>(s, k, a.rec, bound, a.M);
+                    if (!s.done && (s.nb > 0 || s.cut != kNoKey)) flush<MODE>(s, k, a.rec, bound, a.M);
                 }
             }
             // entries without a relevant successor in this chunk: bound by the next chunk
-            if (!s.done && (s.nb > 0 || s.has_cut)) flush<MODE>(s, k, a.rec, ws.key[32] * kMargin, a.M);
+            if (!s.done && (s.nb > 0 || s.cut != kNoKey)) flush<MODE>(s, k, a.rec, ws.key[32] * kMargin, a.M);
             __syncwarp();
         }
         // end of list: everything pending below the smallest dropped pair is final
         flush<MODE>(s, k, a.rec, INFINITY, a.M);
-        const bool again = !s.done && s.ovf;
+        const bool again = !s.done && s.ovf != kNoKey;
         if (!again) s.done = true;
         if (!__any_sync(kFull, again)) break;
-        if (again) { s.ovf = false; s.nb = 0; }
+        if (again) { s.ovf = kNoKey; s.nb = 0; }
     }
 }
 
@@ -337,9 +340,8 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
     const int end = (int)min((long long)__ldg(&a.tile_ptr[tile + 1]), a.capacity);
 
     Walk s;
-    s.T = 1.f; s.cnt = 0; s.nb = 0; s.have_floor = false; s.ft = 0.f; s.fid = 0;
-    s.ovf = false; s.ot = 0.f; s.oid = 0;
-    s.has_cut = false; s.ct = 0.f; s.cid = 0;
+    s.T = 1.f; s.cnt = 0; s.nb = 0;
+    s.floor_ = 0ull; s.ovf = kNoKey; s.cut = kNoKey;
     s.done = !inside;
     Sink k;
     k.acc = Accum{0.f, 0.f, 0.f, 0.f, 0.f, -1};
