@@ -108,6 +108,9 @@ def parse():
     ap.add_argument("--ablation-variants", default="plain,mono,sphere,single_radii,split,split_low,gaussian")
     ap.add_argument("--profile-case", action="store_true",
                     help="for ncu: set up, warm up 3 steps, run one step inside a profiler range, exit")
+    ap.add_argument("--profile-gemm", action="store_true",
+                    help="the seed network's tcgen05 GEMM (65,536 x 64 x 576): time it, then run one "
+                         "inside a profiler range (for ncu), exit")
     return ap.parse_args()
 
 
@@ -806,10 +809,48 @@ def profile_case(args):
     return 0 if status == 0 else 1
 
 
+def profile_gemm(args):
+    """The seed network's inner-layer GEMM (im2col rows of 64 patches' 32x32
+    outputs, 64 channels, K = 9 x 64): bf16 operands, FP32 output; 50 timed
+    launches (CUDA events), then one inside cudaProfilerStart/Stop."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2412_03451_gb300 import binding as B
+    M, N, K = 65536, 64, 576
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn(M, K, device="cuda", generator=g).bfloat16()
+    Bm = torch.randn(N, K, device="cuda", generator=g).bfloat16()
+    C = torch.empty(M, N, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        B.ps_gemm_bf16(A, Bm, None, C, None, err=err)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(50):
+        B.ps_gemm_bf16(A, Bm, None, C, None, err=err)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 50
+    torch.cuda.cudart().cudaProfilerStart()
+    B.ps_gemm_bf16(A, Bm, None, C, None, err=err)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    ok = bool(torch.allclose(C, A.float() @ Bm.float().T, rtol=1e-4, atol=1e-3 * K ** 0.5))
+    nbytes = (M * K + N * K) * 2 + M * N * 4
+    print(json.dumps({"profile_gemm": "%dx%dx%d" % (M, N, K), "us": round(ms * 1e3, 2),
+                      "TFLOP/s": round(2 * M * N * K / ms / 1e9, 1), "GB/s": round(nbytes / ms / 1e6, 0),
+                      "matches_fp32_matmul": ok, "error_word": int(err.item())}))
+    return 0 if ok and int(err.item()) == 0 else 1
+
+
 def main():
     args = parse()
     if args.profile_case:
         return profile_case(args)
+    if args.profile_gemm:
+        return profile_gemm(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
