@@ -39,7 +39,8 @@
  *   {n_c, n_c.p_c, v^x_c, v^x_c.p_c, v^y_c, v^y_c.p_c, r^x+, r^x-, r^y+, r^y-},
  *   its tile rectangle (4 ints, inclusive, empty = (0,0,-1,-1)) and its depth
  *   key (1 float: smallest camera z of the plane widened by the filter margin,
- *   rounded down to f32; a record whose key is >= z_far is culled).
+ *   evaluated in FP32, see ps_project_cull; a record whose key is >= z_far is
+ *   culled).
  *
  * Tiles: each view is cut into tile_w x tile_h pixel tiles, numbered
  *   row-major within a view and concatenated over views.  A tile list holds the
