@@ -6,17 +6,17 @@
 //   C[M, N] = A[M, K] . B[N, K]^T (+ bias[N]) (ReLU) , A and B bf16 row-major
 //   (K contiguous), C fp32 or bf16 row-major with leading dimension ldc.
 //
-// One CTA computes a 128 x 64 tile of C over 64-wide slices of K, two slices
-// in flight: one thread issues, per slice, 8 + 8 TMA tile copies
-// (cp.async.bulk.tensor.2d) of 8-element-wide column blocks of A (128 rows)
-// and B (64 rows) into a shared-memory stage -- each copy lands as 8-row x
-// 16-byte core matrices stacked along M/N, which is the canonical K-major,
-// non-swizzled layout with core matrices 128 bytes apart along M/N and one
-// column block apart along K -- with an mbarrier counting the bytes; once a
-// stage is full it issues four tcgen05.mma (M = 128, N = 64, K = 16) into a
-// 64-column FP32 accumulator in tensor memory and commits them to the stage's
-// second mbarrier, which frees the stage for the slice after next.  Rows past
-// M or N are zero-filled by the copies.  After the last slice every warp reads
+// One CTA computes a 128 x 64 tile of C over 64-wide slices of K with
+// kStages slices in flight: one thread issues, per slice, one TMA tile copy
+// (cp.async.bulk.tensor.2d, 128-byte swizzle) of A (128 rows x 128 bytes) and
+// one of B (64 rows) into a shared-memory stage -- rows of 128 bytes in
+// 8-row, 1024-byte swizzle atoms, the canonical K-major SWIZZLE_128B layout --
+// with an mbarrier counting the bytes; once a stage is full it issues four
+// tcgen05.mma (M = 128, N = 64, K = 16; each K step starts 32 bytes further
+// into the atom rows) into a 64-column FP32 accumulator in tensor memory and
+// commits them to the stage's second mbarrier; the stage is refilled with the
+// slice kStages ahead once those MMAs are done.  Rows past M or N and columns
+// past K are zero-filled by the copies.  After the last slice every warp reads
 // its 32 rows of the accumulator with tcgen05.ld and applies the epilogue.
 // Every mbarrier wait is bounded: on time-out the kernel sets an error flag,
 // waits (bounded) for the copies and MMAs it issued, frees its tensor memory
@@ -35,26 +35,31 @@ constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int kThreads = 128;
 constexpr unsigned kTmemCols = 64;           // FP32 accumulator columns (= BN)
 constexpr long long kWaitPolls = 1LL << 24;  // bounded mbarrier wait
-constexpr int kStages = 2;
-constexpr int kABytes = BM * BK * 2, kBBytes = BN * BK * 2;
+#ifndef PS_GEMM_STAGES
+#define PS_GEMM_STAGES 2
+#endif
+constexpr int kStages = PS_GEMM_STAGES;
+constexpr int kABytes = BM * BK * 2, kBBytes = BN * BK * 2;   // multiples of the 1024-byte atom
 constexpr int kStageBytes = kABytes + kBBytes;
-constexpr int kColA = BM * 16, kColB = BN * 16;   // bytes of one 8-element column block
+static_assert(kStages >= 2 && kStages * kStageBytes >= BM * (BN + 1) * 4, "epilogue tile fits the stages");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor (K-major, no swizzle): start address, leading
-// byte offset (between core matrices adjacent in K), stride byte offset
-// (between core matrices adjacent in M/N), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+// Shared-memory matrix descriptor, K-major with 128-byte swizzle: start address,
+// leading byte offset (unused by this layout when one MMA's K fits an atom row;
+// 16 bytes), stride byte offset 1024 (between 8-row atoms along M/N), descriptor
+// version 1, base offset 0 (atoms 1024-byte aligned), layout type 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -90,26 +95,24 @@ struct GemmArgs {
     int* err;                 // error flag (device), set on a wait time-out
 };
 
-// k-slice j of A and B into stage s: 8 column blocks each, bytes counted on full[s]
+// k-slice j of A and B into the stage at sa / sb: one box each (x = j * 64 elements,
+// 128 bytes: TMA-aligned), bytes counted on the stage's full barrier
 __device__ __forceinline__ void issue_slice(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sa,
                                             uint32_t sb, uint32_t full, int j, int m0, int n0)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  :: "r"(full), "r"(kStageBytes) : "memory");
-#pragma unroll
-    for (int kh = 0; kh < BK / 8; ++kh) {
-        const int x = j * BK + kh * 8;
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3}], [%4];"
-            :: "r"(sa + kh * kColA), "l"(reinterpret_cast<uint64_t>(tmA)), "r"(x), "r"(m0), "r"(full)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3}], [%4];"
-            :: "r"(sb + kh * kColB), "l"(reinterpret_cast<uint64_t>(tmB)), "r"(x), "r"(n0), "r"(full)
-            : "memory");
-    }
+    const int x = j * BK;
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(sa), "l"(reinterpret_cast<uint64_t>(tmA)), "r"(x), "r"(m0), "r"(full)
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(sb), "l"(reinterpret_cast<uint64_t>(tmB)), "r"(x), "r"(n0), "r"(full)
+        : "memory");
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
@@ -148,22 +151,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 
     if (tid == 0 && nk > 0) {
         const uint32_t idesc = instr_desc(BM, BN);
-        issue_slice(&tmA, &tmB, base, base + kABytes, smem_u32(&full[0]), 0, m0, n0);
-        issued = 1;
+        // the first kStages slices, one per stage
+        for (int j = 0; j < nk && j < kStages; ++j) {
+            const uint32_t st = base + (uint32_t)j * kStageBytes;
+            issue_slice(&tmA, &tmB, st, st + kABytes, smem_u32(&full[j]), j, m0, n0);
+            issued = j + 1;
+        }
         for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt & 1;
-            if (kt + 1 < nk) {
-                const int s1 = (kt + 1) & 1;
-                // the stage of slice kt + 1 last held slice kt - 1: wait for its MMAs
-                if (kt >= 1 && !mbar_wait(smem_u32(&empty[s1]), (uint32_t)(((kt - 1) >> 1) & 1))) {
-                    failed = 1;
-                    break;
-                }
-                const uint32_t st = base + (uint32_t)s1 * kStageBytes;
-                issue_slice(&tmA, &tmB, st, st + kABytes, smem_u32(&full[s1]), kt + 1, m0, n0);
-                issued = kt + 2;
-            }
-            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((kt >> 1) & 1))) {
+            const int s = kt % kStages;
+            // the u-th use of a stage completes its barriers' phase u: parity (slice / kStages) & 1
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((kt / kStages) & 1))) {
                 failed = 1;
                 break;
             }
@@ -172,10 +169,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             const uint32_t sa = base + (uint32_t)s * kStageBytes, sb = sa + kABytes;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-                // K = 16 spans two column blocks: core matrices one block apart along K,
-                // 128 bytes apart along M/N
-                const uint64_t da = smem_desc(sa + kk * 2 * kColA, kColA, 128);
-                const uint64_t db = smem_desc(sb + kk * 2 * kColB, kColB, 128);
+                // K = 16 is 32 bytes of every 128-byte row of the swizzle atoms
+                const uint64_t da = smem_desc_sw128(sa + kk * 32);
+                const uint64_t db = smem_desc_sw128(sb + kk * 32);
                 const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -187,17 +183,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(&empty[s])) : "memory");
             committed = kt + 1;
+            // refill the previous slice's stage (its MMAs were committed one slice ago)
+            // with the slice kStages after it
+            const int jn = kt - 1 + kStages;
+            if (kt >= 1 && jn < nk) {
+                const int sp = (kt - 1) % kStages;
+                if (!mbar_wait(smem_u32(&empty[sp]), (uint32_t)(((kt - 1) / kStages) & 1))) {
+                    failed = 1;
+                    break;
+                }
+                const uint32_t st = base + (uint32_t)sp * kStageBytes;
+                issue_slice(&tmA, &tmB, st, st + kABytes, smem_u32(&full[sp]), jn, m0, n0);
+                issued = jn + 1;
+            }
         }
         // the accumulator is complete once the last commit has arrived
-        if (!failed && !mbar_wait(smem_u32(&empty[(nk - 1) & 1]), (uint32_t)(((nk - 1) >> 1) & 1)))
+        if (!failed && !mbar_wait(smem_u32(&empty[(nk - 1) % kStages]),
+                                  (uint32_t)(((nk - 1) / kStages) & 1)))
             failed = 1;
         if (failed) {
             if (a.err) atomicExch(a.err, 1);
             // give copies and MMAs in flight a bounded chance to finish before the
             // shared and tensor memory they use is released
-            for (int j = consumed; j < issued; ++j) mbar_wait(smem_u32(&full[j & 1]), (uint32_t)((j >> 1) & 1));
+            for (int j = consumed; j < issued; ++j)
+                mbar_wait(smem_u32(&full[j % kStages]), (uint32_t)((j / kStages) & 1));
             if (committed > 0)
-                mbar_wait(smem_u32(&empty[(committed - 1) & 1]), (uint32_t)(((committed - 1) >> 1) & 1));
+                mbar_wait(smem_u32(&empty[(committed - 1) % kStages]),
+                          (uint32_t)(((committed - 1) / kStages) & 1));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -269,17 +281,18 @@ EncodeTiled encoder()
     return fn;
 }
 
-// 2D map of a row-major bf16 matrix [rows][K], boxes of 8 columns x box_rows rows
+// 2D map of a row-major bf16 matrix [rows][K], boxes of 64 columns (128 bytes) x
+// box_rows rows, written to shared memory with the 128-byte swizzle
 bool make_map(CUtensorMap* m, const void* ptr, int rows, int K, int box_rows)
 {
     EncodeTiled enc = encoder();
     if (!enc) return false;
     const cuuint64_t dim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     const cuuint64_t stride[1] = {(cuuint64_t)K * 2};
-    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dim, stride, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -87,7 +87,7 @@ struct SplatArgs {
 struct WarpStage {
     float4 rec[32][4];
     int id[32];
-    float key[33];            // key[32] = key of the next chunk's first entry
+    float key[33];            // entry keys x (1 - 1/4096); key[32]: the next chunk's first entry
 };
 
 __device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
@@ -249,7 +249,7 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                 const float4* r = a.rec + (size_t)id * 4;
                 const float4 n = __ldg(r + 0), vx = __ldg(r + 1), vy = __ldg(r + 2), rr = __ldg(r + 3);
                 ok = region_may_hit(n, vx, vy, rr, g, a.c);
-                ws.key[lane] = __ldg(&a.key[i]);
+                ws.key[lane] = __ldg(&a.key[i]) * kMargin;
                 if (ok) {
                     ws.id[lane] = id;
                     ws.rec[lane][0] = n; ws.rec[lane][1] = vx; ws.rec[lane][2] = vy; ws.rec[lane][3] = rr;
@@ -258,7 +258,7 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                 ws.key[lane] = INFINITY;
             }
             if (lane == 0)
-                ws.key[32] = (base + 32 < end) ? __ldg(&a.key[base + 32]) : INFINITY;
+                ws.key[32] = (base + 32 < end) ? __ldg(&a.key[base + 32]) * kMargin : INFINITY;
             unsigned m = __ballot_sync(kFull, ok);
             __syncwarp();
             while (m) {
@@ -273,7 +273,7 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                     PairEval pe;
                     const int id = ws.id[e];
                     // keys are sorted: the next entry's key bounds every later depth
-                    const float bound = ws.key[e + 1] * kMargin;
+                    const float bound = ws.key[e + 1];
                     if (eval_pair(ws.rec[e][0], ws.rec[e][1], ws.rec[e][2], ws.rec[e][3], dx, dy,
                                   a.c, pe)) {
                         const CKey key = ckey(pe.t, id);
@@ -290,7 +290,7 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                 }
             }
             // entries without a relevant successor in this chunk: bound by the next chunk
-            if (!s.done && (s.nb > 0 || s.cut != kNoKey)) flush<MODE>(s, k, a.rec, ws.key[32] * kMargin, a.M);
+            if (!s.done && (s.nb > 0 || s.cut != kNoKey)) flush<MODE>(s, k, a.rec, ws.key[32], a.M);
             __syncwarp();
         }
         // end of list: everything pending below the smallest dropped pair is final
