@@ -54,12 +54,27 @@ N_VIEWS, VIEWS_PER_STEP, N_GT, N_INIT = 64, 8, 2000, 3000
 #     + A, B updates 12 + Eq. 7-9 chain 5 + Eq. 6 chain 7 + Eq. 4 chain 8
 #     + record accumulation 16                                         = 66
 FLOP_CAND, FLOP_COMP_FWD, FLOP_COMP_BWD = 27, 12, 66
+# special-function (MUFU) operations of the same formulas: per candidate pair a
+# reciprocal for t (Eq. 4), an exponential and a reciprocal for the sigmoid (Eq. 7-8);
+# per composited pair, backward: those three again plus the reciprocal of d.n (Eq. 4)
+MUFU_CAND, MUFU_COMP_BWD = 3, 4
+MUFU_PER_SM_CLK = 16           # special-function results per SM per clock
 SM_COUNT, FP32_LANES = 152, 128
 # kernels of one step: schedule advance 1 (graphs); project 1; bin: record counts 1, scans
 # (record and tile scans in one launch when both fit one CTA, 49,152 elements; beyond, the
 # record scan takes three launches plus the chunk table 1 and the tile scan six), scatter 1,
 # sorts 2; fused splat 1 + chain 1 (split: fwd 1, loss 1, bwd 1 + chain 1); Adam 2
 ONE_CTA_SCAN = 48 * 1024
+
+
+def measured_peaks() -> dict:
+    """The copy bandwidth and GEMM rates measured on this machine's GPUs (MEASURED_PEAKS.json
+    at the repository root), or {} if the file is absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def scan_launches(n: int, twice: bool = False) -> int:
@@ -401,6 +416,19 @@ def run_ours(args, rank, world, local_rank):
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_clock,
                 "per_launch": {"candidate_pairs": cand // K, "composited_pairs": comp // K,
                                "tested_pairs": tested // K, "ms": round(dom_ms, 4)}}
+    # the other two roofs of this kernel: special functions and DRAM
+    mufu = (cand * MUFU_CAND + (comp * MUFU_COMP_BWD if dom != "splat_fwd" else 0)) / K
+    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * sm_clock * 1e6 / 1e12
+    roofline["other_roofs"] = {
+        "mufu": {"achieved": round(mufu / (dom_ms / 1e3) / 1e12, 4), "peak": round(mufu_peak, 3),
+                 "unit": "Tops/s", "frac": round(mufu / (dom_ms / 1e3) / 1e12 / mufu_peak, 4),
+                 "peak_basis": "152 SMs x 16 per clock x %.0f MHz" % sm_clock}}
+    peaks = measured_peaks()
+    if traffic and peaks.get("hbm_gbs"):
+        gbs = traffic / (dom_ms / 1e3) / 1e9
+        roofline["other_roofs"]["hbm"] = {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                          "frac": round(gbs / peaks["hbm_gbs"], 4),
+                                          "peak_basis": "measured copy bandwidth (ncu DRAM bytes of the launch)"}
 
     cfg = workload_config(args, world)
     cfg["tile"] = "%dx%d" % tile
