@@ -94,7 +94,7 @@ def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:
 # DRAM bytes (read + write) per launch of the fused splat kernel from the ncu
 # capture summarised in profiles/k_splat_fused_room640_8x8.md; reported only while
 # the kernel source is the one it was taken on.
-TRAFFIC = {"splat_fused": 51166976, "src_sha": "cb3f1bc62a83339a"}
+TRAFFIC = {"splat_fused": 51150080, "src_sha": "b83a89d27baf42fd"}
 
 
 def src_hash() -> str:

@@ -385,11 +385,20 @@ ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v
    A, B: device bf16, row-major with K contiguous, 16-byte aligned; K must be a
    multiple of 64 (zero-pad).  C32: device fp32 [M, ldc] or NULL; C16: device
    bf16 [M, ldc] or NULL (at least one); with accumulate, C32 += result.
-   bias: device fp32 [N] or NULL.  d_err: device int set to 1 if a bounded wait
-   for the tensor cores timed out (the tile is then not written). */
+   bias: device fp32 [N] or NULL.  d_err: device status word (or NULL) into which
+   (1 << PS_ERR_TIMEOUT) is OR-ed if a bounded wait for the copies or the tensor
+   cores timed out (the tile is then not written; the copies and MMAs in flight
+   get a bounded wait and the tensor memory is freed, so the context stays usable). */
 ps_status ps_gemm_bf16(const void* A, const void* B, const float* bias, float* C32, void* C16,
                        int M, int N, int K, int ldc, int relu, int accumulate, int* d_err,
                        ps_stream stream);
+
+/* Exercises the time-out path of the bounded device-side waits: one thread
+   waits on an mbarrier that nothing arrives on (the wait routine of
+   ps_gemm_bf16) for `polls` polls (1 .. 2^24), gives up and ORs
+   (1 << PS_ERR_TIMEOUT) into *d_status (device).  Nothing else is issued, so the
+   context stays usable.  For tests of the failure path; no fault is involved. */
+ps_status ps_wait_selftest(int* d_status, long long polls, ps_stream stream);
 
 /* ---- Seed-proposal network (not part of the paper: a learned initialiser of
    the planes of Sec. 3.1).  Four 3x3 stride-2 convolutions (64 channels, ReLU),

@@ -26,7 +26,7 @@ PS_MAX_M = 64
 EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin_tiles",
            "ps_fwd_workspace_bytes", "ps_splat_fwd", "ps_splat_ids", "ps_loss", "ps_bwd_workspace_bytes", "ps_splat_bwd",
            "ps_splat_fused", "ps_adam_step",
-           "ps_count_pairs", "ps_step_advance", "ps_adam_step_state", "ps_gemm_bf16",
+           "ps_count_pairs", "ps_step_advance", "ps_adam_step_state", "ps_gemm_bf16", "ps_wait_selftest",
            "ps_seed_im2col", "ps_seed_col2im", "ps_seed_relu_bwd", "ps_seed_transpose",
            "ps_seed_colsum", "ps_seed_pool", "ps_seed_pool_bwd", "ps_seed_loss", "ps_cast_bf16",
            "ps_radii_grad_accum", "ps_split_planes", "ps_merge_planes", "ps_status_string",
@@ -107,6 +107,7 @@ def load():
             "ps_count_pairs": ([P, P, P, P, P, P, LL, P, P], I),
             "ps_step_advance": ([P, P, I, P, P], I),
             "ps_gemm_bf16": ([P, P, P, P, P, I, I, I, I, I, I, P, P], I),
+            "ps_wait_selftest": ([P, LL, P], I),
             "ps_seed_im2col": ([P, I, I, I, I, I, P, P], I),
             "ps_seed_col2im": ([P, I, I, I, I, I, P, P], I),
             "ps_seed_relu_bwd": ([P, P, LL, F, P, P, P], I),
@@ -352,6 +353,12 @@ def ps_merge_planes(params, n_planes, scene_center, max_angle_deg, max_offset, g
     _check(load().ps_merge_planes(_ptr(params), int(n_planes), c, float(max_angle_deg),
                                   float(max_offset), _ptr(group_of), _ptr(rep_of_group),
                                   _ptr(d_groups), _stream(stream)), "ps_merge_planes")
+
+
+def ps_wait_selftest(status, polls: int, stream=None):
+    """One bounded device wait that runs out (nothing arrives): ORs
+    1 << PS_ERR_TIMEOUT into the status word (device int32)."""
+    _check(load().ps_wait_selftest(_ptr(status), int(polls), _stream(stream)), "ps_wait_selftest")
 
 
 def ps_gemm_bf16(A, B, bias, C32, C16, relu=False, accumulate=False, err=None, stream=None):

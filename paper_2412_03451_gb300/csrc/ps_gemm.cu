@@ -69,9 +69,9 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long polls = kWaitPolls)
 {
-    for (long long i = 0; i < kWaitPolls; ++i) {
+    for (long long i = 0; i < polls; ++i) {
         uint32_t done = 0;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -92,7 +92,7 @@ struct GemmArgs {
     int M, N, K, ldc;
     int relu;
     int accumulate;           // C32 += result
-    int* err;                 // error flag (device), set on a wait time-out
+    int* err;                 // status word (device): 1 << PS_ERR_TIMEOUT on a wait time-out
 };
 
 // k-slice j of A and B into the stage at sa / sb: one box each (x = j * 64 elements,
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                                   (uint32_t)(((nk - 1) / kStages) & 1)))
             failed = 1;
         if (failed) {
-            if (a.err) atomicExch(a.err, 1);
+            if (a.err) atomicOr(a.err, 1 << PS_ERR_TIMEOUT);
             // give copies and MMAs in flight a bounded chance to finish before the
             // shared and tensor memory they use is released
             for (int j = consumed; j < issued; ++j)
@@ -261,6 +261,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      :: "r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// The time-out path of mbar_wait on a barrier that nothing arrives on: one
+// thread initialises an mbarrier expecting one arrival, waits `polls` polls for
+// its first phase, gives up and reports PS_ERR_TIMEOUT; nothing else was issued,
+// so nothing is left in flight.
+__global__ void k_wait_selftest(int* status, long long polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(b, 0u, polls)) atomicOr(status, 1 << PS_ERR_TIMEOUT);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(b) : "memory");
 }
 
 typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -322,6 +337,14 @@ extern "C" ps_status ps_gemm_bf16(const void* A, const void* B, const float* bia
     }
     dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
     k_gemm_tc<<<grid, kThreads, dyn, reinterpret_cast<cudaStream_t>(stream)>>>(tmA, tmB, a);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
+
+extern "C" ps_status ps_wait_selftest(int* d_status, long long polls, ps_stream stream)
+{
+    if (!d_status || polls < 1 || polls > (1LL << 24)) return PS_ERR_ARG;
+    k_wait_selftest<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(d_status, polls);
     PS_LAUNCH_CHECK();
     return PS_OK;
 }

@@ -134,6 +134,15 @@ def test_plane_set_operations_reject_bad_arguments(lib):
     assert lib.ps_radii_grad_accum(None, None, 1.0, 4, None, None) == B.PS_ERR_ARG
 
 
+def test_wait_selftest_rejects_bad_arguments(lib):
+    # a status word is required and the poll count is bounded (1 .. 2^24): nothing is launched
+    from paper_2412_03451_gb300 import binding as B
+    d = ctypes.c_void_p(256)
+    assert lib.ps_wait_selftest(None, 1000, None) == B.PS_ERR_ARG
+    assert lib.ps_wait_selftest(d, 0, None) == B.PS_ERR_ARG
+    assert lib.ps_wait_selftest(d, (1 << 24) + 1, None) == B.PS_ERR_ARG
+
+
 def test_gaussian_flag_checks(lib):
     from paper_2412_03451_gb300 import binding as B
     views, frame = B.ps_plan_views([96], [128], [0], [0, 4], np.eye(3, 4, dtype=np.float32)[None],
