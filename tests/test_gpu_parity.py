@@ -317,17 +317,18 @@ def big_case():
     return room, cams, D, N, init
 
 
-def test_paper_scale_forward_sampled_rows(big_case):
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_paper_scale_forward_sampled_rows(big_case, tile):
     room, cams, D, N, init = big_case
     lam = 20.0 / np.e
-    g = gpu_run(init, cams, lam)
+    g = gpu_run(init, cams, lam, tile=tile)
     rows = (200, 203)
     o = oracle_render(init, cams, lam, rows=rows)
     c = compare_maps(g, o, rows=rows)
-    report("fwd_big", **c)
+    report("fwd_big", tile=tile, **c)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
     # bit-exact bins at full size
-    rect, key32, ptr, ent, ekey = oracle_bins(init, cams, g["delta"], (16, 16))
+    rect, key32, ptr, ent, ekey = oracle_bins(init, cams, g["delta"], tile)
     assert np.array_equal(g["rect"], rect)
     assert np.array_equal(g["tile_ptr"], ptr) and np.array_equal(g["tile_ent"], ent)
     assert np.array_equal(g["tile_key"].view(np.uint32), ekey.view(np.uint32))
@@ -355,6 +356,23 @@ def test_paper_scale_backward_sampled_rows(big_case):
 
 # ---------------------------------------------------------------------------
 # Fused forward + loss + backward.
+
+def test_paper_scale_fused_equals_separate_kernels(big_case):
+    # the benchmark's launch configuration (fused kernel, 8x8 tiles) at full size against
+    # the separate kernels, which the sampled-row tests above tie to the oracle
+    from gpu_cases import gpu_fused_vs_split
+    room, cams, D, N, init = big_case
+    sp, fu, status = gpu_fused_vs_split(init, cams, 20.0 / np.e, D, N, tile=(8, 8))
+    assert status == 0
+    assert np.array_equal(sp["depth"], fu["depth"]) and np.array_equal(sp["normal"], fu["normal"])
+    assert np.array_equal(sp["dLdD"], fu["dLdD"]) and np.array_equal(sp["dLdN"], fu["dLdN"])
+    assert np.allclose(sp["sums"], fu["sums"], rtol=1e-6)
+    K = init.K
+    for a, b in ((0, 3 * K), (3 * K, 7 * K), (7 * K, 11 * K)):
+        gs, gf = sp["grad"][a:b], fu["grad"][a:b]
+        assert np.linalg.norm(gs - gf) <= 1e-5 * np.linalg.norm(gs) + 1e-6
+    report("fused_vs_split_big", views=int(cams.V), planes=int(K))
+
 
 @pytest.mark.parametrize("lam,tile", [(20.0 / np.e, (16, 16)), (20.0, (8, 8)), (300.0, (32, 8))])
 def test_fused_equals_separate_kernels(lam, tile):
