@@ -77,7 +77,7 @@ def _load():
             lib.or_bin_records.argtypes = [I, I, P, P, P, P, P, I, I, I, I, D, D, D, I, P, P, P]
             lib.or_records_ns.argtypes = [I, I, P, P, P, P, P]
             lib.or_render.argtypes = [I, I, P, P, P, P, P, I, I, D, D, D, D, I, I, D, D, D, D,
-                                      I, I, P, P, P, P, P, P]
+                                      I, I, P, P, P, P, P, P, P]
             lib.or_loss.argtypes = [I, I, I, P, P, P, P, D, D, D, P, P, P]
             lib.or_loss.restype = D
             lib.or_backward.argtypes = [I, I, P, P, P, P, P, I, I, D, D, D, D, I, I, P, P, P, P, P]
@@ -251,7 +251,8 @@ def render(center, quat, radii, w2c, intr, H, W, lam, M=M_DEFAULT, w_min=W_MIN,
            z_near=Z_NEAR, z_far=Z_FAR, single_radii=False, eta=1e-6, tol_d=1e-4,
            tol_n=1e-5, rows=None, gaussian=False):
     """Brute-force forward of Eq. 11-13.  Returns a dict of per-pixel arrays:
-    depth [V,H,W], normal [V,H,W,3], alpha, n_sel, n_cand, ill (see ps_oracle.c)."""
+    depth [V,H,W], normal [V,H,W,3], alpha, n_sel, n_cand, ill, and sens_d, sens_n
+    (the first-order FP32 rounding sensitivity of D and N; see ps_oracle.c)."""
     c, q, r = _f64(center), _f64(quat), _f64(radii)
     Rt, K_ = _f64(w2c).reshape(-1, 12), _f64(intr).reshape(-1, 4)
     K, V = c.shape[0], Rt.shape[0]
@@ -259,13 +260,15 @@ def render(center, quat, radii, w2c, intr, H, W, lam, M=M_DEFAULT, w_min=W_MIN,
     out = dict(depth=np.zeros((V, H, W)), normal=np.zeros((V, H, W, 3)),
                alpha=np.zeros((V, H, W)), n_sel=np.zeros((V, H, W), np.int32),
                n_cand=np.zeros((V, H, W), np.int32), ill=np.zeros((V, H, W), np.int32))
+    sens = np.zeros((V, H, W, 2))
     delta = filter_margin(lam, w_min)
     _load().or_render(K, V, _ptr(c), _ptr(q), _ptr(r), _ptr(Rt), _ptr(K_), H, W,
                       float(lam), float(w_min), float(z_near), float(z_far), int(M),
                       _flags(single_radii, gaussian), float(delta), float(eta), float(tol_d),
                       float(tol_n), int(row0), int(row1),
                       _ptr(out["depth"]), _ptr(out["normal"]), _ptr(out["alpha"]),
-                      _ptr(out["n_sel"]), _ptr(out["n_cand"]), _ptr(out["ill"]))
+                      _ptr(out["n_sel"]), _ptr(out["n_cand"]), _ptr(out["ill"]), _ptr(sens))
+    out["sens_d"], out["sens_n"] = sens[..., 0], sens[..., 1]
     return out
 
 

@@ -389,13 +389,19 @@ static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], cons
 /*          move D or N by more than tol_d/2 or tol_n/2, or flip the filter, */
 /*          the depth order or the z range;                                  */
 /*   bit 1: bit 0, or the min / sign branch of a weighted, partly            */
-/*          transparent entry is within eta of flipping (gradients only).    */
+/*          transparent entry is within eta of flipping (gradients only);    */
+/*   bit 2: of bit 0, the discontinuous part: the filter, the depth order or */
+/*          the z range could flip.                                          */
+/* sens (optional) [pixel][2]: the first-order size of those rounding        */
+/* effects on D and on the largest component of N, sum over the composited  */
+/* pairs of |dD/dm_j| eta_j (likewise N), from the adjoint of Eq. 11-13.     */
 /* Rows [row0, row1) of every view are rendered; others are left untouched.  */
 void or_render(int K, int V, const double* center, const double* quat, const double* radii,
                const double* w2c, const double* intr, int H, int W,
                double lambda, double w_min, double z_near, double z_far, int M, int flags,
                double delta, double eta, double tol_d, double tol_n, int row0, int row1,
-               double* depth, double* normal, double* alpha, int* n_sel, int* n_cand, int* ill)
+               double* depth, double* normal, double* alpha, int* n_sel, int* n_cand, int* ill,
+               double* sens)
 {
     or_set S = {lambda, w_min, z_near, z_far, M, flags};
     const int gauss = flags & OR_GAUSS;
@@ -429,11 +435,12 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
                         T = T * (1.0 - cs[s].w);
                     }
                     /* conditioning */
-                    int bad_val = near_filter, bad_grad = 0;
+                    int flip = near_filter, bad_grad = 0;
                     for (int s = 0; s + 1 < nc && s < M; ++s) {
                         double e = eta * (1.0 + fabs(cs[s + 1].t));
-                        if (cs[s + 1].t - cs[s].t < e) bad_val = 1;
+                        if (cs[s + 1].t - cs[s].t < e) flip = 1;
                     }
+                    int bad_val = flip;
                     /* sensitivity of D, N to the margins: back-to-front sums */
                     double Ab = 0.0, Bb[3] = {0, 0, 0};
                     double sD = 0.0, sN[3] = {0, 0, 0};
@@ -471,7 +478,11 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
                     if (alpha) alpha[pix] = A;
                     if (n_sel) n_sel[pix] = ns;
                     if (n_cand) n_cand[pix] = nc;
-                    if (ill) ill[pix] = (bad_val ? 3 : 0) | (bad_grad ? 2 : 0);
+                    if (ill) ill[pix] = (bad_val ? 3 : 0) | (bad_grad ? 2 : 0) | (flip ? 4 : 0);
+                    if (sens) {
+                        sens[2 * pix] = sD;
+                        sens[2 * pix + 1] = fmax(sN[0], fmax(sN[1], sN[2]));
+                    }
                 }
             }
             free(cs);

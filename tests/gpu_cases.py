@@ -2,6 +2,9 @@
 the same seeded inputs and collect comparable numpy arrays."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 from oracle import oracle as O
@@ -13,6 +16,20 @@ Z_FAR32 = 100.0
 
 def f32(x: float) -> float:
     return float(np.float32(x))
+
+
+REPORT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out",
+                      "parity_report.jsonl")
+
+
+def record(name, **kw):
+    """Appends one line of measured parity figures to the run's report (best effort)."""
+    try:
+        os.makedirs(os.path.dirname(REPORT), exist_ok=True)
+        with open(REPORT, "a") as f:
+            f.write(json.dumps(dict(test=name, **kw)) + "\n")
+    except OSError:
+        pass
 
 
 def gpu_run(planes: S.Planes, cams: S.Cameras, lam: float, tile=(16, 16), M=30, flags=0,
@@ -72,17 +89,28 @@ def oracle_render(planes, cams, lam, M=30, rows=None, gaussian=False):
 
 def compare_maps(g, o, rows=None, tol_d=1e-4, tol_n=1e-5):
     """Max depth / normal error over well-conditioned pixels (oracle ill bit 0
-    clear) and the count of ill-conditioned pixels."""
+    clear) and the count of ill-conditioned pixels.  Of those, the pixels where
+    only the size of the rounding effect is the issue (bit 2 clear: no filter,
+    order or range flip) are checked against the oracle's own first-order
+    estimate of it: |D - D*| <= max(tol_d, 2 sens_d), likewise N."""
     sl = slice(None) if rows is None else slice(rows[0], rows[1])
-    well = (o["ill"][:, sl] & 1) == 0
+    ill = o["ill"][:, sl]
+    well = (ill & 1) == 0
+    sens = ((ill & 1) != 0) & ((ill & 4) == 0)
     dd = np.abs(g["depth"][:, sl].astype(np.float64) - o["depth"][:, sl])
     dn = np.abs(g["normal"][:, sl].astype(np.float64) - o["normal"][:, sl]).max(axis=-1)
+    bd = np.maximum(tol_d, 2.0 * o["sens_d"][:, sl])
+    bn = np.maximum(tol_n, 2.0 * o["sens_n"][:, sl])
     return dict(
-        n_pix=int(well.size), n_ill=int((~well).sum()),
+        n_pix=int(well.size), n_ill=int((~well).sum()), n_sens=int(sens.sum()),
+        n_flip=int(((ill & 4) != 0).sum()),
         max_dd_well=float(dd[well].max()) if well.any() else 0.0,
         max_dn_well=float(dn[well].max()) if well.any() else 0.0,
         max_dd_ill=float(dd[~well].max()) if (~well).any() else 0.0,
         n_bad_d=int((dd[well] > tol_d).sum()), n_bad_n=int((dn[well] > tol_n).sum()),
+        n_bad_sens_d=int((dd[sens] > bd[sens]).sum()), n_bad_sens_n=int((dn[sens] > bn[sens]).sum()),
+        worst_sens_ratio_d=float((dd[sens] / bd[sens]).max()) if sens.any() else 0.0,
+        worst_sens_ratio_n=float((dn[sens] / bn[sens]).max()) if sens.any() else 0.0,
     )
 
 

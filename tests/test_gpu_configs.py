@@ -20,7 +20,7 @@ import pytest
 from oracle import oracle as O
 from paper_2412_03451_gb300 import scenes as S
 
-from gpu_cases import Z_NEAR32, compare_maps, f32, grad_errors
+from gpu_cases import Z_NEAR32, compare_maps, f32, grad_errors, record
 
 pytestmark = pytest.mark.gpu
 
@@ -135,7 +135,9 @@ def test_stress_forward_sampled_rows(torch, stress):
     g = {"depth": depth[views].cpu().numpy(),
          "normal": r.normal.view(cams.V, H, W, 3)[views].cpu().numpy()}
     c = compare_maps(g, o, rows=rows)
+    record("stress_fwd", **c)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
     # 10,000 planes seeded on 2,000 surfaces overlap at equal depths, so the oracle marks many
     # pixels whose depth order FP32 rounding may decide; the bars hold on the rest (>= 1,000)
     assert c["n_pix"] - c["n_ill"] >= 1000, c

@@ -8,7 +8,7 @@ import pytest
 from oracle import oracle as O
 from paper_2412_03451_gb300 import scenes as S
 
-from gpu_cases import compare_maps, f32, gpu_run, grad_errors, oracle_bins, oracle_render
+from gpu_cases import compare_maps, f32, gpu_run, grad_errors, oracle_bins, oracle_render, record
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,9 @@ def test_gauss_forward_tiny_room(lam):
     g = gpu_run(init, room.cams, lam, flags=_flags())
     o = oracle_render(init, room.cams, lam, gaussian=True)
     c = compare_maps(g, o)
+    record("gauss_fwd", lam=lam, **c)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
     # Eq. 5 has no flat interior: at every covered pixel dw/dP != 0, so the oracle's
     # FP32 noise model (position error 1e-6 (1 + t + |p_c|)) marks many pixels; the
     # bars hold on the rest, and a 10x looser bar on all pixels
@@ -68,7 +70,9 @@ def test_gauss_forward_dense_overlaps():
     g = gpu_run(p, cams, 20.0, flags=_flags(), tile=(8, 8))
     o = oracle_render(p, cams, 20.0, gaussian=True)
     c = compare_maps(g, o)
+    record("gauss_fwd_dense", **c)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
     assert c["max_dd_ill"] < 1e-3, c
     assert (o["n_sel"] >= 5).mean() > 0.05
 

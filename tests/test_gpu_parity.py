@@ -128,6 +128,7 @@ def test_forward_tiny_room(lam):
     c = compare_maps(g, o)
     report("fwd_tiny", lam=lam, **c)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
     assert c["n_ill"] < 0.5 * c["n_pix"]
     well = (o["ill"] & 1) == 0
     assert np.abs(g["alpha"][well] - o["alpha"][well]).max() < 1e-5
@@ -141,6 +142,7 @@ def test_forward_other_tiles(tile):
     c = compare_maps(g, o)
     report("fwd_tiles", tile=tile, **c)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
 
 
 def test_forward_dense_overlaps_top_m_and_restarts():
@@ -155,6 +157,7 @@ def test_forward_dense_overlaps_top_m_and_restarts():
         report("fwd_dense", M=M, max_cand=int(o["n_cand"].max()), **c)
         assert o["n_cand"].max() > 30
         assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+        assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
 
 
 def test_forward_stack_of_40_equal_weights():
@@ -327,6 +330,7 @@ def test_paper_scale_forward_sampled_rows(big_case, tile):
     c = compare_maps(g, o, rows=rows)
     report("fwd_big", tile=tile, **c)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
     # bit-exact bins at full size
     rect, key32, ptr, ent, ekey = oracle_bins(init, cams, g["delta"], tile)
     assert np.array_equal(g["rect"], rect)
@@ -543,6 +547,7 @@ def test_m_extremes_forward_backward(M):
     g = gpu_run(p, cams, lam, M=M, dLdD=dD, dLdN=dN, backward=True)
     c = compare_maps(g, o)
     assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
     gc, gq, gr = O.backward(p.center, p.quat, p.radii, cams.w2c, cams.intr, cams.H, cams.W,
                             f32(lam), dD, dN, M=M, z_near=f32(0.01))
     for k, ref in (("g_center", gc), ("g_quat", gq), ("g_radii", gr)):

@@ -381,6 +381,32 @@ def test_backward_single_radii_and_small_m():
     _fd_check(p, cams, 20.0, seed=6, M=2)
 
 
+def test_rounding_sensitivity_matches_finite_differences():
+    # sens_d is sum_j |dD/dm_j| eta (1 + t + |p_c|): for one fronto-parallel plane whose
+    # right edge band crosses the centre row, dD/dm = dD/dr^x+ (m = r^x+ - P_X there);
+    # central differences of the render in r^x+ must give the same slope
+    w2c, intr = ident_cams()
+    Z, lam, eta = 2.0, 20.0, 1e-6
+    c, q, r = plane([0.0, 0.0, Z], [1, 0, 0, 0], [0.3, 0.6, 0.6, 0.6])
+    o = O.render(c, q, r, w2c, intr, 96, 128, lam, eta=eta)
+    h = 1e-5
+    rp, rm = r.copy(), r.copy()
+    rp[0, 0] += h
+    rm[0, 0] -= h
+    fd = (O.render(c, q, rp, w2c, intr, 96, 128, lam)["depth"] -
+          O.render(c, q, rm, w2c, intr, 96, 128, lam)["depth"]) / (2 * h)
+    j = 48
+    band = [i for i in range(64, 128) if 1e-3 < o["alpha"][0, j, i] < 0.999]
+    assert len(band) >= 3
+    pc = np.array([0.0, 0.0, Z])
+    for i in band:
+        e = eta * (1.0 + o["depth"][0, j, i] / o["alpha"][0, j, i] + np.linalg.norm(pc))
+        assert o["sens_d"][0, j, i] == pytest.approx(abs(fd[0, j, i]) * e, rel=1e-4)
+        assert o["ill"][0, j, i] & 4 == 0
+    # interior pixels (w = 1) have no first-order sensitivity
+    assert o["sens_d"][0, j, 64] == 0.0
+
+
 # ---------------------------------------------------------------------------
 # Binning: conservativeness against single-plane brute force, list contents.
 
