@@ -391,7 +391,8 @@ static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], cons
 /*   bit 1: bit 0, or the min / sign branch of a weighted, partly            */
 /*          transparent entry is within eta of flipping (gradients only);    */
 /*   bit 2: of bit 0, the discontinuous part: the filter, the depth order or */
-/*          the z range could flip.                                          */
+/*          the z range could flip;                                          */
+/*   bit 3: of bit 1, the branch part (a min / sign branch could flip).      */
 /* sens (optional) [pixel][2]: the first-order size of those rounding        */
 /* effects on D and on the largest component of N, sum over the composited  */
 /* pairs of |dD/dm_j| eta_j (likewise N), from the adjoint of Eq. 11-13.     */
@@ -478,7 +479,7 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
                     if (alpha) alpha[pix] = A;
                     if (n_sel) n_sel[pix] = ns;
                     if (n_cand) n_cand[pix] = nc;
-                    if (ill) ill[pix] = (bad_val ? 3 : 0) | (bad_grad ? 2 : 0) | (flip ? 4 : 0);
+                    if (ill) ill[pix] = (bad_val ? 3 : 0) | (bad_grad ? 10 : 0) | (flip ? 4 : 0);
                     if (sens) {
                         sens[2 * pix] = sD;
                         sens[2 * pix + 1] = fmax(sN[0], fmax(sN[1], sN[2]));

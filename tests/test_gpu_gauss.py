@@ -84,7 +84,7 @@ def test_gauss_backward():
     rng = np.random.default_rng(3)
     dD = rng.normal(size=o["depth"].shape)
     dN = rng.normal(size=o["normal"].shape)
-    ill = (o["ill"] & 2) != 0
+    ill = (o["ill"] & 12) != 0
     dD[ill] = 0
     dN[ill] = 0
     dD, dN = dD.astype(np.float32), dN.astype(np.float32)

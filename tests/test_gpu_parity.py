@@ -257,7 +257,9 @@ def test_adam_parity():
 # ---------------------------------------------------------------------------
 # Backward.
 
-def _upstream(o, gt_D, gt_N, mask_bits=2):
+def _upstream(o, gt_D, gt_N, mask_bits=12):
+    # masked (same input on both sides): pixels where FP32 rounding could flip a min / sign
+    # branch, the filter, the depth order or the z range (oracle flag bits 3 and 2)
     _, dD, dN, _ = O.loss(o["depth"], o["normal"], gt_D, gt_N)
     ill = (o["ill"] & mask_bits) != 0
     dD[ill] = 0.0
@@ -277,7 +279,8 @@ def test_backward_tiny_room(lam):
                             room.cams.H, room.cams.W, f32(lam), dD, dN, z_near=f32(0.01))
     res = {k: grad_errors(g[k], ref) for k, ref in
            (("g_center", gc), ("g_quat", gq), ("g_radii", gr))}
-    report("bwd_tiny", lam=lam, ill_frac=ill, **{k: v for k, v in res.items()})
+    report("bwd_tiny", lam=lam, masked_frac=ill, **{k: v for k, v in res.items()})
+    assert ill < 1e-3
     for k, (nbad, worst) in res.items():
         assert nbad == 0, (k, nbad, worst)
 
@@ -290,7 +293,7 @@ def test_backward_dense_overlaps():
     rng = np.random.default_rng(3)
     dD = rng.normal(size=o["depth"].shape)
     dN = rng.normal(size=o["normal"].shape)
-    ill = (o["ill"] & 2) != 0
+    ill = (o["ill"] & 12) != 0
     dD[ill] = 0
     dN[ill] = 0
     dD, dN = dD.astype(np.float32), dN.astype(np.float32)
@@ -540,7 +543,7 @@ def test_m_extremes_forward_backward(M):
     rng = np.random.default_rng(8)
     dD = rng.normal(size=o["depth"].shape)
     dN = rng.normal(size=o["normal"].shape)
-    ill = (o["ill"] & 2) != 0
+    ill = (o["ill"] & 12) != 0
     dD[ill] = 0
     dN[ill] = 0
     dD, dN = dD.astype(np.float32), dN.astype(np.float32)
