@@ -355,6 +355,11 @@ def evaluate(net, n_rooms=8, seed0=9000, planes=3000, iters=5000, device="cuda",
            "reached_plain": sum(p["done_at"][0] is not None for p in pl),
            "iterations_plain": [p["done_at"][0][0] if p["done_at"][0] else None for p in pl],
            "variants": []}
+    # warm the network's kernels once (first-call set-up is not inference)
+    c0 = rooms[0].cams
+    propose_planes(net, rooms[0], ss_p.gt_depth[:c0.H * c0.W].view(1, c0.H, c0.W),
+                   ss_p.gt_normal[:c0.H * c0.W].view(1, c0.H, c0.W, 3), [0], seed=seed0, max_planes=100)
+    torch.cuda.synchronize()
     for var in variants:
         opts = {k: v for k, v in var.items() if k not in ("name", "lam_offset")}
         learned, infer_ms, n_l, n_f = [], 0.0, 0, 0
