@@ -68,7 +68,7 @@ ONE_CTA_SCAN = 48 * 1024
 
 
 def measured_peaks() -> dict:
-    """The copy bandwidth and GEMM rates measured on this machine's GPUs (MEASURED_PEAKS.json
+    """The copy bandwidth and GEMM rates measured on the GPUs this runs on (MEASURED_PEAKS.json
     at the repository root), or {} if the file is absent."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -351,8 +351,10 @@ def run_ours(args, rank, world, local_rank):
     wl.r.status.zero_()
     saved = (wl.flat.clone(), wl.fit.m.clone(), wl.fit.v.clone(), wl.fit.ite)
     # clocks are sampled from here to the end of the timed pass (both passes keep the GPU busy)
-    clk = ClockSampler(local_rank, os.path.join(ROOT, "gpurun_out", "clocks_r%d.csv" % rank)
-                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    # the raw samples are also written out when PS_CLOCKS_DIR names a directory
+    cdir = os.environ.get("PS_CLOCKS_DIR")
+    clk = ClockSampler(local_rank, os.path.join(cdir, "clocks_r%d.csv" % rank)
+                       if cdir and os.path.isdir(cdir) else None)
     clk.start()
 
     # pass 1 (eager launches): per-stage CUDA events and exact work counts

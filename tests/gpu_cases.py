@@ -18,12 +18,15 @@ def f32(x: float) -> float:
     return float(np.float32(x))
 
 
-REPORT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out",
-                      "parity_report.jsonl")
+# measured parity figures are appended to $PS_REPORT_DIR/parity_report.jsonl when it is set
+REPORT = (os.path.join(os.environ["PS_REPORT_DIR"], "parity_report.jsonl")
+          if os.environ.get("PS_REPORT_DIR") else None)
 
 
 def record(name, **kw):
     """Appends one line of measured parity figures to the run's report (best effort)."""
+    if REPORT is None:
+        return
     try:
         os.makedirs(os.path.dirname(REPORT), exist_ok=True)
         with open(REPORT, "a") as f:

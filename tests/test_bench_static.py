@@ -1,5 +1,5 @@
 """bench.py calls only functions it defines, imports or gets from builtins, and
-its argument parser accepts the driver's flags (CPU only, nothing is run)."""
+its argument parser accepts the flags of the benchmark contract (CPU only, nothing is run)."""
 import ast
 import builtins
 import os
