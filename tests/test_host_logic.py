@@ -1,0 +1,42 @@
+"""Host-side logic that needs no GPU: the autotuner's cache keys and file cache,
+and the seeded scene generators' determinism (every input is seeded)."""
+import json
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2412_03451_gb300 import autotune as AT
+from paper_2412_03451_gb300 import scenes as S
+
+
+def test_autotune_key_buckets_planes_and_sorts_sizes():
+    k = AT._key([(480, 640), (240, 320), (480, 640)], 8, 3000)
+    assert k == "240x320,480x640|v8|k11"
+    assert AT._key([(480, 640)], 8, 2048) == AT._key([(480, 640)], 8, 4095)
+    assert AT._key([(480, 640)], 8, 2047) != AT._key([(480, 640)], 8, 2048)
+
+
+def test_autotune_answers_from_the_file_cache_without_timing(tmp_path, monkeypatch):
+    key = AT._key([(480, 640)], 8, 3000)
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({key: {"tile": [32, 8], "ms": {"32x8": 1.0}}}))
+    monkeypatch.setenv("PS_AUTOTUNE_CACHE", str(path))
+    monkeypatch.setattr(AT, "_cache", {})
+
+    def no_renderer(tile):
+        raise AssertionError("a cached key must not be timed")
+
+    tile, ms = AT.pick_tile(no_renderer, None, None, None, 20.0, key)
+    assert tile == (32, 8) and ms == {"32x8": 1.0}
+
+
+def test_scene_generators_are_seeded():
+    a, b = S.large_room(1003, n_rect=300, n_views=4), S.large_room(1003, n_rect=300, n_views=4)
+    assert np.array_equal(a.gt.center, b.gt.center) and np.array_equal(a.gt.quat, b.gt.quat)
+    assert np.array_equal(a.cams.w2c, b.cams.w2c)
+    c = S.large_room(1004, n_rect=300, n_views=4)
+    assert not np.array_equal(a.gt.center, c.gt.center)
+    p, q = S.surface_init(a, 200, 5), S.surface_init(a, 200, 5)
+    assert np.array_equal(p.center, q.center) and np.array_equal(p.radii, q.radii)
