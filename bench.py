@@ -95,6 +95,10 @@ def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:
 # capture summarised in profiles/k_splat_fused_room640_8x8.md; reported only while
 # the kernel source is the one it was taken on.
 TRAFFIC = {"splat_fused": 51150080, "src_sha": "b83a89d27baf42fd"}
+# warp instructions of the same captured launch (smsp__inst_executed.sum), for the
+# issue roof: 152 SMs x 4 schedulers x one warp instruction per clock
+INSTR = {"splat_fused": 413433394, "src_sha": "b83a89d27baf42fd"}
+SCHEDULERS_PER_SM = 4
 
 
 def src_hash() -> str:
@@ -425,6 +429,15 @@ def run_ours(args, rank, world, local_rank):
         "mufu": {"achieved": round(mufu / (dom_ms / 1e3) / 1e12, 4), "peak": round(mufu_peak, 3),
                  "unit": "Tops/s", "frac": round(mufu / (dom_ms / 1e3) / 1e12 / mufu_peak, 4),
                  "peak_basis": "152 SMs x 16 per clock x %.0f MHz" % sm_clock}}
+    instr = INSTR.get(dom) if INSTR.get("src_sha") == src_hash() else None
+    if instr:
+        ips = instr / (dom_ms / 1e3) / 1e9
+        ipeak = SM_COUNT * SCHEDULERS_PER_SM * sm_clock * 1e6 / 1e9
+        roofline["other_roofs"]["issue"] = {
+            "achieved": round(ips, 1), "peak": round(ipeak, 1), "unit": "G warp instructions/s",
+            "frac": round(ips / ipeak, 4),
+            "peak_basis": "152 SMs x 4 schedulers x %.0f MHz; instructions from the ncu capture of one "
+                          "launch of the same kernel source" % sm_clock}
     peaks = measured_peaks()
     if traffic and peaks.get("hbm_gbs"):
         gbs = traffic / (dom_ms / 1e3) / 1e9
