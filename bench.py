@@ -67,6 +67,57 @@ SM_COUNT, FP32_LANES = 152, 128
 ONE_CTA_SCAN = 48 * 1024
 
 
+def roofline_entry(counts, stages, K, clocks, sha, peaks):
+    """Roofline of the dominant splat kernel from the exact work counts of K launches
+    (tested, candidate, composited pairs), the per-stage CUDA-event times (ms lists),
+    the sampled clocks, the kernel source hash (profile-derived constants apply only
+    to the source they were taken on) and the measured peaks.  FP32 work of the
+    formulas against the FP32 peak; special functions, instruction issue and DRAM
+    as the other roofs."""
+    tested, cand, comp = counts
+    sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES * 2 * sm_clock * 1e6 / 1e12
+    if "splat_fused" in stages:
+        # one walk: candidates evaluated once, composited pairs forward + adjoint
+        dom, dom_ms = "splat_fused", statistics.mean(stages["splat_fused"])
+        flops = (cand * FLOP_CAND + comp * (FLOP_COMP_FWD + FLOP_COMP_BWD)) / K
+    else:
+        fwd_ms = statistics.mean(stages["splat_fwd"])
+        bwd_ms = statistics.mean(stages["splat_bwd"])
+        dom = "splat_bwd" if bwd_ms >= fwd_ms else "splat_fwd"
+        dom_ms = max(fwd_ms, bwd_ms)
+        flops = ((cand * FLOP_CAND + comp * FLOP_COMP_BWD) if dom == "splat_bwd"
+                 else (cand * FLOP_CAND + comp * FLOP_COMP_FWD)) / K
+    achieved = flops / (dom_ms / 1e3) / 1e12
+    traffic = TRAFFIC.get(dom) if TRAFFIC.get("src_sha") == sha else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_clock,
+                "per_launch": {"candidate_pairs": cand // K, "composited_pairs": comp // K,
+                               "tested_pairs": tested // K, "ms": round(dom_ms, 4)}}
+    mufu = (cand * MUFU_CAND + (comp * MUFU_COMP_BWD if dom != "splat_fwd" else 0)) / K
+    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * sm_clock * 1e6 / 1e12
+    roofline["other_roofs"] = {
+        "mufu": {"achieved": round(mufu / (dom_ms / 1e3) / 1e12, 4), "peak": round(mufu_peak, 3),
+                 "unit": "Tops/s", "frac": round(mufu / (dom_ms / 1e3) / 1e12 / mufu_peak, 4),
+                 "peak_basis": "152 SMs x 16 per clock x %.0f MHz" % sm_clock}}
+    instr = INSTR.get(dom) if INSTR.get("src_sha") == sha else None
+    if instr:
+        ips = instr / (dom_ms / 1e3) / 1e9
+        ipeak = SM_COUNT * SCHEDULERS_PER_SM * sm_clock * 1e6 / 1e9
+        roofline["other_roofs"]["issue"] = {
+            "achieved": round(ips, 1), "peak": round(ipeak, 1), "unit": "G warp instructions/s",
+            "frac": round(ips / ipeak, 4),
+            "peak_basis": "152 SMs x 4 schedulers x %.0f MHz; instructions from the ncu capture of one "
+                          "launch of the same kernel source" % sm_clock}
+    if traffic and (peaks or {}).get("hbm_gbs"):
+        gbs = traffic / (dom_ms / 1e3) / 1e9
+        roofline["other_roofs"]["hbm"] = {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                          "frac": round(gbs / peaks["hbm_gbs"], 4),
+                                          "peak_basis": "measured copy bandwidth (ncu DRAM bytes of the launch)"}
+    return roofline
+
+
 def measured_peaks() -> dict:
     """The copy bandwidth and GEMM rates measured on the GPUs this runs on (MEASURED_PEAKS.json
     at the repository root), or {} if the file is absent."""
@@ -398,52 +449,8 @@ def run_ours(args, rank, world, local_rank):
     pix = VIEWS_PER_STEP * H * W
     value = RK.job_throughput(RK.sum_over_ranks(pix * args.steps, device), dev_ms / 1e3) / 1e6
 
-    # roofline of the dominant kernel (ALU-bound: FP32 work of the formulas),
-    # its duration from the eager pass's CUDA events on the launching stream
     tested, cand, comp = counts
-    K = args.steps
-    sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT * FP32_LANES * 2 * sm_clock * 1e6 / 1e12
-    if "splat_fused" in stages:
-        # one walk: candidates evaluated once, composited pairs forward + adjoint
-        dom, dom_ms = "splat_fused", statistics.mean(stages["splat_fused"])
-        flops = (cand * FLOP_CAND + comp * (FLOP_COMP_FWD + FLOP_COMP_BWD)) / K
-    else:
-        fwd_ms = statistics.mean(stages["splat_fwd"])
-        bwd_ms = statistics.mean(stages["splat_bwd"])
-        dom = "splat_bwd" if bwd_ms >= fwd_ms else "splat_fwd"
-        dom_ms = max(fwd_ms, bwd_ms)
-        flops = ((cand * FLOP_CAND + comp * FLOP_COMP_BWD) if dom == "splat_bwd"
-                 else (cand * FLOP_CAND + comp * FLOP_COMP_FWD)) / K
-    achieved = flops / (dom_ms / 1e3) / 1e12
-    traffic = TRAFFIC.get(dom) if TRAFFIC.get("src_sha") == src_hash() else None
-    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_clock,
-                "per_launch": {"candidate_pairs": cand // K, "composited_pairs": comp // K,
-                               "tested_pairs": tested // K, "ms": round(dom_ms, 4)}}
-    # the other two roofs of this kernel: special functions and DRAM
-    mufu = (cand * MUFU_CAND + (comp * MUFU_COMP_BWD if dom != "splat_fwd" else 0)) / K
-    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * sm_clock * 1e6 / 1e12
-    roofline["other_roofs"] = {
-        "mufu": {"achieved": round(mufu / (dom_ms / 1e3) / 1e12, 4), "peak": round(mufu_peak, 3),
-                 "unit": "Tops/s", "frac": round(mufu / (dom_ms / 1e3) / 1e12 / mufu_peak, 4),
-                 "peak_basis": "152 SMs x 16 per clock x %.0f MHz" % sm_clock}}
-    instr = INSTR.get(dom) if INSTR.get("src_sha") == src_hash() else None
-    if instr:
-        ips = instr / (dom_ms / 1e3) / 1e9
-        ipeak = SM_COUNT * SCHEDULERS_PER_SM * sm_clock * 1e6 / 1e9
-        roofline["other_roofs"]["issue"] = {
-            "achieved": round(ips, 1), "peak": round(ipeak, 1), "unit": "G warp instructions/s",
-            "frac": round(ips / ipeak, 4),
-            "peak_basis": "152 SMs x 4 schedulers x %.0f MHz; instructions from the ncu capture of one "
-                          "launch of the same kernel source" % sm_clock}
-    peaks = measured_peaks()
-    if traffic and peaks.get("hbm_gbs"):
-        gbs = traffic / (dom_ms / 1e3) / 1e9
-        roofline["other_roofs"]["hbm"] = {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                          "frac": round(gbs / peaks["hbm_gbs"], 4),
-                                          "peak_basis": "measured copy bandwidth (ncu DRAM bytes of the launch)"}
+    roofline = roofline_entry(counts, stages, args.steps, clocks, src_hash(), measured_peaks())
 
     cfg = workload_config(args, world)
     cfg["tile"] = "%dx%d" % tile

@@ -28,3 +28,56 @@ def test_bench_accepts_driver_flags(monkeypatch):
     assert a.gpus == 1 and a.steps == 7 and a.warmup == 3 and a.impl == "ours"
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference"])
     assert bench.parse().impl == "reference"
+
+
+def test_roofline_entry_arithmetic():
+    # 10 launches of 1 ms with 2e8 candidate and 1e8 composited pairs in total at 2,070 MHz:
+    # FP32 work per launch (2e7 x 27 + 1e7 x 78) = 1.32 GFLOP -> 1.32 TFLOP/s of 80.55
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.roofline_entry((5e8, 2e8, 1e8), {"splat_fused": [1.0] * 10}, 10,
+                             {"sm_max_mhz": 2070.0}, "no-such-source", {"hbm_gbs": 6790.0})
+    assert r["kernel"] == "splat_fused" and r["bound"] == "alu"
+    assert abs(r["achieved"] - 1.32) < 1e-9 and abs(r["peak"] - 80.55) < 0.01
+    assert r["per_launch"]["candidate_pairs"] == 2e7 and r["per_launch"]["composited_pairs"] == 1e7
+    # special functions: (2e7 x 3 + 1e7 x 4) per ms = 0.1 Tops/s of 152 x 16 x 2.07 GHz
+    assert abs(r["other_roofs"]["mufu"]["achieved"] - 0.1) < 1e-9
+    assert abs(r["other_roofs"]["mufu"]["peak"] - 5.034) < 1e-3
+    # profile-derived roofs apply only to the source they were measured on
+    assert r["traffic"] is None and "issue" not in r["other_roofs"] and "hbm" not in r["other_roofs"]
+    r2 = bench.roofline_entry((5e8, 2e8, 1e8), {"splat_fused": [1.0] * 10}, 10,
+                              {"sm_max_mhz": 2070.0}, bench.INSTR["src_sha"], {"hbm_gbs": 6790.0})
+    assert r2["traffic"] == bench.TRAFFIC["splat_fused"]
+    assert abs(r2["other_roofs"]["issue"]["achieved"] - bench.INSTR["splat_fused"] / 1e6) < 0.06
+    assert abs(r2["other_roofs"]["hbm"]["achieved"] - bench.TRAFFIC["splat_fused"] / 1e6) < 0.1
+
+
+def test_bench_functions_bind_every_name_they_read():
+    # every name a top-level function of bench.py reads (nested functions included) is bound
+    # in it, at module level, or a builtin: catches a local lost in a refactor without a GPU
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    module = set(dir(builtins))
+    for n in tree.body:
+        if isinstance(n, (ast.FunctionDef, ast.ClassDef)):
+            module.add(n.name)
+        elif isinstance(n, ast.Assign):
+            module |= {x.id for t in n.targets for x in ast.walk(t) if isinstance(x, ast.Name)}
+        elif isinstance(n, (ast.Import, ast.ImportFrom)):
+            module |= {(a.asname or a.name).split(".")[0] for a in n.names}
+    for f in (n for n in tree.body if isinstance(n, ast.FunctionDef)):
+        bound = set()
+        for x in ast.walk(f):
+            if isinstance(x, ast.Name) and isinstance(x.ctx, (ast.Store, ast.Del)):
+                bound.add(x.id)
+            elif isinstance(x, (ast.FunctionDef, ast.Lambda)):
+                if isinstance(x, ast.FunctionDef):
+                    bound.add(x.name)
+                a = x.args
+                bound |= {y.arg for y in a.args + a.kwonlyargs + a.posonlyargs}
+                bound |= {y.arg for y in (a.vararg, a.kwarg) if y is not None}
+            elif isinstance(x, (ast.Import, ast.ImportFrom)):
+                bound |= {(a.asname or a.name).split(".")[0] for a in x.names}
+            elif isinstance(x, ast.ExceptHandler) and x.name:
+                bound.add(x.name)
+        loads = {x.id for x in ast.walk(f) if isinstance(x, ast.Name) and isinstance(x.ctx, ast.Load)}
+        assert not loads - bound - module, (f.name, sorted(loads - bound - module))
