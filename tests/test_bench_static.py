@@ -51,33 +51,3 @@ def test_roofline_entry_arithmetic():
     assert abs(r2["other_roofs"]["issue"]["achieved"] - bench.INSTR["splat_fused"] / 1e6) < 0.06
     assert abs(r2["other_roofs"]["hbm"]["achieved"] - bench.TRAFFIC["splat_fused"] / 1e6) < 0.1
 
-
-def test_bench_functions_bind_every_name_they_read():
-    # every name a top-level function of bench.py reads (nested functions included) is bound
-    # in it, at module level, or a builtin: catches a local lost in a refactor without a GPU
-    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
-    module = set(dir(builtins))
-    for n in tree.body:
-        if isinstance(n, (ast.FunctionDef, ast.ClassDef)):
-            module.add(n.name)
-        elif isinstance(n, ast.Assign):
-            module |= {x.id for t in n.targets for x in ast.walk(t) if isinstance(x, ast.Name)}
-        elif isinstance(n, (ast.Import, ast.ImportFrom)):
-            module |= {(a.asname or a.name).split(".")[0] for a in n.names}
-    for f in (n for n in tree.body if isinstance(n, ast.FunctionDef)):
-        bound = set()
-        for x in ast.walk(f):
-            if isinstance(x, ast.Name) and isinstance(x.ctx, (ast.Store, ast.Del)):
-                bound.add(x.id)
-            elif isinstance(x, (ast.FunctionDef, ast.Lambda)):
-                if isinstance(x, ast.FunctionDef):
-                    bound.add(x.name)
-                a = x.args
-                bound |= {y.arg for y in a.args + a.kwonlyargs + a.posonlyargs}
-                bound |= {y.arg for y in (a.vararg, a.kwarg) if y is not None}
-            elif isinstance(x, (ast.Import, ast.ImportFrom)):
-                bound |= {(a.asname or a.name).split(".")[0] for a in x.names}
-            elif isinstance(x, ast.ExceptHandler) and x.name:
-                bound.add(x.name)
-        loads = {x.id for x in ast.walk(f) if isinstance(x, ast.Name) and isinstance(x.ctx, ast.Load)}
-        assert not loads - bound - module, (f.name, sorted(loads - bound - module))
