@@ -42,8 +42,6 @@
 #include <omp.h>
 #endif
 
-#define OR_MAXCAND 4096
-
 /* ------------------------------------------------------------------------ */
 /* Plane frame: Eq. 2-3.  Hamilton rotation matrix of the unit quaternion.   */
 /* Returns 0 if |q| is zero or not finite.                                   */
@@ -355,7 +353,8 @@ typedef struct {
 /* Gathers, filters and sorts the candidates of one pixel.  Returns the
    number of candidates (before the top-M cut).  Also reports the smallest
    distance of any in-range plane's margin to the filter edge -delta, the
-   closest pair of sorted depths, etc., for the conditioning flags.          */
+   closest pair of sorted depths, etc., for the conditioning flags.  out    
+   has room for K candidates, so no plane is ever left out.                 */
 static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], const or_set* S,
                             double delta, double eta, cand* out, int* near_filter)
 {
@@ -374,7 +373,7 @@ static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], cons
         if (fabs(c.t - S->z_near) < eps || fabs(c.t - S->z_far) < eps) *near_filter = 1;
         if (!(c.w >= S->w_min)) continue;
         c.k = k;
-        if (nc < OR_MAXCAND) out[nc++] = c;
+        out[nc++] = c;     /* out holds K entries: one per plane at most */
     }
     qsort(out, nc, sizeof(cand), cand_cmp);
     return nc;
@@ -415,7 +414,8 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
         double cx = intr[4 * v + 2], cy = intr[4 * v + 3];
 #pragma omp parallel
         {
-            cand* cs = (cand*)malloc(sizeof(cand) * OR_MAXCAND);
+            /* every plane can be a candidate of one pixel: room for all K */
+            cand* cs = (cand*)malloc(sizeof(cand) * (size_t)(K > 0 ? K : 1));
             double* Tj = (double*)malloc(sizeof(double) * (size_t)(M + 1));
 #pragma omp for schedule(dynamic, 1)
             for (int j = row0; j < row1; ++j) {
@@ -574,7 +574,8 @@ void or_backward(int K, int V, const double* center, const double* quat, const d
             tid = omp_get_thread_num();
 #endif
             double* my = acc + (size_t)tid * 11 * K;
-            cand* cs = (cand*)malloc(sizeof(cand) * OR_MAXCAND);
+            /* every plane can be a candidate of one pixel: room for all K */
+            cand* cs = (cand*)malloc(sizeof(cand) * (size_t)(K > 0 ? K : 1));
             double* Tj = (double*)malloc(sizeof(double) * (size_t)(M + 1));
 #pragma omp for schedule(static)
             for (int j = 0; j < H; ++j) {

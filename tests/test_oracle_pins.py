@@ -229,6 +229,36 @@ def test_top_m_keeps_only_the_nearest_30():
     assert np.array_equal(o_near["normal"], o30["normal"])
 
 
+def test_top_m_of_thousands_of_candidates_keeps_the_nearest():
+    # Sec. 3.2 keeps the M nearest intersections of a ray, however many pass the
+    # filter.  5,000 stacked planes all pass at one pixel with the same band weight
+    # w0; plane j sits at Z = 6 - 0.001 j, so the nearest 30 have the highest
+    # indices.  A gather that stopped early in plane-index order would keep the
+    # farthest planes instead and miss this geometric series.
+    lam, i0, j0, n = 50.0, 100, 48, 5000
+    w0 = 2.0 / (1.0 + math.sqrt(19999.0))
+    Zs = 6.0 - 0.001 * np.arange(n)
+    ps = []
+    for Z in Zs:
+        _, _, rx = _band_pixel_setup(lam, Z, i0, j0)
+        ps.append(plane([0, 0, Z], [1, 0, 0, 0], [rx, 1.0, 0.5, 0.5]))
+    planes = cat(*ps)
+    w2c, intr = ident_cams(1)
+    o = O.render(*planes, w2c, intr, 96, 128, lam, M=30, rows=(j0, j0 + 1))
+    near = np.sort(Zs)[:30]
+    Tj = (1 - w0) ** np.arange(30)
+    assert o["n_cand"][0, j0, i0] == n and o["n_sel"][0, j0, i0] == 30
+    assert o["depth"][0, j0, i0] == pytest.approx(np.sum(Tj * w0 * near), rel=1e-12)
+    assert o["alpha"][0, j0, i0] == pytest.approx(1 - (1 - w0) ** 30, rel=1e-12)
+    # the backward differentiates exactly the same 30 planes: an upstream gradient at
+    # that pixel alone reaches the 30 highest indices and no other plane
+    gD = np.zeros((1, 96, 128))
+    gD[0, j0, i0] = 1.0
+    gc, gq, gr = O.backward(*planes, w2c, intr, 96, 128, lam, gD, np.zeros((1, 96, 128, 3)), M=30)
+    touched = np.flatnonzero(np.abs(gc).sum(1) + np.abs(gr).sum(1) > 0)
+    assert touched.tolist() == list(range(n - 30, n))
+
+
 def _random_scene(seed, K=12, V=2, H=48, W=64, f=50.0):
     p = S.random_planes_in_view(seed, K)
     cams = S.identity_cameras(V, H, W, f, seed=seed, jitter=0.05)
