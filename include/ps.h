@@ -235,8 +235,9 @@ ps_status ps_loss(const ps_frame* frame, const ps_settings* settings, const floa
                   const float* normal, const float* gt_depth, const float* gt_normal,
                   float* dL_dD, float* dL_dN, double* view_sums, ps_stream stream);
 
-/* Bytes of scratch that ps_splat_bwd needs (per-record gradient accumulators
-   and a work counter). */
+/* Bytes of scratch that ps_splat_bwd and ps_splat_fused need (per-record
+   gradient accumulators, a work counter and, for ps_splat_fused, 32 partial
+   loss sums per view). */
 size_t ps_bwd_workspace_bytes(const ps_frame* frame);
 
 /* Backward splatting: gradient of sum(dL_dD * D + dL_dN . N) with respect to
@@ -324,6 +325,36 @@ ps_status ps_count_pairs(const ps_frame* frame, const ps_settings* settings, con
    lambda, delta and Adam bias corrections. */
 ps_status ps_step_advance(ps_step_state* d_state, const ps_step_state* d_sched, int n_sched,
                           int* d_iter, ps_stream stream);
+
+/* ---- Host-side schedule of the optimisation.  Plain host functions: no device
+   work, no CUDA call; usable without a GPU. ---- */
+
+/* Eq. 10: lambda = min(20 exp(-(1 - 0.001 ite)), 300), evaluated in FP64; ite
+   counts optimisation iterations from 0. */
+double ps_lambda_schedule(int ite);
+
+/* The binning margin delta of ps_settings: the distance outside a rectangle's
+   edge at which the weight 2 sigmoid(5 lambda m) of Eq. 7-8 falls to the filter
+   threshold of Sec. 3.2, 2 sigmoid(-5 lambda delta) = w_min, i.e.
+   delta = ln((1 - w_min/2) / (w_min/2)) / (5 lambda), in FP64.  Returns NaN if
+   lambda <= 0 or w_min is not in (0, 1). */
+double ps_filter_margin(double lambda, double w_min);
+
+/* With PS_GAUSSIAN the binning scales every radius by kappa, where the Eq. 5
+   weight of one axis falls to w_min: exp(-kappa^2 / 2) = w_min, kappa =
+   sqrt(2 ln(1 / w_min)).  NaN if w_min is not in (0, 1). */
+double ps_gauss_extent(double w_min);
+
+/* Fills out[0 .. n-1] (host memory, caller-owned) with the per-iteration scalars
+   of iterations first .. first + n - 1 for ps_step_advance: lambda = Eq. 10 at
+   iteration ite + lam_offset rounded to f32, delta = ps_filter_margin(that f32
+   lambda, w_min), step = ite + 1 (Adam counts from 1), bc1 = 1 - b1^step and
+   bc2 = 1 - b2^step rounded to f32 (the values ps_adam_step computes for that
+   step).  A fit from a good initialisation may pass lam_offset > 0 to start the
+   schedule later; Adam's step count is not shifted.  PS_ERR_ARG if first < 0,
+   n < 0, out is NULL with n > 0, b1 or b2 is outside [0, 1) or w_min outside (0, 1). */
+ps_status ps_step_schedule(int first, int n, int lam_offset, float b1, float b2, double w_min,
+                           ps_step_state* out);
 
 /* Plane splitting, part 1 (Sec. 3.3 "Plane Splitting", App. A.2): adds this
    step's radius gradients to a running sum.  g_radii [P][4] (device, the

@@ -51,6 +51,11 @@ constexpr int kWarps = 4;                 // warps per CTA of the splat kernels
 // Eq. 14 loss and backward fused in one walk per pixel.
 constexpr int kFwd = 0, kBwd = 1, kFused = 2;
 
+// Fused mode: per-view loss sums are added into kSlots partial sums per view
+// (spread over L2 slices, so that strips of one view do not serialise on one
+// address), which the chain kernel adds up into view_sums.
+constexpr int kSlots = 32;
+
 struct SplatArgs {
     const ps_view* views;
     int n_views;
@@ -79,7 +84,7 @@ struct SplatArgs {
     const float* gt_normal;
     float* out_dLdD;          // optional
     float* out_dLdN;          // optional
-    double* view_sums;        // [V][4]
+    double* vs_slots;         // [V][kSlots][4] partial loss sums (zeroed before the launch)
     float a_cos, a_l1n, a_depth;
 };
 
@@ -303,8 +308,16 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
 }
 
 // One strip: pixel setup, walk, then the forward output or the backward adjoint.
+// The lane's Eq. 14 terms of a fused strip: |1 - N.N*|, ||N - N*||_1, |D - D*|,
+// 1 (supervised pixels), and the strip's view.
+struct StripLoss {
+    int v;
+    float sc, sl, sd, one;
+};
+
 template <int TW, int TH, int MODE>
-__device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int2* stk_warp, int item)
+__device__ __forceinline__ StripLoss run_strip(const SplatArgs& a, WarpStage& ws, int2* stk_warp,
+                                               int item)
 {
     constexpr int NS = TW * TH / 32;       // strips per tile
     const int lane = threadIdx.x & 31;
@@ -384,6 +397,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
         }
     }
     bool supervised = inside;
+    StripLoss out{v, 0.f, 0.f, 0.f, 0.f};
     if constexpr (MODE == kFused) {
         // Eq. 14 at this pixel and its gradient with respect to D and N
         float sc = 0.f, sl = 0.f, sd = 0.f, one = 0.f;
@@ -411,22 +425,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
                 a.out_dLdN[3 * pix + 2] = gN2;
             }
         }
-        // the strip's 32 pixels belong to one view: one set of atomics per strip
-        double x0 = sc, x1 = sl, x2 = sd, x3 = one;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x0 += __shfl_xor_sync(kFull, x0, o);
-            x1 += __shfl_xor_sync(kFull, x1, o);
-            x2 += __shfl_xor_sync(kFull, x2, o);
-            x3 += __shfl_xor_sync(kFull, x3, o);
-        }
-        if (lane == 0 && x3 > 0.0) {
-            double* vs = a.view_sums + 4 * (size_t)v;
-            atomicAdd(vs + 0, x0);
-            atomicAdd(vs + 1, x1);
-            atomicAdd(vs + 2, x2);
-            atomicAdd(vs + 3, x3);
-        }
+        out.sc = sc; out.sl = sl; out.sd = sd; out.one = one;
     }
     if constexpr (MODE != kFwd) {
         // back to front over the stack
@@ -576,6 +575,7 @@ __device__ __forceinline__ void run_strip(const SplatArgs& a, WarpStage& ws, int
             }
         }
     }
+    return out;
 }
 
 // Persistent warps: each takes strips from the work counter until none is left.
@@ -600,13 +600,45 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == kFwd ? 6 : 5) k_splat(Spl
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     int2* stk_warp = dyn_stk + (size_t)w * a.M * 32;
+    // fused: the lane's loss terms over the warp's consecutive strips of one view (items
+    // are handed out in increasing order, so a warp meets each view in one run)
+    int vcur = -1;
+    float l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f;
+    const int slot = (blockIdx.x * kWarps + w) % kSlots;
+    auto flush_loss = [&]() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            l0 += __shfl_xor_sync(kFull, l0, o);
+            l1 += __shfl_xor_sync(kFull, l1, o);
+            l2 += __shfl_xor_sync(kFull, l2, o);
+            l3 += __shfl_xor_sync(kFull, l3, o);
+        }
+        if (lane == 0 && l3 > 0.f) {
+            double* d = a.vs_slots + ((size_t)vcur * kSlots + slot) * 4;
+            atomicAdd(d + 0, (double)l0);
+            atomicAdd(d + 1, (double)l1);
+            atomicAdd(d + 2, (double)l2);
+            atomicAdd(d + 3, (double)l3);
+        }
+        l0 = l1 = l2 = l3 = 0.f;
+    };
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.counter, 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= a.n_items) break;
-        run_strip<TW, TH, MODE>(a, stage[w], stk_warp, item);
+        const StripLoss sl = run_strip<TW, TH, MODE>(a, stage[w], stk_warp, item);
+        if constexpr (MODE == kFused) {
+            if (sl.v != vcur) {
+                if (vcur >= 0) flush_loss();
+                vcur = sl.v;
+            }
+            l0 += sl.sc; l1 += sl.sl; l2 += sl.sd; l3 += sl.one;
+        }
         __syncwarp();
+    }
+    if constexpr (MODE == kFused) {
+        if (vcur >= 0) flush_loss();
     }
 }
 
@@ -704,11 +736,21 @@ struct ChainArgs {
     float* g_quat;
     float* g_radii;
     int single_radii;
+    const double* vs_slots;   // fused: [V][kSlots][4] partial loss sums, or NULL
+    double* view_sums;        // fused: [V][4] written from vs_slots
 };
 
 __global__ void __launch_bounds__(128) k_chain(ChainArgs a)
 {
     const int v = blockIdx.y;
+    if (a.vs_slots && blockIdx.x == 0 && threadIdx.x < 4) {
+        // the fused kernel's loss sums of view v, added up in a fixed order
+        const double* sp = a.vs_slots + (size_t)v * kSlots * 4 + threadIdx.x;
+        double t = 0.0;
+        for (int i = 0; i < kSlots; ++i) t += sp[4 * i];
+        a.view_sums[4 * v + threadIdx.x] = t;
+    }
+    if (!a.g_rec) return;
     const ps_view* vw = a.views + v;
     const int K = __ldg(&vw->K);
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -952,9 +994,16 @@ cudaError_t launch_count(const SplatArgs& a, int n_tiles, unsigned long long* co
 
 constexpr size_t kCounterBytes = 256;
 
+// ps_splat_bwd: the record gradients, then the work counter
 inline size_t bwd_ws(const ps_frame* f)
 {
     return sizeof(float4) * 4 * (size_t)f->n_records + kCounterBytes;
+}
+
+// ps_splat_fused: as ps_splat_bwd, then the per-view partial loss sums
+inline size_t fused_ws(const ps_frame* f)
+{
+    return bwd_ws(f) + sizeof(double) * 4 * kSlots * (size_t)f->n_views;
 }
 
 }  // namespace
@@ -1009,8 +1058,8 @@ extern "C" ps_status ps_splat_ids(const ps_frame* f, const ps_settings* s, const
 
 extern "C" size_t ps_bwd_workspace_bytes(const ps_frame* f)
 {
-    if (!f || f->n_records < 0) return 0;
-    return bwd_ws(f);
+    if (!f || f->n_records < 0 || f->n_views < 0) return 0;
+    return fused_ws(f);
 }
 
 extern "C" ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* f, const ps_settings* s,
@@ -1042,6 +1091,7 @@ extern "C" ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* f, co
     c.views = f->views; c.center = planes->center; c.quat = planes->quat; c.radii = planes->radii;
     c.g_rec = a.g_rec; c.g_center = g_center; c.g_quat = g_quat; c.g_radii = g_radii;
     c.single_radii = (s->flags & PS_SINGLE_RADII) ? 1 : 0;
+    c.vs_slots = nullptr; c.view_sums = nullptr;
     dim3 grid((f->max_K + 127) / 128, f->n_views);
     k_chain<<<grid, 128, 0, st>>>(c);
     PS_LAUNCH_CHECK();
@@ -1062,12 +1112,12 @@ extern "C" ps_status ps_splat_fused(const ps_planes* planes, const ps_frame* f,
     if (!gt_depth || !gt_normal || !view_sums || !g_center || !g_quat || !g_radii || !ws)
         return PS_ERR_ARG;
     if (s->flags & PS_HARD) return PS_ERR_ARG;
-    if (ws_bytes < bwd_ws(f) || (reinterpret_cast<uintptr_t>(ws) & 15)) return PS_ERR_ARG;
+    if (ws_bytes < fused_ws(f) || (reinterpret_cast<uintptr_t>(ws) & 15)) return PS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    PS_CUDA_CHECK(cudaMemsetAsync(view_sums, 0, sizeof(double) * 4 * (size_t)f->n_views, st));
     const size_t grec_bytes = sizeof(float4) * 4 * (size_t)f->n_records;
-    // the record gradients and the work counter after them: one memset
-    PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, grec_bytes + sizeof(int), st));
+    // record gradients, work counter and partial loss sums: one memset
+    PS_CUDA_CHECK(cudaMemsetAsync(ws, 0, fused_ws(f), st));
+    double* slots = reinterpret_cast<double*>(static_cast<char*>(ws) + bwd_ws(f));
     SplatArgs a{};
     a.views = f->views; a.n_views = f->n_views;
     a.rec = reinterpret_cast<const float4*>(rec); a.key = key;
@@ -1077,15 +1127,16 @@ extern "C" ps_status ps_splat_fused(const ps_planes* planes, const ps_frame* f,
     a.g_rec = reinterpret_cast<float4*>(ws); a.status = d_status;
     a.counter = reinterpret_cast<int*>(static_cast<char*>(ws) + grec_bytes);
     a.gt_depth = gt_depth; a.gt_normal = gt_normal;
-    a.out_dLdD = dL_dD; a.out_dLdN = dL_dN; a.view_sums = view_sums;
+    a.out_dLdD = dL_dD; a.out_dLdN = dL_dN; a.vs_slots = slots;
     a.a_cos = s->a_cos; a.a_l1n = s->a_l1n; a.a_depth = s->a_depth;
     if (dispatch<kFused>(a, s, f->n_tiles, st, true) != cudaSuccess) return PS_ERR_CUDA;
-    if (f->n_records == 0) return PS_OK;
     ChainArgs c;
     c.views = f->views; c.center = planes->center; c.quat = planes->quat; c.radii = planes->radii;
-    c.g_rec = a.g_rec; c.g_center = g_center; c.g_quat = g_quat; c.g_radii = g_radii;
+    c.g_rec = f->n_records > 0 ? a.g_rec : nullptr;
+    c.g_center = g_center; c.g_quat = g_quat; c.g_radii = g_radii;
     c.single_radii = (s->flags & PS_SINGLE_RADII) ? 1 : 0;
-    dim3 grid((f->max_K + 127) / 128, f->n_views);
+    c.vs_slots = slots; c.view_sums = view_sums;
+    dim3 grid(f->max_K > 0 ? (f->max_K + 127) / 128 : 1, f->n_views);
     k_chain<<<grid, 128, 0, st>>>(c);
     PS_LAUNCH_CHECK();
     return PS_OK;
