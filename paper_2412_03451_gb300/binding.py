@@ -8,7 +8,6 @@ missing, every call raises -- there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 import threading
 
@@ -30,7 +29,8 @@ EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin
            "ps_seed_im2col", "ps_seed_col2im", "ps_seed_relu_bwd", "ps_seed_transpose",
            "ps_seed_colsum", "ps_seed_pool", "ps_seed_pool_bwd", "ps_seed_loss", "ps_cast_bf16",
            "ps_radii_grad_accum", "ps_split_planes", "ps_merge_planes", "ps_status_string",
-           "ps_version")
+           "ps_version", "ps_lambda_schedule", "ps_filter_margin", "ps_gauss_extent",
+           "ps_step_schedule")
 
 
 class PsSettings(ctypes.Structure):
@@ -123,6 +123,10 @@ def load():
             "ps_merge_planes": ([P, I, P, F, F, P, P, P, P], I),
             "ps_status_string": ([I], ctypes.c_char_p),
             "ps_version": ([], I),
+            "ps_lambda_schedule": ([I], D),
+            "ps_filter_margin": ([D, D], D),
+            "ps_gauss_extent": ([D], D),
+            "ps_step_schedule": ([I, I, I, F, F, D, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -193,38 +197,29 @@ def make_settings(lam, delta, M=30, tile_w=16, tile_h=16, flags=0, w_min=1e-4, z
 
 
 def step_schedule(n: int, first: int = 0, b1: float = 0.9, b2: float = 0.999,
-                  lam_offset: int = 0) -> bytes:
-    """Packed ps_step_state entries for optimisation steps first .. first + n - 1:
-    lambda (Eq. 10 at iteration step + lam_offset, rounded to f32), the binning
-    margin of that f32 lambda, the Adam step number (step + 1) and its bias
-    corrections -- the same values the host path uses."""
+                  lam_offset: int = 0, w_min: float = 1e-4) -> bytes:
+    """Packed ps_step_state entries for optimisation steps first .. first + n - 1
+    (ps_step_schedule: Eq. 10 lambda, its binning margin, Adam's step number and
+    bias corrections)."""
     arr = (PsStepState * n)()
-    for i in range(n):
-        ite = first + i
-        lam = float(np.float32(lambda_schedule(ite + lam_offset)))
-        arr[i].lambda_ = lam
-        arr[i].delta = filter_margin(lam)
-        arr[i].step = ite + 1
-        arr[i].bc1 = float(np.float32(1.0 - b1 ** (ite + 1)))
-        arr[i].bc2 = float(np.float32(1.0 - b2 ** (ite + 1)))
+    _check(load().ps_step_schedule(int(first), int(n), int(lam_offset), float(b1), float(b2),
+                                   float(w_min), arr), "ps_step_schedule")
     return bytes(arr)
 
 
 def filter_margin(lam: float, w_min: float = 1e-4) -> float:
-    """delta with 2 sigmoid(-5 lam delta) = w_min (Eq. 7-8 and the Sec. 3.2 filter)."""
-    h = 0.5 * w_min
-    return math.log((1.0 - h) / h) / (5.0 * lam)
+    """ps_filter_margin: delta with 2 sigmoid(-5 lam delta) = w_min (Eq. 7-8, Sec. 3.2)."""
+    return float(load().ps_filter_margin(float(lam), float(w_min)))
 
 
 def gauss_extent(w_min: float = 1e-4) -> float:
-    """kappa with exp(-kappa^2 / 2) = w_min: with PS_GAUSSIAN the binning scales
-    every radius by kappa (the Eq. 5 weight passes the filter within kappa sigma)."""
-    return math.sqrt(2.0 * math.log(1.0 / w_min))
+    """ps_gauss_extent: the radius factor kappa of the Eq. 5 binning."""
+    return float(load().ps_gauss_extent(float(w_min)))
 
 
 def lambda_schedule(ite: int) -> float:
-    """Eq. 10: lambda = min(20 e^{-(1 - 0.001 ite)}, 300)."""
-    return min(20.0 * math.exp(-(1.0 - 0.001 * ite)), 300.0)
+    """ps_lambda_schedule: Eq. 10 at iteration ite (from 0)."""
+    return float(load().ps_lambda_schedule(int(ite)))
 
 
 # ---------------------------------------------------------------------------

@@ -368,6 +368,50 @@ extern "C" ps_status ps_adam_step(float* param, const float* grad, float* m, flo
     return PS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Host-side schedule of the optimisation (no device work).
+
+extern "C" double ps_lambda_schedule(int ite)
+{
+    // Eq. 10: the sharpness of the rectangle weight grows with the iteration
+    const double lam = 20.0 * exp(-(1.0 - 0.001 * (double)ite));
+    return lam < 300.0 ? lam : 300.0;
+}
+
+extern "C" double ps_filter_margin(double lambda, double w_min)
+{
+    // Eq. 7-8 and the w >= w_min filter of Sec. 3.2: 2 sigmoid(-5 lambda delta) = w_min
+    if (!(lambda > 0.0) || !(w_min > 0.0) || !(w_min < 1.0)) return NAN;
+    const double h = 0.5 * w_min;
+    return log((1.0 - h) / h) / (5.0 * lambda);
+}
+
+extern "C" double ps_gauss_extent(double w_min)
+{
+    // Eq. 5 on one axis: exp(-kappa^2 / 2) = w_min
+    if (!(w_min > 0.0) || !(w_min < 1.0)) return NAN;
+    return sqrt(2.0 * log(1.0 / w_min));
+}
+
+extern "C" ps_status ps_step_schedule(int first, int n, int lam_offset, float b1, float b2,
+                                      double w_min, ps_step_state* out)
+{
+    if (first < 0 || n < 0 || (n > 0 && !out)) return PS_ERR_ARG;
+    if (!(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f)) return PS_ERR_ARG;
+    if (!(w_min > 0.0) || !(w_min < 1.0)) return PS_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        const int ite = first + i;
+        const float lam = (float)ps_lambda_schedule(ite + lam_offset);
+        out[i].lambda = lam;
+        out[i].delta = ps_filter_margin((double)lam, w_min);
+        out[i].step = ite + 1;
+        // the same bias corrections as ps_adam_step computes for this step
+        out[i].bc1 = (float)(1.0 - pow((double)b1, (double)(ite + 1)));
+        out[i].bc2 = (float)(1.0 - pow((double)b2, (double)(ite + 1)));
+    }
+    return PS_OK;
+}
+
 extern "C" ps_status ps_step_advance(ps_step_state* d_state, const ps_step_state* d_sched,
                                      int n_sched, int* d_iter, ps_stream stream)
 {
