@@ -154,3 +154,41 @@ def test_gaussian_flag_checks(lib):
         code = lib.ps_splat_fwd(ctypes.byref(frame), ctypes.byref(s), dummy, dummy, dummy, dummy,
                                 1, dummy, dummy, None, dummy, 256, None, None)
         assert code == B.PS_ERR_ARG, flags
+
+
+def test_schedule_functions_host_only(lib):
+    # Eq. 10 and the filter margin of Eq. 7-8 / Sec. 3.2, computed by the library on the host,
+    # against the oracle's independent definitions and closed forms
+    import math
+    from oracle import oracle as O
+    from paper_2412_03451_gb300 import binding as B
+    for ite in (0, 1, 999, 1000, 2000, 5703, 5704, 10000):
+        assert B.lambda_schedule(ite) == O.lambda_schedule(ite)
+    assert B.lambda_schedule(0) == pytest.approx(20.0 / math.e, rel=1e-15)
+    assert B.lambda_schedule(1000) == pytest.approx(20.0, rel=1e-15)
+    assert B.lambda_schedule(10 ** 6) == 300.0
+    for lam in (7.36, 20.0, 300.0):
+        d = B.filter_margin(lam)
+        assert d == pytest.approx(O.filter_margin(lam), rel=1e-15)
+        # 2 sigmoid(-5 lam delta) = w_min
+        assert 2.0 / (1.0 + math.exp(5.0 * lam * d)) == pytest.approx(1e-4, rel=1e-12)
+    assert math.isnan(B.filter_margin(0.0)) and math.isnan(B.filter_margin(1.0, 1.5))
+    k = B.gauss_extent()
+    assert math.exp(-0.5 * k * k) == pytest.approx(1e-4, rel=1e-12)
+    raw = B.step_schedule(5, first=998, lam_offset=2)
+    st = (B.PsStepState * 5).from_buffer_copy(raw)
+    for i, e in enumerate(st):
+        ite = 998 + i
+        assert e.step == ite + 1
+        assert e.lambda_ == np.float32(O.lambda_schedule(ite + 2))
+        assert e.delta == pytest.approx(O.filter_margin(float(np.float32(O.lambda_schedule(ite + 2)))),
+                                        rel=1e-15)
+        assert e.bc1 == np.float32(1.0 - np.float64(np.float32(0.9)) ** (ite + 1))
+        assert e.bc2 == np.float32(1.0 - np.float64(np.float32(0.999)) ** (ite + 1))
+    # argument checks happen on the host
+    arr = (B.PsStepState * 1)()
+    assert lib.ps_step_schedule(-1, 1, 0, 0.9, 0.999, 1e-4, arr) == B.PS_ERR_ARG
+    assert lib.ps_step_schedule(0, 1, 0, 1.0, 0.999, 1e-4, arr) == B.PS_ERR_ARG
+    assert lib.ps_step_schedule(0, 1, 0, 0.9, 0.999, 0.0, arr) == B.PS_ERR_ARG
+    assert lib.ps_step_schedule(0, 1, 0, 0.9, 0.999, 1e-4, None) == B.PS_ERR_ARG
+    assert lib.ps_step_schedule(0, 0, 0, 0.9, 0.999, 1e-4, None) == B.PS_OK

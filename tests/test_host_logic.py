@@ -40,3 +40,27 @@ def test_scene_generators_are_seeded():
     assert not np.array_equal(a.gt.center, c.gt.center)
     p, q = S.surface_init(a, 200, 5), S.surface_init(a, 200, 5)
     assert np.array_equal(p.center, q.center) and np.array_equal(p.radii, q.radii)
+
+
+def test_sphere_init_on_bounding_sphere_facing_its_centre():
+    # Sec. 4.3 ablation start: planes of radius 0.05 on the scene's bounding sphere
+    # (centre of the room box, radius half its diagonal), normals toward the centre
+    from scipy.spatial.transform import Rotation
+    room = S.large_room(1005, n_rect=300, n_views=4)
+    p = S.sphere_init(room, 500, 3)
+    size = np.asarray(room.size, np.float64)
+    centre = size / 2.0
+    R = 0.5 * np.linalg.norm(size)
+    off = p.center.astype(np.float64) - centre
+    assert np.allclose(np.linalg.norm(off, axis=1), R, rtol=1e-6)
+    # third column of the rotation of (w, x, y, z) is the plane normal (Eq. 2-3)
+    q = p.quat.astype(np.float64)
+    mats = Rotation.from_quat(np.concatenate([q[:, 1:], q[:, :1]], axis=1)).as_matrix()
+    n = mats[:, :, 2]
+    assert np.allclose(n, -off / np.linalg.norm(off, axis=1, keepdims=True), atol=1e-5)
+    assert np.all(p.radii == np.float32(0.05))
+    # directions cover the sphere (no hemisphere left empty)
+    u = off / R
+    assert (u[:, 0] > 0.5).any() and (u[:, 0] < -0.5).any() and (u[:, 2] > 0.5).any() and (u[:, 2] < -0.5).any()
+    q2 = S.sphere_init(room, 500, 3)
+    assert np.array_equal(p.center, q2.center) and np.array_equal(p.quat, q2.quat)
