@@ -80,7 +80,7 @@ def _load():
                                       I, I, P, P, P, P, P, P, P]
             lib.or_loss.argtypes = [I, I, I, P, P, P, P, D, D, D, P, P, P]
             lib.or_loss.restype = D
-            lib.or_backward.argtypes = [I, I, P, P, P, P, P, I, I, D, D, D, D, I, I, P, P, P, P, P]
+            lib.or_backward.argtypes = [I, I, P, P, P, P, P, I, I, D, D, D, D, I, I, P, P, P, P, P, P]
             lib.or_raycast.argtypes = [I, I, P, P, P, P, P, I, I, D, D, I, I, P, P, P]
             lib.or_adam.argtypes = [L, P, P, P, P, D, D, D, D, I, D]
             lib.or_num_threads.restype = I
@@ -287,18 +287,24 @@ def loss(depth, normal, gt_depth, gt_normal, a_cos=ALPHA1, a_l1n=ALPHA1, a_depth
 
 
 def backward(center, quat, radii, w2c, intr, H, W, lam, dLdD, dLdN, M=M_DEFAULT,
-             w_min=W_MIN, z_near=Z_NEAR, z_far=Z_FAR, single_radii=False, gaussian=False):
+             w_min=W_MIN, z_near=Z_NEAR, z_far=Z_FAR, single_radii=False, gaussian=False,
+             with_abs=False):
     """Analytic FP64 gradient of sum(dLdD * D + dLdN . N) with respect to the
-    plane centers [K,3], quaternions [K,4] and radii [K,4]."""
+    plane centers [K,3], quaternions [K,4] and radii [K,4].  With with_abs, a fourth
+    array [K,11] holds per plane and parameter the sum of the absolute per-pixel
+    contributions (how much the sum cancels)."""
     c, q, r = _f64(center), _f64(quat), _f64(radii)
     Rt, K_ = _f64(w2c).reshape(-1, 12), _f64(intr).reshape(-1, 4)
     K, V = c.shape[0], Rt.shape[0]
     gD, gN = _f64(dLdD), _f64(dLdN)
     gc, gq, gr = np.zeros((K, 3)), np.zeros((K, 4)), np.zeros((K, 4))
+    ga = np.zeros((K, 11)) if with_abs else None
     _load().or_backward(K, V, _ptr(c), _ptr(q), _ptr(r), _ptr(Rt), _ptr(K_), H, W,
                         float(lam), float(w_min), float(z_near), float(z_far), int(M),
                         _flags(single_radii, gaussian), _ptr(gD), _ptr(gN), _ptr(gc), _ptr(gq),
-                        _ptr(gr))
+                        _ptr(gr), None if ga is None else _ptr(ga))
+    if with_abs:
+        return gc, gq, gr, ga
     return gc, gq, gr
 
 

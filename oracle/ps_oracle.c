@@ -293,7 +293,17 @@ typedef struct {
     double PX, PY, den;
     double sX, sY;    /* radius on the side of P_X, P_Y (Eq. 7-8; Eq. 5 scales) */
     int branchX;      /* 1 if w came from the X side (w_X < w_Y) */
+    /* FP32 rounding model (conditioning flags only; set by pixel_candidates):  */
+    double kappa;     /* sum |d_i n_i| / |d . n|: condition number of Eq. 4's denominator */
+    double eps_t;     /* size of an FP32 rounding effect on t                            */
+    double eps_m;     /* size of an FP32 rounding effect on the active margin            */
 } cand;
+
+/* A composited pair whose Eq. 4 denominator is this ill-conditioned (the ray
+   within about half a degree of the plane) carries an FP32 relative error of
+   about eta * kappa into its gradient (t, and the chain through 1 / (d . n)):
+   above 100 that passes a tenth of the 1e-3 gradient bar.                    */
+#define OR_KAPPA_GRAD 100.0
 
 static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
 
@@ -364,13 +374,24 @@ static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], cons
         if (!pcs[k].ok) continue;
         cand c;
         if (!eval_pair(&pcs[k], d, S->lambda, S->z_near, S->z_far, S->flags & OR_GAUSS, &c)) continue;
-        double eps = eta * (1.0 + fabs(c.t) + pcs[k].pcn);
+        /* FP32 rounding of Eq. 4: the denominator d . n loses kappa ulps to cancellation
+           at grazing incidence, so t carries a relative error of about eta kappa and the
+           margin P = t (d . v) - a the same times t |d . v| */
+        const double* n_ = pcs[k].nc;
+        c.kappa = ((fabs(d[0] * n_[0]) + fabs(d[1] * n_[1])) + fabs(n_[2])) / fabs(c.den);
+        double dv = (S->flags & OR_GAUSS)
+                        ? fmax(fabs(dot3(d, pcs[k].vxc)), fabs(dot3(d, pcs[k].vyc)))
+                        : fabs(dot3(d, c.branchX ? pcs[k].vxc : pcs[k].vyc));
+        c.eps_t = eta * (1.0 + fabs(c.t)) * c.kappa;
+        c.eps_m = eta * (1.0 + fabs(c.t) + pcs[k].pcn) + eta * fabs(c.t) * dv * (c.kappa - 1.0);
+        double eps = c.eps_m;
         if (S->flags & OR_GAUSS) {
             /* w moves by about w (|P_X| / sigma_X^2 + |P_Y| / sigma_Y^2) eps */
             double dw = c.w * (fabs(c.PX) / (c.sX * c.sX) + fabs(c.PY) / (c.sY * c.sY)) * eps;
             if (fabs(c.w - S->w_min) < dw) *near_filter = 1;
         } else if (fabs(c.m + delta) < eps) *near_filter = 1;
-        if (fabs(c.t - S->z_near) < eps || fabs(c.t - S->z_far) < eps) *near_filter = 1;
+        double et = fmax(eps, c.eps_t);
+        if (fabs(c.t - S->z_near) < et || fabs(c.t - S->z_far) < et) *near_filter = 1;
         if (!(c.w >= S->w_min)) continue;
         c.k = k;
         out[nc++] = c;     /* out holds K entries: one per plane at most */
@@ -384,17 +405,23 @@ static int pixel_candidates(const plane_cam* pcs, int K, const double d[3], cons
 /* Outputs per pixel: depth, normal (camera frame), alpha = sum T_j w_j,     */
 /* n_sel = number composited (<= M), n_cand = number of (plane) candidates   */
 /* with w >= w_min and t in range (the algorithmic pair count), and ill:     */
-/*   bit 0: FP32 rounding (a margin error of eta (1 + t + |p_c|)) could      */
-/*          move D or N by more than tol_d/2 or tol_n/2, or flip the filter, */
-/*          the depth order or the z range;                                  */
+/*   bit 0: FP32 rounding could move D or N by more than tol_d/2 or        */
+/*          tol_n/2, or flip the filter, the depth order or the z range.     */
+/*          The rounding model: a margin error of eta (1 + t + |p_c|) +     */
+/*          eta t |d . v| (kappa - 1) and a depth error of eta (1 + t) kappa, */
+/*          kappa = sum |d_i n_i| / |d . n| (the denominator of Eq. 4 loses  */
+/*          precision when the ray grazes the plane);                        */
 /*   bit 1: bit 0, or the min / sign branch of a weighted, partly            */
-/*          transparent entry is within eta of flipping (gradients only);    */
+/*          transparent entry is within its margin error of flipping, or a  */
+/*          composited entry has kappa > OR_KAPPA_GRAD (gradients only);     */
 /*   bit 2: of bit 0, the discontinuous part: the filter, the depth order or */
 /*          the z range could flip;                                          */
-/*   bit 3: of bit 1, the branch part (a min / sign branch could flip).      */
+/*   bit 3: of bit 1, the part that is not a smooth value error (a min /     */
+/*          sign branch could flip, or a composited entry grazes).           */
 /* sens (optional) [pixel][2]: the first-order size of those rounding        */
 /* effects on D and on the largest component of N, sum over the composited  */
-/* pairs of |dD/dm_j| eta_j (likewise N), from the adjoint of Eq. 11-13.     */
+/* pairs of |dD/dm_j| times the margin error (likewise N), from the adjoint  */
+/* of Eq. 11-13.                                                             */
 /* Rows [row0, row1) of every view are rendered; others are left untouched.  */
 void or_render(int K, int V, const double* center, const double* quat, const double* radii,
                const double* w2c, const double* intr, int H, int W,
@@ -438,7 +465,7 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
                     /* conditioning */
                     int flip = near_filter, bad_grad = 0;
                     for (int s = 0; s + 1 < nc && s < M; ++s) {
-                        double e = eta * (1.0 + fabs(cs[s + 1].t));
+                        double e = fmax(eta * (1.0 + fabs(cs[s + 1].t)), fmax(cs[s].eps_t, cs[s + 1].eps_t));
                         if (cs[s + 1].t - cs[s].t < e) flip = 1;
                     }
                     int bad_val = flip;
@@ -448,7 +475,7 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
                     for (int s = ns - 1; s >= 0; --s) {
                         const plane_cam* p = &pcs[cs[s].k];
                         double w = cs[s].w, t = cs[s].t, m = cs[s].m;
-                        double e = eta * (1.0 + fabs(t) + p->pcn);
+                        double e = cs[s].eps_m;
                         double slope;
                         if (gauss)                                  /* |dw/dP| summed over both axes */
                             slope = w * (fabs(cs[s].PX) / (cs[s].sX * cs[s].sX) +
@@ -461,6 +488,7 @@ void or_render(int K, int V, const double* center, const double* quat, const dou
                         double gD = Tj[s] * (t - Ab);
                         sD += fabs(gD) * slope * e;
                         for (int c = 0; c < 3; ++c) sN[c] += fabs(Tj[s] * (p->nc[c] - Bb[c])) * slope * e;
+                        if (Tj[s] > 0.0 && cs[s].kappa > OR_KAPPA_GRAD) bad_grad = 1;
                         if (gauss) {
                             /* the side (sigma) choice of P_X or P_Y flips near 0 */
                             if (Tj[s] > 0.0 && (fabs(cs[s].PX) < e || fabs(cs[s].PY) < e)) bad_grad = 1;
@@ -543,11 +571,14 @@ double or_loss(int V, int H, int W, const double* depth, const double* normal,
 /*   dD/dw_j = T_j (t_j - A_{j+1}),  dD/dt_j = T_j w_j,  dN/dn_j = T_j w_j   */
 /* (no division by 1 - w), and chained through Eq. 9, 7-8, 6, 4 and 2-3 to   */
 /* the world parameters.  The clamp min(1, .) has derivative 0 at m >= 0.   */
+/* g_abs (optional, [K][11]): per plane and parameter, the sum over pixels of the   */
+/* absolute per-pixel contributions; its ratio to |g| measures how much the sum    */
+/* cancels, i.e. how far rounding of the parts can move the total.                 */
 void or_backward(int K, int V, const double* center, const double* quat, const double* radii,
                  const double* w2c, const double* intr, int H, int W,
                  double lambda, double w_min, double z_near, double z_far, int M, int flags,
                  const double* dLdD, const double* dLdN,
-                 double* g_center, double* g_quat, double* g_radii)
+                 double* g_center, double* g_quat, double* g_radii, double* g_abs)
 {
     or_set S = {lambda, w_min, z_near, z_far, M, flags};
     const int single_radii = flags & OR_SINGLE, gauss = flags & OR_GAUSS;
@@ -560,6 +591,7 @@ void or_backward(int K, int V, const double* center, const double* quat, const d
     nthreads = omp_get_max_threads();
 #endif
     double* acc = (double*)calloc((size_t)nthreads * 11 * (size_t)K, sizeof(double));
+    double* acc_abs = g_abs ? (double*)calloc((size_t)nthreads * 11 * (size_t)K, sizeof(double)) : NULL;
     /* per-view camera-frame gradient accumulators, chained to world per view */
     for (int v = 0; v < V; ++v) {
         const double* Rt = w2c + 12 * v;
@@ -671,6 +703,12 @@ void or_backward(int K, int V, const double* center, const double* quat, const d
                         for (int q = 0; q < 3; ++q) o[q] += gp[q];
                         for (int q = 0; q < 4; ++q) o[3 + q] += gq[q];
                         for (int q = 0; q < 4; ++q) o[7 + q] += gr[q];
+                        if (acc_abs) {
+                            double* oa = acc_abs + (size_t)tid * 11 * K + 11 * (size_t)c->k;
+                            for (int q = 0; q < 3; ++q) oa[q] += fabs(gp[q]);
+                            for (int q = 0; q < 4; ++q) oa[3 + q] += fabs(gq[q]);
+                            for (int q = 0; q < 4; ++q) oa[7 + q] += fabs(gr[q]);
+                        }
                     }
                 }
             }
@@ -685,6 +723,12 @@ void or_backward(int K, int V, const double* center, const double* quat, const d
             for (int q = 0; q < 4; ++q) g_quat[4 * k + q] += my[11 * k + 3 + q];
             for (int q = 0; q < 4; ++q) g_radii[4 * k + q] += my[11 * k + 7 + q];
         }
+    }
+    if (acc_abs) {
+        memset(g_abs, 0, sizeof(double) * 11 * (size_t)K);
+        for (int tid = 0; tid < nthreads; ++tid)
+            for (size_t e = 0; e < 11 * (size_t)K; ++e) g_abs[e] += acc_abs[(size_t)tid * 11 * K + e];
+        free(acc_abs);
     }
     free(acc);
     free(pcs);

@@ -581,3 +581,41 @@ def test_adam_matches_torch():
     p2 = np.full(4, 1e-3)
     O.adam(p2, np.ones(4), np.zeros(4), np.zeros(4), 1, clamp_min=1e-3)
     assert np.all(p2 == 1e-3)
+
+
+def test_grazing_incidence_flags_gradient_pixels():
+    # Eq. 4 divides by d . n; where a pixel ray nearly lies in a composited plane the
+    # FP32 evaluation loses about log2(kappa) bits, kappa = sum |d_i n_i| / |d . n|.
+    # The oracle marks those pixels (kappa > 100) as not comparable for gradients
+    # (flag bit 3).  Here a plane is tilted 0.002 rad out of the pixel ray of one
+    # column and centred where that ray meets it at 5 m; kappa is computed in the
+    # test from the plane equation alone.
+    lam = 50.0
+    H, W, f = 48, 64, 50.0
+    i0 = 17
+    d0 = np.array([(i0 + 0.5 - W / 2.0) / f, 0.0, 1.0])
+    u = d0 / np.linalg.norm(d0)
+    n = np.array([u[2], 0.0, -u[0]]) + 0.002 * u
+    n /= np.linalg.norm(n)
+    vy = np.array([0.0, 1.0, 0.0])
+    vx = np.cross(vy, n)
+    quat = S.quat_from_frame(vx, vy, n)
+    t0 = 5.0
+    center = t0 * d0
+    w2c, intr = ident_cams(1, H, W, f)
+    o = O.render(*plane(center, quat, [5.0, 5.0, 5.0, 5.0]), w2c, intr, H, W, lam)
+    grazing = other = 0
+    for j in range(H):
+        for i in range(W):
+            if not o["alpha"][0, j, i] > 0:
+                continue
+            dx, dy = pix_ray(i, j, f, W / 2.0, H / 2.0)
+            den = dx * n[0] + dy * n[1] + n[2]
+            kappa = (abs(dx * n[0]) + abs(dy * n[1]) + abs(n[2])) / abs(den)
+            if kappa > 100.0:
+                grazing += 1
+                assert o["ill"][0, j, i] & 8, (i, j, kappa)
+                assert o["depth"][0, j, i] / o["alpha"][0, j, i] == pytest.approx(t0, rel=1e-9)
+            else:
+                other += 1
+    assert grazing >= H // 2 and other >= 1
