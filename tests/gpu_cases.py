@@ -85,9 +85,27 @@ def oracle_bins(planes, cams, delta, tile, gaussian=False):
     return rect, key32, ptr, ent, ekey
 
 
-def oracle_render(planes, cams, lam, M=30, rows=None, gaussian=False):
+def oracle_render(planes, cams, lam, M=30, rows=None, gaussian=False, single_radii=False):
     return O.render(planes.center, planes.quat, planes.radii, cams.w2c, cams.intr, cams.H, cams.W,
-                    f32(lam), M=M, z_near=Z_NEAR32, z_far=Z_FAR32, rows=rows, gaussian=gaussian)
+                    f32(lam), M=M, z_near=Z_NEAR32, z_far=Z_FAR32, rows=rows, gaussian=gaussian,
+                    single_radii=single_radii)
+
+
+def loss_mask(o, gt_depth, gt_normal, tol_d=1e-4, tol_n=1e-5):
+    """Pixels to leave unsupervised on both sides (ground-truth depth set to 0) when
+    the GPU computes the Eq. 14 gradient from its own FP32 render (the fused kernel):
+    pixels where FP32 rounding could flip a min / sign branch, the filter, the depth
+    order or the z range (oracle flag bits 2 and 3), and pixels where the sign of
+    D - D*, of a component of N - N* or of 1 - N.N* could differ between the FP32
+    render and the oracle's, because the oracle's value lies within twice the bar the
+    render is held to (max(tol, 2 x the oracle's rounding-sensitivity estimate))."""
+    bd = np.maximum(tol_d, 2.0 * o["sens_d"])
+    bn = np.maximum(tol_n, 2.0 * o["sens_n"])
+    m = (o["ill"] & 12) != 0
+    m |= np.abs(o["depth"] - gt_depth) <= 2.0 * bd
+    m |= (np.abs(o["normal"] - gt_normal) <= 2.0 * bn[..., None]).any(axis=-1)
+    m |= np.abs(1.0 - (o["normal"] * gt_normal).sum(axis=-1)) <= 6.0 * bn
+    return m
 
 
 def compare_maps(g, o, rows=None, tol_d=1e-4, tol_n=1e-5):

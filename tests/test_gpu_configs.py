@@ -154,17 +154,17 @@ def test_stress_gradients_against_oracle_and_finite_differences(torch, stress):
     rect, _, _ = O.bin_records(init.center, init.quat, init.radii, cc.w2c, cc.intr, CH, CW, CW, CH,
                                O.filter_margin(lam32), z_near=Z_NEAR32)
     ok = rect[..., 2] >= rect[..., 0]
-    # upstream gradient on the crops, zero where FP32 noise could flip a min / sign branch or the
-    # depth order: with 10,000 planes seeded through the same surfaces, depths ten metres out and
-    # many near-ties, the noise model is taken at eta = 1e-5 (ten times the small-scene value)
+    # upstream gradient on the crops, zero where FP32 rounding could flip a min / sign branch,
+    # the filter, the depth order or the z range (the oracle's flag bits 2 and 3 at its
+    # standard noise model, eta = 1e-6: the same mask as every other gradient test)
     rng = np.random.default_rng(9)
     gD_c = rng.normal(size=(len(CROPS), CH, CW))
     gN_c = rng.normal(size=(len(CROPS), CH, CW, 3))
     for i in range(len(CROPS)):
         idx = _subset(ok, i)
         o = O.render(init.center[idx], init.quat[idx], init.radii[idx], cc.w2c[i:i + 1], cc.intr[i:i + 1],
-                     CH, CW, lam32, z_near=Z_NEAR32, eta=1e-5)
-        ill = (o["ill"][0] & 2) != 0
+                     CH, CW, lam32, z_near=Z_NEAR32)
+        ill = (o["ill"][0] & 12) != 0
         gD_c[i][ill] = 0
         gN_c[i][ill] = 0
         assert o["n_sel"][0].max() >= 3          # overlapping planes in every crop
@@ -183,10 +183,23 @@ def test_stress_gradients_against_oracle_and_finite_differences(torch, stress):
     from paper_2412_03451_gb300 import splat as SP
     gc, gq, gr = (t.double().cpu().numpy() for t in SP.flat_views(g, K))
     # every plane's gradient against the oracle's adjoint (the crops as sixteen small views)
-    oc, oq, orr = O.backward(init.center, init.quat, init.radii, cc.w2c, cc.intr, CH, CW, lam32,
-                             gD_c, gN_c, z_near=Z_NEAR32)
-    for name, a, b in (("center", gc, oc), ("quat", gq, oq), ("radii", gr, orr)):
-        nbad, worst = grad_errors(a, b)
+    oc, oq, orr, oabs = O.backward(init.center, init.quat, init.radii, cc.w2c, cc.intr, CH, CW, lam32,
+                                   gD_c, gN_c, z_near=Z_NEAR32, with_abs=True)
+    res = {name: grad_errors(a, b) for name, a, b in (("center", gc, oc), ("quat", gq, oq),
+                                                       ("radii", gr, orr))}
+    worst = []
+    for name, a, b, cols in (("center", gc, oc, slice(0, 3)), ("quat", gq, oq, slice(3, 7)),
+                             ("radii", gr, orr, slice(7, 11))):
+        n_or = np.linalg.norm(b, axis=1)
+        err = np.linalg.norm(a - b, axis=1)
+        bound = 1e-3 * n_or + 1e-6 * n_or.max()
+        canc = np.linalg.norm(oabs[:, cols], axis=1) / np.maximum(n_or, 1e-300)
+        for k in np.argsort(-(err / np.maximum(bound, 1e-300)))[:3]:
+            worst.append(dict(group=name, plane=int(k), ratio=float(err[k] / bound[k]), norm=float(n_or[k]),
+                              cancel=float(canc[k]), cancel_p99=float(np.percentile(canc[n_or > 0], 99))))
+    record("stress_bwd_detail", worst=worst)
+    record("stress_bwd_vs_oracle", **{k: list(v) for k, v in res.items()})
+    for name, (nbad, worst) in res.items():
         assert nbad == 0, (name, nbad, worst)
     # 64 planes: central differences of the oracle's crop renders with h = 1e-5.  The render
     # is discontinuous where the front-most planes swap (normals jump at occlusion crossings),
@@ -246,7 +259,8 @@ def test_stress_gradients_against_oracle_and_finite_differences(torch, stress):
                 fd[n, col] = (J(k, *plus) - J(k, *minus)) / (2 * h)
                 col += 1
     # per-plane bar: the oracle's adjoint to FD truncation and rounding, the GPU's to its own bar
-    for name, a, rel in (("oracle", an, 1e-4), ("gpu", gpu, 2e-3)):
+    for name, a, rel in (("oracle", an, 1e-4), ("gpu", gpu, 1e-3)):
         err = np.linalg.norm(a - fd, axis=1)
         bound = rel * np.linalg.norm(fd, axis=1) + 1e-5 * np.linalg.norm(fd, axis=1).max()
+        record("stress_vs_fd", arm=name, worst=float((err / np.maximum(bound, 1e-30)).max()))
         assert (err <= bound).all(), (name, np.sort(err / np.maximum(bound, 1e-30))[-5:])

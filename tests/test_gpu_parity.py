@@ -310,6 +310,46 @@ def test_backward_dense_overlaps():
         assert nbad == 0, (k, nbad, worst)
 
 
+@pytest.mark.parametrize("scene", ["tiny", "dense"])
+def test_single_radii_forward_backward(scene):
+    # the "w/o double radii" variant of Sec. 4.3: r^x+ serves both X sides and r^y+
+    # both Y sides; the one-sided radii of the inputs differ, so reading the wrong
+    # side or sending gradient to r^x- / r^y- would show
+    from paper_2412_03451_gb300 import binding as B
+    if scene == "tiny":
+        room, p = tiny_init()
+        cams = room.cams
+    else:
+        p = S.random_planes_in_view(9, 60, depth_range=(1.0, 3.0), half=(0.2, 0.8), fov=0.5)
+        cams = S.identity_cameras(2, 40, 56, 30.0, seed=5, jitter=0.05)
+    assert np.abs(p.radii[:, 0] - p.radii[:, 1]).max() > 0.05
+    lam = 20.0
+    o = oracle_render(p, cams, lam, single_radii=True)
+    rng = np.random.default_rng(11)
+    dD = rng.normal(size=o["depth"].shape)
+    dN = rng.normal(size=o["normal"].shape)
+    ill = (o["ill"] & 12) != 0
+    dD[ill] = 0
+    dN[ill] = 0
+    dD, dN = dD.astype(np.float32), dN.astype(np.float32)
+    g = gpu_run(p, cams, lam, flags=B.PS_SINGLE_RADII, dLdD=dD, dLdN=dN, backward=True)
+    assert g["status"] == 0
+    c = compare_maps(g, o)
+    report("single_radii", scene=scene, **c)
+    assert c["n_bad_d"] == 0 and c["n_bad_n"] == 0, c
+    assert c["n_bad_sens_d"] == 0 and c["n_bad_sens_n"] == 0, c
+    assert c["n_pix"] - c["n_ill"] >= 0.5 * c["n_pix"], c
+    # the double-radii render differs: the variant is really exercised
+    o2 = oracle_render(p, cams, lam)
+    assert np.abs(o2["depth"] - o["depth"]).max() > 1e-2
+    gc, gq, gr = O.backward(p.center, p.quat, p.radii, cams.w2c, cams.intr, cams.H, cams.W,
+                            f32(lam), dD, dN, z_near=f32(0.01), single_radii=True)
+    for k, ref in (("g_center", gc), ("g_quat", gq), ("g_radii", gr)):
+        nbad, worst = grad_errors(g[k], ref)
+        assert nbad == 0, (scene, k, nbad, worst)
+    assert (g["g_radii"][:, [1, 3]] == 0).all()
+
+
 # ---------------------------------------------------------------------------
 # Paper-scale room (640x480, 3000 planes, 8 views): sampled rows.
 
@@ -404,14 +444,23 @@ def test_fused_equals_separate_kernels(lam, tile):
     report("fused_vs_split", lam=lam, tile=tile)
 
 
-def test_fused_gradient_against_oracle():
-    from gpu_cases import gpu_fused_vs_split
+@pytest.mark.parametrize("lam", [20.0 / np.e, 20.0])
+def test_fused_gradient_against_oracle(lam):
+    # the fused kernel takes the Eq. 14 gradient of its own FP32 render; pixels where a
+    # branch or a sign of the loss could come out differently in FP32 are left
+    # unsupervised on both sides (ground-truth depth 0), every other plane gradient is
+    # held to the same bar as the separate backward, with no failure allowed
+    from gpu_cases import gpu_fused_vs_split, loss_mask
     room, init = tiny_init(4)
-    lam = 20.0
     D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, room.cams.w2c,
                         room.cams.intr, room.cams.H, room.cams.W)
-    sp, fu, status = gpu_fused_vs_split(init, room.cams, lam, D, N)
+    D = D.astype(np.float32).astype(np.float64)
+    N = N.astype(np.float32).astype(np.float64)
     o = oracle_render(init, room.cams, lam)
+    drop = loss_mask(o, D, N)
+    D[drop] = 0.0
+    sp, fu, status = gpu_fused_vs_split(init, room.cams, lam, D, N)
+    assert status == 0
     tot, dD, dN, sums = O.loss(o["depth"], o["normal"], D, N)
     gc, gq, gr = O.backward(init.center, init.quat, init.radii, room.cams.w2c, room.cams.intr,
                             room.cams.H, room.cams.W, f32(lam), dD, dN, z_near=f32(0.01))
@@ -420,12 +469,20 @@ def test_fused_gradient_against_oracle():
     res = {k: grad_errors(g[a:b].reshape(K, -1), ref) for k, (a, b), ref in
            (("g_center", (0, 3 * K), gc), ("g_quat", (3 * K, 7 * K), gq),
             ("g_radii", (7 * K, 11 * K), gr))}
+    # the loss gradients of the render: identical signs everywhere the loss is taken
+    V, H, W = room.cams.V, room.cams.H, room.cams.W
+    assert np.array_equal(fu["dLdD"].reshape(V, H, W), dD.astype(np.float32))
+    assert np.abs(fu["dLdN"].reshape(V, H, W, 3) - dN).max() <= 1e-5
+    assert np.array_equal(fu["sums"][:, 3], sums[:, 3])
     loss_gpu = float((fu["sums"][:, :3] * np.array([5.0, 5.0, 1.0])).sum())
-    report("fused_vs_oracle", loss_rel=abs(loss_gpu - tot) / tot, **res)
+    report("fused_vs_oracle", lam=lam, dropped=float(drop.mean()), loss_rel=abs(loss_gpu - tot) / tot,
+           **res)
     assert abs(loss_gpu - tot) <= 1e-4 * tot
-    # unmasked upstream: a few ill-conditioned pixels may move a plane's gradient
-    nbad = sum(v[0] for v in res.values())
-    assert nbad <= 0.05 * 3 * K, res
+    # the mask keeps most of the image: at these lambdas the oracle's rounding-sensitivity
+    # bars are wide on the many partly transparent pixels of a perturbed start
+    assert drop.mean() < 0.25
+    for k, (nbad, worst) in res.items():
+        assert nbad == 0, (k, nbad, worst)
 
 
 # ---------------------------------------------------------------------------
