@@ -86,7 +86,11 @@ class Renderer:
         self.fwd_ws = torch.zeros((B.ps_fwd_workspace_bytes(f) + 255) // 256 * 64,
                                   dtype=torch.float32, device=dev)
         self._batches = None
+        self._views_tensor = self.views_dev
         self.settings = None
+        # bumped whenever the records / tile lists or the camera descriptors change, so a
+        # holder of an earlier render (PlaneSplatFunction) can tell that they are stale
+        self.generation = 0
 
     # -- buffers ---------------------------------------------------------------
     def _alloc_lists(self, capacity: int):
@@ -105,6 +109,8 @@ class Renderer:
         raw = np.frombuffer(bytes(self._views_host), dtype=np.uint8).copy()
         self.views_dev.copy_(torch.from_numpy(raw))
         self.frame.views = self.views_dev.data_ptr()
+        self._views_tensor = self.views_dev
+        self.generation += 1
 
     def preplan(self, w2c_batches, intr_batches, gt_off_batches=None):
         """Plans several camera batches of this renderer's shape once and keeps
@@ -123,6 +129,12 @@ class Renderer:
 
     def select(self, i: int):
         self.frame.views = self._batches[i].data_ptr()
+        self._views_tensor = self._batches[i]
+        self.generation += 1
+
+    def views_snapshot(self) -> torch.Tensor:
+        """Device copy of the current view descriptors (V x 128 bytes)."""
+        return self._views_tensor.clone()
 
     def make_settings(self, lam, flags=None, d_state=None):
         fl = self.flags if flags is None else flags
@@ -145,6 +157,7 @@ class Renderer:
 
     # -- the path ----------------------------------------------------------------
     def project_bin(self, flat: torch.Tensor, lam: float, flags=None, d_state=None):
+        self.generation += 1
         s = self.make_settings(lam, flags, d_state)
         pl = self.planes_struct(flat)
         B.ps_project_cull(pl, self.frame, s, self.rec, self.rect, self.key, self.status)
@@ -217,23 +230,53 @@ class Renderer:
 
 
 class PlaneSplatFunction(torch.autograd.Function):
-    """(center, quat, radii) -> (depth, normal) through libps; the backward is
-    the hand-written adjoint kernel ps_splat_bwd."""
+    """(planes) -> (depth, normal) through libps, as a torch.autograd.Function
+    whose backward is the hand-written adjoint kernel ps_splat_bwd.
+
+    apply(flat, renderer, lam, flags=None): flat is the [11 P] float32 parameter
+    buffer of the renderer's scenes ([center P*3 | quat P*4 | radii P*4]); lam the
+    Eq. 10 value.  The forward grows the renderer's tile-list capacity when needed
+    (one host synchronisation), projects, bins and splats the renderer's current
+    views, and returns copies of depth [n_pixels] and normal [n_pixels, 3].
+
+    The backward recomputes every pixel's compositing state from the tile lists;
+    nothing per pixel is kept.  If the renderer has projected, binned or switched
+    cameras since this forward (another render before .backward()), the backward
+    first rebuilds this forward's records and tile lists from the saved planes,
+    camera descriptors and lambda: binning is deterministic, so they are the
+    forward's own lists bit for bit.  The renderer's buffers then hold this
+    rebuilt state and its generation moves on, so later holders rebuild theirs."""
 
     @staticmethod
-    def forward(ctx, flat, renderer: Renderer, lam: float):
-        depth, normal = renderer.forward(flat, lam)
+    def forward(ctx, flat, renderer: Renderer, lam: float, flags=None):
+        if renderer.ensure_capacity(flat, lam, flags):
+            renderer.project_bin(flat, lam, flags)      # the lists of the grown buffers
+        renderer.splat_forward(alpha=False)
         ctx.renderer = renderer
+        ctx.lam, ctx.flags = lam, flags
+        ctx.generation = renderer.generation
+        ctx.views = renderer.views_snapshot()
         ctx.save_for_backward(flat)
-        return depth.clone(), normal.clone()
+        return renderer.depth.clone(), renderer.normal.clone()
 
     @staticmethod
     def backward(ctx, gD, gN):
         (flat,) = ctx.saved_tensors
         r = ctx.renderer
         g = torch.zeros_like(flat)
-        r.backward(flat, g, gD.contiguous(), gN.contiguous())
-        return g, None, None
+        if r.generation == ctx.generation:
+            r.backward(flat, g, gD.contiguous(), gN.contiguous())
+            return g, None, None, None
+        cur_views, cur_tensor = r.frame.views, r._views_tensor
+        try:
+            r.frame.views = ctx.views.data_ptr()
+            r._views_tensor = ctx.views
+            r.project_bin(flat, ctx.lam, ctx.flags)
+            r.backward(flat, g, gD.contiguous(), gN.contiguous())
+        finally:
+            r.frame.views, r._views_tensor = cur_views, cur_tensor
+            r.generation += 1
+        return g, None, None, None
 
 
 class Fitter:
