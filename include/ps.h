@@ -271,7 +271,9 @@ ps_status ps_splat_bwd(const ps_planes* planes, const ps_frame* frame,
    return PS_ERR_ARG before anything is launched.  No cudaMalloc, cudaFree or
    other allocating call is made.  The first call on a device looks up the
    array's device address (cudaGetSymbolAddress) with that device current and
-   caches it; make that first call before any stream capture.  Every call
+   caches it with the current CUDA context; a call under another context (after
+   cudaDeviceReset, or with a context the caller made current) looks it up again.
+   Make the first call in a context before any stream capture.  Every call
    clears the part of the array it uses, but all calls share the one array:
    calls that may overlap on the GPU (different streams, or different host
    threads on the same device) race and must be serialised by the caller. */
@@ -325,6 +327,23 @@ ps_status ps_count_pairs(const ps_frame* frame, const ps_settings* settings, con
    lambda, delta and Adam bias corrections. */
 ps_status ps_step_advance(ps_step_state* d_state, const ps_step_state* d_sched, int n_sched,
                           int* d_iter, ps_stream stream);
+
+/* Scene initialisation (Sec. 3.1): every plane starts with its radii at half
+   the distance from its centre to the nearest other centre.  For points (device
+   f32 [n][3]): dist[i] (device f32 [n], or NULL) = the Euclidean distance from
+   points[i] to the nearest other point, +inf if n == 1, exact up to FP32 rounding
+   of the distances (the minimum over every other point); radii (device f32
+   [n][4], 16-byte aligned, or NULL) = all four radii of plane i set to
+   clamp(scale x dist[i], r_lo, r_hi) (scale 0.5 in the paper).  Points are
+   counted into a hashed uniform grid (cell edge about the cube root of the
+   bounding box's volume per point) and each query searches shells of cells around
+   its own until the nearest point found lies within the searched radius.  ws
+   (device, 16-byte aligned, >= ps_nn_workspace_bytes(n)) is scratch.  Asynchronous
+   on the stream; five launches.  PS_ERR_ARG for n < 0, NULL points or ws, both
+   outputs NULL, scale < 0, r_lo > r_hi or a small workspace. */
+size_t ps_nn_workspace_bytes(int n);
+ps_status ps_nn_distance(const float* points, int n, float scale, float r_lo, float r_hi,
+                         float* dist, float* radii, void* ws, size_t ws_bytes, ps_stream stream);
 
 /* ---- Host-side schedule of the optimisation.  Plain host functions: no device
    work, no CUDA call; usable without a GPU. ---- */

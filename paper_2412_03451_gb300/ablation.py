@@ -33,6 +33,7 @@ from . import batch as BT
 from . import evaluate as EV
 from . import binding as B
 from . import scenes as S
+from . import starts as ST
 
 VARIANTS = ("plain", "mono", "sphere", "single_radii", "split", "split_low", "gaussian")
 
@@ -46,15 +47,15 @@ def _gt_maps(ss: BT.SceneSet, i: int):
     return d, n
 
 
-def make_inits(name: str, rooms, ss_ref: BT.SceneSet, planes: int, seed0: int):
+def make_inits(name: str, rooms, ss_ref: BT.SceneSet, planes: int, seed0: int, device="cuda"):
     out = []
     for i, room in enumerate(rooms):
         seed = seed0 + 100 + i
         if name == "plain":
-            out.append(S.surface_init_nn(room, planes, seed))
+            out.append(ST.surface_start(room, planes, seed, device))
         elif name in ("mono", "single_radii", "split", "split_low", "gaussian"):
             d, n = _gt_maps(ss_ref, i)
-            out.append(S.mono_init(room, d, n, planes, seed))
+            out.append(ST.mono_start(room, d, n, planes, seed, device))
         elif name == "sphere":
             out.append(S.sphere_init(room, planes, seed))
         else:
@@ -65,13 +66,13 @@ def make_inits(name: str, rooms, ss_ref: BT.SceneSet, planes: int, seed0: int):
 def run(n_rooms: int = 4, planes: int = 2000, iters: int = 5000, seed0: int = 7000,
         variants=VARIANTS, device="cuda", tile=(16, 16), evaluate: bool = True) -> dict:
     rooms = [S.large_room(seed0 + i, n_rect=2000, n_views=64) for i in range(n_rooms)]
-    ss_ref = BT.SceneSet(rooms, [S.surface_init_nn(r, planes, seed0 + 100 + i)
+    ss_ref = BT.SceneSet(rooms, [ST.surface_start(r, planes, seed0 + 100 + i, device)
                                  for i, r in enumerate(rooms)], device=device, tile=tile)
     out = {"rooms": n_rooms, "planes": planes, "iteration_cap": iters,
            "what": "per variant: rooms fitted one by one; GPU seconds, iterations to mean depth "
                    "error <= 2 cm (None: not reached), error at the end"}
     for name in variants:
-        inits = make_inits(name, rooms, ss_ref, planes, seed0)
+        inits = make_inits(name, rooms, ss_ref, planes, seed0, device)
         flags = {"single_radii": B.PS_SINGLE_RADII, "gaussian": B.PS_GAUSSIAN}.get(name, 0)
         ss = BT.SceneSet(rooms, inits, device=device, tile=tile, flags=flags)
         split = 1000 if name in ("split", "split_low") else 0

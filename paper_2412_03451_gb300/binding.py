@@ -30,7 +30,7 @@ EXPORTS = ("ps_plan_views", "ps_project_cull", "ps_bin_workspace_bytes", "ps_bin
            "ps_seed_colsum", "ps_seed_pool", "ps_seed_pool_bwd", "ps_seed_loss", "ps_cast_bf16",
            "ps_radii_grad_accum", "ps_split_planes", "ps_merge_planes", "ps_status_string",
            "ps_version", "ps_lambda_schedule", "ps_filter_margin", "ps_gauss_extent",
-           "ps_step_schedule")
+           "ps_step_schedule", "ps_nn_workspace_bytes", "ps_nn_distance")
 
 
 class PsSettings(ctypes.Structure):
@@ -127,6 +127,8 @@ def load():
             "ps_filter_margin": ([D, D], D),
             "ps_gauss_extent": ([D], D),
             "ps_step_schedule": ([I, I, I, F, F, D, P], I),
+            "ps_nn_workspace_bytes": ([I], SZ),
+            "ps_nn_distance": ([P, I, F, F, F, P, P, P, SZ, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -348,6 +350,21 @@ def ps_merge_planes(params, n_planes, scene_center, max_angle_deg, max_offset, g
     _check(load().ps_merge_planes(_ptr(params), int(n_planes), c, float(max_angle_deg),
                                   float(max_offset), _ptr(group_of), _ptr(rep_of_group),
                                   _ptr(d_groups), _stream(stream)), "ps_merge_planes")
+
+
+def ps_nn_distance(points, dist=None, radii=None, scale=0.5, r_lo=0.0, r_hi=float("inf"), ws=None,
+                   stream=None):
+    """Nearest-other-point distances of points [n, 3] (device f32) into dist [n]
+    and/or the Sec. 3.1 initial radii clamp(scale * dist, r_lo, r_hi) into radii
+    [n, 4]; scratch is allocated here when ws is None."""
+    import torch
+    n = int(points.shape[0])
+    need = int(load().ps_nn_workspace_bytes(n))
+    if ws is None:
+        ws = torch.empty((need + 15) // 16 * 4, dtype=torch.float32, device=points.device)
+    _check(load().ps_nn_distance(_ptr(points), n, float(scale), float(r_lo), float(r_hi), _ptr(dist),
+                                 _ptr(radii), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "ps_nn_distance")
 
 
 def ps_wait_selftest(status, polls: int, stream=None):

@@ -446,9 +446,9 @@ def sphere_init(room: Room, n: int, seed: int, radius: float = 0.05) -> Planes:
     return Planes(centers.astype(np.float32), quat.astype(np.float32), radii.astype(np.float32))
 
 
-def mono_init(room: Room, depth: np.ndarray, normal: np.ndarray, n: int, seed: int,
-              scale_sigma: float = 0.03, depth_sigma: float = 0.01, normal_sigma_deg: float = 8.0,
-              radius_scale: float = 0.5) -> Planes:
+def mono_points(room: Room, depth: np.ndarray, normal: np.ndarray, n: int, seed: int,
+                scale_sigma: float = 0.03, depth_sigma: float = 0.01,
+                normal_sigma_deg: float = 8.0) -> Planes:
     """Stand-in for the monocular-depth initialisation of Sec. 3.1: the
     ground-truth depth and camera-frame normal maps [V, H, W] / [V, H, W, 3] are
     degraded like a monocular prediction (a per-view depth scale error
@@ -456,8 +456,9 @@ def mono_init(room: Room, depth: np.ndarray, normal: np.ndarray, n: int, seed: i
     tilted by N(0, normal_sigma_deg) degrees about a random axis), n random
     valid pixels are back-projected to plane centres, each plane's normal is the
     degraded normal (so its rotation comes from the coarse geometry), its
-    in-plane rotation is random, and every radius is radius_scale x the distance
-    to the nearest other centre."""
+    in-plane rotation is random.  The radii are left at 0: they follow from the
+    centres (mono_init here on the host, the library's nearest-neighbour kernel in
+    the package)."""
     rng = np.random.default_rng(seed)
     cams = room.cams
     V = depth.shape[0]
@@ -484,11 +485,20 @@ def mono_init(room: Room, depth: np.ndarray, normal: np.ndarray, n: int, seed: i
     vx /= np.linalg.norm(vx, axis=1, keepdims=True)
     vy = np.cross(nw, vx)
     quat = np.array([quat_from_frame(vx[k], vy[k], nw[k]) for k in range(n)])
-    from scipy.spatial import cKDTree
-    d, _ = cKDTree(centers).query(centers, k=2)
-    r = np.clip(radius_scale * d[:, 1], 0.02, 2.0)
-    radii = np.repeat(r[:, None], 4, axis=1)
+    radii = np.zeros((n, 4))
     return Planes(centers.astype(np.float32), quat.astype(np.float32), radii.astype(np.float32))
+
+
+def mono_init(room: Room, depth: np.ndarray, normal: np.ndarray, n: int, seed: int,
+              radius_scale: float = 0.5, **kw) -> Planes:
+    """mono_points with every radius radius_scale x the distance to the nearest
+    other centre (clipped to [0.02, 2] m), computed on the host."""
+    p = mono_points(room, depth, normal, n, seed, **kw)
+    from scipy.spatial import cKDTree
+    c = p.center.astype(np.float64)
+    d, _ = cKDTree(c).query(c, k=2)
+    p.radii[:] = np.clip(radius_scale * d[:, 1], 0.02, 2.0)[:, None].astype(np.float32)
+    return p
 
 
 def batch_rooms(n_rooms: int, seed0: int = 1000, planes=(200, 3000), views=(16, 96),
