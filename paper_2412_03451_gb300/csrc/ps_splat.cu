@@ -34,6 +34,8 @@
 // into the world parameters.
 #include <mutex>
 
+#include <cuda.h>
+
 #include "ps_internal.cuh"
 
 using namespace ps;
@@ -90,7 +92,7 @@ struct SplatArgs {
 
 // A warp's staging area: one list chunk.
 struct WarpStage {
-    float4 rec[32][4];
+    float4 rec[4][32];        // record float4 c of chunk entry e at rec[c][e] (no bank conflicts)
     int id[32];
     float key[33];            // entry keys x (1 - 1/4096); key[32]: the next chunk's first entry
 };
@@ -197,13 +199,12 @@ struct Sink {
 };
 
 template <int MODE>
-__device__ __forceinline__ void composite(Walk& s, Sink& k, const float4* __restrict__ rec,
-                                          float t, float w, int id, int M)
+__device__ __forceinline__ void composite(Walk& s, Sink& k, const float4& n, float t, float w, int id,
+                                          int M)
 {
     if constexpr (MODE != kFwd) k.stk[s.cnt * 32] = make_int2(id, __float_as_int(s.T));
     if constexpr (MODE != kBwd) {
         if (k.acc.first < 0) k.acc.first = id;
-        const float4 n = __ldg(&rec[(size_t)id * 4]);
         const float tw = s.T * w;
         k.acc.D = fmaf(tw, t, k.acc.D);
         k.acc.N0 = fmaf(tw, n.x, k.acc.N0);
@@ -230,7 +231,9 @@ __device__ __forceinline__ void flush(Walk& s, Sink& k, const float4* __restrict
         if (!(k0 < s.ovf)) break;
         const float w = s.bw[0];
         pend_pop(s);
-        composite<MODE>(s, k, rec, key_t(k0), w, key_id(k0), M);
+        float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (MODE != kBwd) n = __ldg(&rec[(size_t)key_id(k0) * 4]);
+        composite<MODE>(s, k, n, key_t(k0), w, key_id(k0), M);
     }
     if (final_ && s.nb == 0 && s.ovf == kNoKey) s.done = true;
 }
@@ -257,7 +260,7 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                 ws.key[lane] = __ldg(&a.key[i]) * kMargin;
                 if (ok) {
                     ws.id[lane] = id;
-                    ws.rec[lane][0] = n; ws.rec[lane][1] = vx; ws.rec[lane][2] = vy; ws.rec[lane][3] = rr;
+                    ws.rec[0][lane] = n; ws.rec[1][lane] = vx; ws.rec[2][lane] = vy; ws.rec[3][lane] = rr;
                 }
             } else {
                 ws.key[lane] = INFINITY;
@@ -274,19 +277,22 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
                 }
                 const int e = __ffs(m) - 1;
                 m &= m - 1;
+                // keys are sorted and entries that fail the region test cannot reach any
+                // pixel of the strip: the next surviving entry's key (or the next chunk's
+                // first key) bounds every later depth
+                const int en = m ? __ffs(m) - 1 : 32;
                 if (!s.done) {
                     PairEval pe;
                     const int id = ws.id[e];
-                    // keys are sorted: the next entry's key bounds every later depth
-                    const float bound = ws.key[e + 1];
-                    if (eval_pair(ws.rec[e][0], ws.rec[e][1], ws.rec[e][2], ws.rec[e][3], dx, dy,
-                                  a.c, pe)) {
+                    const float bound = ws.key[en];
+                    const float4 n = ws.rec[0][e];
+                    if (eval_pair(n, ws.rec[1][e], ws.rec[2][e], ws.rec[3][e], dx, dy, a.c, pe)) {
                         const CKey key = ckey(pe.t, id);
                         if (s.floor_ < key) {
                             // nothing pending and nothing later can come before it: composite
                             // at once (what inserting and flushing would do)
                             if (s.nb == 0 && pe.t < bound && key < s.ovf && !(s.cut < key))
-                                composite<MODE>(s, k, a.rec, pe.t, pe.w, id, a.M);
+                                composite<MODE>(s, k, n, pe.t, pe.w, id, a.M);
                             else
                                 pend_insert(s, key, pe.w, a.M);
                         }
@@ -917,7 +923,8 @@ cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool 
     if (e != cudaSuccess) return e;
     LaunchCache& c = cache[dev & 7];
     if (c.dev != dev || c.dyn != dyn) {
-        if (dyn > 48 * 1024) {
+        if (dyn > 0) {
+            // static + dynamic shared memory above 48 KB needs the opt-in
             e = cudaFuncSetAttribute(k_splat<TW, TH, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)dyn);
             if (e != cudaSuccess) return e;
@@ -1206,10 +1213,28 @@ constexpr size_t kNoAllocBytes = sizeof(float4) * 4 * (size_t)kNoAllocMaxRecords
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of g_noalloc_scratch per device.  In host code the symbol's
-// name is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// name is only a host-side stand-in, so the address is looked up with the
+// device current and cached together with the CUDA context it belongs to: after
+// cudaDeviceReset, or when the caller makes another context current, the
+// library's module is loaded again and the address is looked up again.
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[64] = {};
+CUcontext g_noalloc_ctx[64] = {};
+
+typedef CUresult (*CtxGetCurrent)(CUcontext*);
+
+CtxGetCurrent ctx_get_current()
+{
+    static CtxGetCurrent fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrent>(p);
+    }
+    return fn;
+}
 
 }  // namespace
 
@@ -1226,13 +1251,19 @@ extern "C" ps_status ps_splat_bwd_noalloc(const ps_planes* planes, const ps_fram
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
     if (dev < 0 || dev >= 64) return PS_ERR_ARG;
+    CtxGetCurrent get_ctx = ctx_get_current();
+    CUcontext ctx = nullptr;
+    if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS) return PS_ERR_CUDA;
     void* ws = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        if (!ctx || !g_noalloc_addr[dev] || g_noalloc_ctx[dev] != ctx) {
+            // (this also makes the device's primary context current if none was)
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PS_ERR_CUDA;
+            if (!ctx && (get_ctx(&ctx) != CUDA_SUCCESS || !ctx)) return PS_ERR_CUDA;
             g_noalloc_addr[dev] = p;
+            g_noalloc_ctx[dev] = ctx;
         }
         ws = g_noalloc_addr[dev];
     }
