@@ -170,12 +170,17 @@ def parse():
                     help="also fit up to this many iterations and report time to depth error <= 2 cm")
     ap.add_argument("--start-ite", type=int, default=0, help="iteration (lambda schedule) to start at")
     ap.add_argument("--no-graphs", action="store_true", help="time eager launches instead of graph replays")
+    ap.add_argument("--regimes", default="1000,2000,4000",
+                    help="iterations of a real fit of the same room at which stage times and the roofline "
+                         "are measured again (lambda 20, 54, 300); empty: none")
     ap.add_argument("--batched", type=int, default=32,
                     help="rooms in the batched-vs-plain time-to-2cm comparison (0: skip)")
     ap.add_argument("--batched-iters", type=int, default=5000)
     ap.add_argument("--ablation", type=int, default=0,
                     help="rooms of the Sec. 4.3 ablation (init variants, single radii); 0 = skip")
     ap.add_argument("--ablation-variants", default="plain,mono,sphere,single_radii,split,split_low,gaussian")
+    ap.add_argument("--profile-ite", type=int, default=0,
+                    help="with --profile-case: fit this many iterations before the profiled step")
     ap.add_argument("--profile-case", action="store_true",
                     help="for ncu: set up, warm up 3 steps, run one step inside a profiler range, exit")
     ap.add_argument("--profile-gemm", action="store_true",
@@ -473,6 +478,9 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_e2e:
         result["e2e"] = run_e2e(wl, args, first + args.steps, world)
+    cps = [int(x) for x in args.regimes.split(",") if x.strip()]
+    if cps:
+        result["regimes"] = run_regimes(wl, cps, args.steps, clocks, measured_peaks())
     if args.ttd:
         result["time_to_2cm"] = run_ttd(wl, args.ttd)
     if args.batched > 0:
@@ -504,8 +512,15 @@ def run_batched(args, rank, device):
                        Sec. 3.1), rooms fitted one by one;
       batched:         the same initialisation, all rooms in one launch per
                        kernel per step, rooms leaving the batch when done;
+      batched_offset:  the plain initialisation batched, with Eq. 10 started
+                       at the learned arm's offset (control: what the later
+                       lambda start alone gains);
       batched_learned: network-proposed initialisation (inference time
-                       included), batched."""
+                       included), batched.
+    Besides the totals (capped rooms stop at the cap), every arm reports the
+    rooms it brings to 2 cm and, on the rooms that every arm reaches, the GPU
+    time until the last of them is done (room by room: the sum of their fit
+    times) and their mean iterations to 2 cm."""
     import torch
     from paper_2412_03451_gb300 import autotune
     from paper_2412_03451_gb300 import batch as BT
@@ -528,6 +543,10 @@ def run_batched(args, rank, device):
     ss.tile = tile
     plain = [BT.fit_until(ss, [s], max_iters=args.batched_iters) for s in range(n)]
     bat = BT.fit_until(ss, list(range(n)), max_iters=args.batched_iters)
+    off = BT.fit_until(ss, list(range(n)), max_iters=args.batched_iters,
+                       lam_offset=ST.LEARNED_LAM_OFFSET)
+    arms = {"plain": [p["done_at"][0] for p in plain], "batched": bat["done_at"],
+            "batched_offset": off["done_at"]}
     t_plain = sum(p["gpu_ms"] for p in plain) / 1e3
     t_bat = bat["gpu_ms"] / 1e3
     out = {"rooms": n, "what": "GPU seconds to fit every room to mean depth error <= 2 cm "
@@ -538,6 +557,8 @@ def run_batched(args, rank, device):
            "reached_batched": sum(d is not None for d in bat["done_at"]),
            "iteration_cap": args.batched_iters, "tile": "%dx%d" % tile,
            "autotune_ms": {k: round(v, 4) for k, v in tuning.items()},
+           "batched_offset_s": round(off["gpu_ms"] / 1e3, 3),
+           "reached_batched_offset": sum(d is not None for d in off["done_at"]),
            "init_plain": "random surface points, random orientation, radii 0.5 x nearest-neighbour distance"}
     net = ST.load(device=device)
     if net is None:
@@ -571,6 +592,33 @@ def run_batched(args, rank, device):
                 "speedup_batched_learned": round(t_plain / t_bl, 3) if t_bl > 0 else None,
                 "reached_batched_learned": sum(d is not None for d in bl["done_at"]),
                 "learned_lambda_start_iteration": ST.LEARNED_LAM_OFFSET})
+    arms["batched_learned"] = bl["done_at"]
+    out["common_rooms"] = common_room_times(arms, infer_ms / 1e3)
+    return out
+
+
+def common_room_times(arms, learned_extra_s=0.0):
+    """Per arm, on the rooms that every arm brings to 2 cm: the GPU seconds until
+    the last of them is done (the "plain" arm fits rooms one by one, so its time
+    is the sum of their fit times; batched arms report the batch's clock when the
+    last common room finished) and their mean iterations to 2 cm.  done_at entries
+    are (iteration, GPU ms) or None."""
+    names = list(arms)
+    n = len(arms[names[0]])
+    common = [s for s in range(n) if all(arms[a][s] is not None for a in names)]
+    out = {"rooms": len(common), "reached": {a: sum(d is not None for d in arms[a]) for a in names}}
+    for a in names:
+        if not common:
+            break
+        its = [arms[a][s][0] for s in common]
+        ms = [arms[a][s][1] for s in common]
+        t = sum(ms) if a == "plain" else max(ms)
+        if a == "batched_learned":
+            t += learned_extra_s * 1e3
+        out[a] = {"seconds": round(t / 1e3, 3), "mean_iterations": round(sum(its) / len(its), 1)}
+    if common and "plain" in out:
+        for a in names[1:]:
+            out[a]["speedup_vs_plain"] = round(out["plain"]["seconds"] / max(out[a]["seconds"], 1e-9), 3)
     return out
 
 
@@ -638,6 +686,41 @@ def run_e2e(wl, args, first, world):
             "ms_per_step": round(t * 1e3 / K, 4),
             "pipeline": "copies of step s+1 on a second stream overlap step s (two device buffers)",
             "l2": "not flushed: every step's supervision arrives from host memory"}
+
+
+def run_regimes(wl, checkpoints, K, clocks, peaks):
+    """Stage times and the roofline at later points of a real fit of the benchmark
+    room (Eq. 10 sharpens the weight: the lists shrink and more pairs are opaque).
+    The room is fitted from its initial planes with eager steps; at each checkpoint
+    K more steps are timed with per-stage CUDA events (L2 flushed between steps)
+    and their work counted exactly."""
+    import torch
+    wl.reset(0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=wl.flat.device)
+    nb = N_VIEWS // VIEWS_PER_STEP
+    out = []
+    for cp in checkpoints:
+        while wl.fit.ite < cp:
+            s = wl.fit.ite
+            if s % 100 == 0:
+                for b in range(nb):
+                    wl.grow_if_needed(s + b)
+            wl.step(s)
+        for b in range(nb):
+            wl.grow_if_needed(wl.fit.ite + b)
+        wl.r.status.zero_()
+        first = wl.fit.ite
+        counts = []
+        per_step, stages = time_steps(wl, first, K, flush, counts_out=counts)
+        if int(wl.r.status.item()) & CAPACITY_BIT:
+            raise RuntimeError("tile-list capacity overflow in the regime measurement")
+        vs = wl.r.view_sums.cpu().numpy()
+        out.append({"iteration": first, "lambda": round(wl.B.lambda_schedule(first), 3),
+                    "ms_per_step_eager": round(statistics.mean(per_step), 4),
+                    "stage_ms": {k: round(statistics.mean(v), 4) for k, v in stages.items()},
+                    "mean_abs_depth_err_m": round(float(vs[:, 2].sum() / max(vs[:, 3].sum(), 1.0)), 5),
+                    "roofline": roofline_entry(counts, stages, K, clocks, src_hash(), peaks)})
+    return out
 
 
 def run_ttd(wl, max_iters):
@@ -838,24 +921,32 @@ def run_reference(args):
 
 def profile_case(args):
     """One eager optimisation step of the workload inside cudaProfilerStart/Stop
-    (for `ncu --profile-from-start off`), after 3 warm-up steps."""
+    (for `ncu --profile-from-start off`), after 3 warm-up steps, or, with
+    --profile-ite N, after a real fit of N iterations (eager steps, outside the
+    profiled range)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     tile = (16, 16) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
     wl = Workload(0, tile, "cuda:0")
     wl.reset(args.start_ite)
-    for i in range(3):
-        wl.grow_if_needed(i)
+    last = max(3, args.profile_ite)
+    nb = N_VIEWS // VIEWS_PER_STEP
+    for i in range(last):
+        if i < 3 or i % 100 == 0:
+            for b in range(nb):
+                wl.grow_if_needed(i + b)
         wl.step(i)
-    wl.grow_if_needed(3)
+    wl.grow_if_needed(last)
+    wl.r.status.zero_()
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStart()
-    wl.step(3)
+    wl.step(last)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
     status = int(wl.r.status.item())
-    print(json.dumps({"profile_case": "step 3", "tile": "%dx%d" % tile, "status": status}))
+    print(json.dumps({"profile_case": "step %d" % last, "lambda": wl.B.lambda_schedule(last),
+                      "tile": "%dx%d" % tile, "status": status}))
     return 0 if status == 0 else 1
 
 

@@ -51,3 +51,18 @@ def test_roofline_entry_arithmetic():
     assert abs(r2["other_roofs"]["issue"]["achieved"] - bench.INSTR["splat_fused"] / 1e6) < 0.06
     assert abs(r2["other_roofs"]["hbm"]["achieved"] - bench.TRAFFIC["splat_fused"] / 1e6) < 0.1
 
+
+
+def test_common_room_times_compare_only_rooms_every_arm_reaches():
+    import bench
+    arms = {"plain": [(100, 50.0), (200, 80.0), None, (400, 10.0)],
+            "batched": [(110, 40.0), (210, 60.0), (300, 90.0), (380, 95.0)],
+            "batched_learned": [(50, 20.0), (100, 35.0), (120, 40.0), None]}
+    out = bench.common_room_times(arms, learned_extra_s=0.005)
+    assert out["rooms"] == 2 and out["reached"] == {"plain": 3, "batched": 4, "batched_learned": 3}
+    # room by room: the sum of the common rooms' fit times; batched: the clock when the last is done
+    assert out["plain"]["seconds"] == 0.13 and out["batched"]["seconds"] == 0.06
+    assert out["batched_learned"]["seconds"] == 0.04          # 35 ms + 5 ms of inference
+    assert out["plain"]["mean_iterations"] == 150.0
+    assert out["batched"]["speedup_vs_plain"] == round(0.13 / 0.06, 3)
+    assert bench.common_room_times({"plain": [None], "batched": [(1, 1.0)]})["rooms"] == 0
