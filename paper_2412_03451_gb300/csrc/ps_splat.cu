@@ -28,10 +28,13 @@
 //   A_j = w_j t_j + (1 - w_j) A_{j+1},  dD/dw_j = T_j (t_j - A_{j+1}),
 //   dD/dt_j = T_j w_j,  dN/dn_j = T_j w_j,  and the same for N with n_j,
 // so nothing is divided by 1 - w_j.  Each pair's gradient is chained through
-// Eq. 9, 7-8, 6 and 4 into the 16 record floats, summed over the lanes of a
-// warp that hold the same record, and added to a per-record accumulator; a
-// second kernel chains the records through the camera transform and Eq. 2-3
-// into the world parameters.
+// Eq. 9, 7-8, 6 and 4 into 16 record floats (the gradients of n_c, v^x_c, v^y_c
+// at a fixed plane centre, of s, a_x, a_y and of the radii; the first three use
+// the intersection relative to the centre, t d - p_c = P_X v^x + P_Y v^y, so no
+// metre-sized terms are summed only to cancel), summed over the lanes of a warp
+// that hold the same record and added to a per-record accumulator; a second
+// kernel chains the records through the camera transform and Eq. 2-3 into the
+// world parameters.
 #include <mutex>
 
 #include <cuda.h>
@@ -314,6 +317,40 @@ __device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Wa
 }
 
 // One strip: pixel setup, walk, then the forward output or the backward adjoint.
+// Sums v[8] over the warp's 32 lanes as a transpose-reduction: after 3 exchange
+// levels each lane carries one float (index bit2 + 2 bit3 + 4 bit4 of its lane),
+// and two more levels leave lanes 4c .. 4c + 3 with the total of float c in v[0].
+__device__ __forceinline__ void warp_transpose8(float (&v)[8])
+{
+    const int lane = threadIdx.x & 31;
+    {
+        const bool hi = lane & 16;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float send = hi ? v[c] : v[c + 4];
+            const float keep = hi ? v[c + 4] : v[c];
+            v[c] = keep + __shfl_xor_sync(kFull, send, 16);
+        }
+    }
+    {
+        const bool hi = lane & 8;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float send = hi ? v[c] : v[c + 2];
+            const float keep = hi ? v[c + 2] : v[c];
+            v[c] = keep + __shfl_xor_sync(kFull, send, 8);
+        }
+    }
+    {
+        const bool hi = lane & 4;
+        const float send = hi ? v[0] : v[1];
+        const float keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(kFull, send, 4);
+    }
+    v[0] += __shfl_xor_sync(kFull, v[0], 2);
+    v[0] += __shfl_xor_sync(kFull, v[0], 1);
+}
+
 // The lane's Eq. 14 terms of a fused strip: |1 - N.N*|, ||N - N*||_1, |D - D*|,
 // 1 (supervised pixels), and the strip's view.
 struct StripLoss {
@@ -472,7 +509,12 @@ __device__ __forceinline__ StripLoss run_strip(const SplatArgs& a, WarpStage& ws
                                        gN2 * (n.z - B2));
                 const float Tw = Tj * w;
                 float gt = Tw * gD;
-                float gnx = Tw * gN0, gny = Tw * gN1, gnz = Tw * gN2;
+                // the intersection relative to the plane centre, t d - p_c = P_X v^x + P_Y v^y
+                // (Eq. 6 on the plane): radius-sized, so the gradients of n_c and v_c below
+                // (at fixed p_c) are accumulated without the cancellation of t d against p_c
+                const float ox = fmaf(pe.X, vx.x, pe.Y * vy.x);
+                const float oy = fmaf(pe.X, vx.y, pe.Y * vy.y);
+                const float oz = fmaf(pe.X, vx.z, pe.Y * vy.z);
                 A = fmaf(w, t, (1.f - w) * A);
                 B0 = fmaf(w, n.x, (1.f - w) * B0);
                 B1 = fmaf(w, n.y, (1.f - w) * B1);
@@ -484,18 +526,15 @@ __device__ __forceinline__ StripLoss run_strip(const SplatArgs& a, WarpStage& ws
                     const float gX = -gw * w * pe.X * ix * ix;
                     const float gY = -gw * w * pe.Y * iy * iy;
                     const float grX = -gX * pe.X * ix, grY = -gY * pe.Y * iy;
-                    // Eq. 6 in record form on both axes
+                    // Eq. 6 on both axes: P = t (d . v_c) - a, dP/dv_c = t d - p_c at fixed p_c
                     gt = fmaf(gX, pe.dvx, gt);
                     gt = fmaf(gY, pe.dvy, gt);
-                    const float gvx = gX * t, gvy = gY * t;
+                    // Eq. 4: t = s / (d . n_c); dt/dn_c = (p_c - t d) / (d . n_c) at fixed p_c
                     const float gs = __fdividef(gt, pe.den);
-                    const float gden = -gs * t;
-                    gnx = fmaf(gden, dx, gnx);
-                    gny = fmaf(gden, dy, gny);
-                    gnz = gnz + gden;
-                    gr[0] = gnx; gr[1] = gny; gr[2] = gnz; gr[3] = gs;
-                    gr[4] = gvx * dx; gr[5] = gvx * dy; gr[6] = gvx; gr[7] = -gX;
-                    gr[8] = gvy * dx; gr[9] = gvy * dy; gr[10] = gvy; gr[11] = -gY;
+                    gr[0] = fmaf(-gs, ox, Tw * gN0); gr[1] = fmaf(-gs, oy, Tw * gN1);
+                    gr[2] = fmaf(-gs, oz, Tw * gN2); gr[3] = gs;
+                    gr[4] = gX * ox; gr[5] = gX * oy; gr[6] = gX * oz; gr[7] = -gX;
+                    gr[8] = gY * ox; gr[9] = gY * oy; gr[10] = gY * oz; gr[11] = -gY;
                     const bool px = pe.X > 0.f, py = pe.Y > 0.f;
                     gr[12] = px ? grX : 0.f; gr[13] = px ? 0.f : grX;
                     gr[14] = py ? grY : 0.f; gr[15] = py ? 0.f : grY;
@@ -505,23 +544,19 @@ __device__ __forceinline__ StripLoss run_strip(const SplatArgs& a, WarpStage& ws
                 // m = r_side - |P|: the radius gets gm, P gets -gm sgn(P)
                 const int ridx = (pe.sideX ? 0 : 2) + (pe.pos ? 0 : 1);
                 const float gP = (pe.P > 0.f) ? -gm : ((pe.P < 0.f) ? gm : 0.f);
-                // Eq. 6 in record form: P = t (d . v_c) - a
+                // Eq. 6: P = t (d . v_c) - a, dP/dv_c = t d - p_c at fixed p_c
                 gt = fmaf(gP, pe.dv, gt);
-                const float gv = gP * t;
-                // Eq. 4: t = s / (d . n_c)
+                // Eq. 4: t = s / (d . n_c); dt/dn_c = (p_c - t d) / (d . n_c) at fixed p_c
                 const float gs = __fdividef(gt, pe.den);
-                const float gden = -gs * t;
-                gnx = fmaf(gden, dx, gnx);
-                gny = fmaf(gden, dy, gny);
-                gnz = gnz + gden;
-                gr[0] = gnx; gr[1] = gny; gr[2] = gnz; gr[3] = gs;
+                gr[0] = fmaf(-gs, ox, Tw * gN0); gr[1] = fmaf(-gs, oy, Tw * gN1);
+                gr[2] = fmaf(-gs, oz, Tw * gN2); gr[3] = gs;
                 const int vo = pe.sideX ? 4 : 8;
 #pragma unroll
                 for (int c = 4; c < 12; c += 4) {
                     if (c == vo) {
-                        gr[c + 0] = gv * dx;
-                        gr[c + 1] = gv * dy;
-                        gr[c + 2] = gv;
+                        gr[c + 0] = gP * ox;
+                        gr[c + 1] = gP * oy;
+                        gr[c + 2] = gP * oz;
                         gr[c + 3] = -gP;
                     }
                 }
@@ -543,39 +578,13 @@ __device__ __forceinline__ StripLoss run_strip(const SplatArgs& a, WarpStage& ws
                 rem &= ~gmask;
                 const bool member = (gmask >> lane) & 1u;
                 float* dst = reinterpret_cast<float*>(a.g_rec + (size_t)gid * 4);
-                // two halves of 8 floats: 9 shuffles each leave lanes 4c..4c+3 holding
-                // the total of float c of the half
+                // two halves of 8 floats: lanes 4c..4c+3 end with the total of float c of the half
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float v[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) v[c] = member ? gr[8 * h + c] : 0.f;
-                    {
-                        const bool hi = lane & 16;
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const float send = hi ? v[c] : v[c + 4];
-                            const float keep = hi ? v[c + 4] : v[c];
-                            v[c] = keep + __shfl_xor_sync(kFull, send, 16);
-                        }
-                    }
-                    {
-                        const bool hi = lane & 8;
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            const float send = hi ? v[c] : v[c + 2];
-                            const float keep = hi ? v[c + 2] : v[c];
-                            v[c] = keep + __shfl_xor_sync(kFull, send, 8);
-                        }
-                    }
-                    {
-                        const bool hi = lane & 4;
-                        const float send = hi ? v[0] : v[1];
-                        const float keep = hi ? v[1] : v[0];
-                        v[0] = keep + __shfl_xor_sync(kFull, send, 4);
-                    }
-                    v[0] += __shfl_xor_sync(kFull, v[0], 2);
-                    v[0] += __shfl_xor_sync(kFull, v[0], 1);
+                    warp_transpose8(v);
                     if ((lane & 3) == 0) atomicAdd(dst + 8 * h + ((lane >> 2) & 7), v[0]);
                 }
             }
@@ -781,21 +790,20 @@ __global__ void __launch_bounds__(128) k_chain(ChainArgs a)
     const float vx[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y)};
     const float vy[3] = {2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x)};
     const float nn[3] = {2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y)};
-    const float pw[3] = {__ldg(&a.center[3 * p + 0]), __ldg(&a.center[3 * p + 1]),
-                         __ldg(&a.center[3 * p + 2])};
-    float pc[3], vxc[3], vyc[3], nc[3];
+    float vxc[3], vyc[3], nc[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        pc[i] = R[4 * i] * pw[0] + R[4 * i + 1] * pw[1] + R[4 * i + 2] * pw[2] + R[4 * i + 3];
         vxc[i] = R[4 * i] * vx[0] + R[4 * i + 1] * vx[1] + R[4 * i + 2] * vx[2];
         vyc[i] = R[4 * i] * vy[0] + R[4 * i + 1] * vy[1] + R[4 * i + 2] * vy[2];
         nc[i] = R[4 * i] * nn[0] + R[4 * i + 1] * nn[1] + R[4 * i + 2] * nn[2];
     }
-    // record = {n_c, n_c.p_c, v^x_c, v^x_c.p_c, v^y_c, v^y_c.p_c, r}
+    // record = {n_c, s = n_c.p_c, v^x_c, a_x = v^x_c.p_c, v^y_c, a_y = v^y_c.p_c, r}; the splat
+    // kernels accumulate the gradients of n_c, v^x_c, v^y_c at fixed p_c and those of s, a_x,
+    // a_y, so the camera-frame gradient of p_c is gs n_c + gax v^x_c + gay v^y_c
     const float gs = g0.w, gax = g1.w, gay = g2.w;
-    const float gnc[3] = {g0.x + gs * pc[0], g0.y + gs * pc[1], g0.z + gs * pc[2]};
-    const float gvxc[3] = {g1.x + gax * pc[0], g1.y + gax * pc[1], g1.z + gax * pc[2]};
-    const float gvyc[3] = {g2.x + gay * pc[0], g2.y + gay * pc[1], g2.z + gay * pc[2]};
+    const float gnc[3] = {g0.x, g0.y, g0.z};
+    const float gvxc[3] = {g1.x, g1.y, g1.z};
+    const float gvyc[3] = {g2.x, g2.y, g2.z};
     float gpc[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) gpc[i] = gs * nc[i] + gax * vxc[i] + gay * vyc[i];
