@@ -67,7 +67,7 @@ SM_COUNT, FP32_LANES = 152, 128
 ONE_CTA_SCAN = 48 * 1024
 
 
-def roofline_entry(counts, stages, K, clocks, sha, peaks):
+def roofline_entry(counts, stages, K, clocks, sha, peaks, regime=0):
     """Roofline of the dominant splat kernel from the exact work counts of K launches
     (tested, candidate, composited pairs), the per-stage CUDA-event times (ms lists),
     the sampled clocks, the kernel source hash (profile-derived constants apply only
@@ -89,7 +89,8 @@ def roofline_entry(counts, stages, K, clocks, sha, peaks):
         flops = ((cand * FLOP_CAND + comp * FLOP_COMP_BWD) if dom == "splat_bwd"
                  else (cand * FLOP_CAND + comp * FLOP_COMP_FWD)) / K
     achieved = flops / (dom_ms / 1e3) / 1e12
-    traffic = TRAFFIC.get(dom) if TRAFFIC.get("src_sha") == sha else None
+    cap = CAPTURES.get(dom, {}).get(regime) if CAPTURES.get("src_sha") == sha else None
+    traffic = cap["dram_bytes"] if cap else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_clock,
@@ -101,7 +102,7 @@ def roofline_entry(counts, stages, K, clocks, sha, peaks):
         "mufu": {"achieved": round(mufu / (dom_ms / 1e3) / 1e12, 4), "peak": round(mufu_peak, 3),
                  "unit": "Tops/s", "frac": round(mufu / (dom_ms / 1e3) / 1e12 / mufu_peak, 4),
                  "peak_basis": "152 SMs x 16 per clock x %.0f MHz" % sm_clock}}
-    instr = INSTR.get(dom) if INSTR.get("src_sha") == sha else None
+    instr = cap["warp_instructions"] if cap else None
     if instr:
         ips = instr / (dom_ms / 1e3) / 1e9
         ipeak = SM_COUNT * SCHEDULERS_PER_SM * sm_clock * 1e6 / 1e9
@@ -142,13 +143,15 @@ def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:
     binning = 1 + scans + 3
     return (1 + 1 + binning + 2 + 2) if fused else (1 + binning + 4 + 2)
 
-# DRAM bytes (read + write) per launch of the fused splat kernel from the ncu
-# capture summarised in profiles/k_splat_fused_room640_8x8.md; reported only while
-# the kernel source is the one it was taken on.
-TRAFFIC = {"splat_fused": 51150080, "src_sha": "b83a89d27baf42fd"}
-# warp instructions of the same captured launch (smsp__inst_executed.sum), for the
-# issue roof: 152 SMs x 4 schedulers x one warp instruction per clock
-INSTR = {"splat_fused": 413433394, "src_sha": "b83a89d27baf42fd"}
+# DRAM bytes (read + write) and warp instructions (smsp__inst_executed.sum) per launch
+# of the fused splat kernel from the ncu captures summarised in
+# profiles/k_splat_fused_room640_8x8_ite3.md (the benchmark's first lambda) and
+# .._ite1000.md (iteration 1,000 of the fit), keyed by the regime's iteration; reported
+# only while the kernel source is the one they were taken on.  The issue roof is
+# 152 SMs x 4 schedulers x one warp instruction per clock.
+CAPTURES = {"src_sha": "2eec71b5a47ed168",
+            "splat_fused": {0: {"dram_bytes": 51195904, "warp_instructions": 403849080},
+                            1000: {"dram_bytes": 44266496, "warp_instructions": 158483425}}}
 SCHEDULERS_PER_SM = 4
 
 
@@ -164,6 +167,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", default="auto", choices=["auto", "16x16", "8x8", "32x8"])
+    ap.add_argument("--warps", type=int, default=0, choices=[0, 2, 4, 8],
+                    help="warps per CTA of the splat kernels when --tile is given (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ttd", type=int, default=0,
@@ -259,7 +264,7 @@ class ClockSampler:
 # Our arm.
 
 class Workload:
-    def __init__(self, rank: int, tile, device):
+    def __init__(self, rank: int, tile, device, warps=0):
         import numpy as np
         import torch
         from paper_2412_03451_gb300 import binding as B
@@ -283,7 +288,7 @@ class Workload:
         self.gt_normal = gtr.normal.clone()
         del gtr
         self.r = SP.Renderer([H] * VIEWS_PER_STEP, [W] * VIEWS_PER_STEP, [0] * VIEWS_PER_STEP,
-                             [0, N_INIT], tile=tile, device=device)
+                             [0, N_INIT], tile=tile, device=device, warps=warps)
         nb = N_VIEWS // VIEWS_PER_STEP
         self.r.preplan([cams.w2c[b * VIEWS_PER_STEP:(b + 1) * VIEWS_PER_STEP] for b in range(nb)],
                        [cams.intr[b * VIEWS_PER_STEP:(b + 1) * VIEWS_PER_STEP] for b in range(nb)])
@@ -346,24 +351,25 @@ def time_steps(wl, first, K, flush, counts_out=None):
 
 
 def autotune_tile(rank, device):
-    """Picks the tile shape for this workload by timing each candidate on its
-    first camera batch (outside every timed region)."""
+    """Picks the tile shape and the warps per CTA (the planes staged per
+    shared-memory batch) for this workload by timing each pair on its first
+    camera batch (outside every timed region)."""
     from paper_2412_03451_gb300 import autotune
     from paper_2412_03451_gb300 import splat as SP
     wl = Workload(rank, (16, 16), device)
     gd, gn = wl.gt_slice(0)
     cams = wl.room.cams
 
-    def make(tile):
+    def make(tile, warps):
         r = SP.Renderer([H] * VIEWS_PER_STEP, [W] * VIEWS_PER_STEP, [0] * VIEWS_PER_STEP,
-                        [0, N_INIT], tile=tile, device=device)
+                        [0, N_INIT], tile=tile, device=device, warps=warps)
         r.set_cameras(cams.w2c[:VIEWS_PER_STEP], cams.intr[:VIEWS_PER_STEP])
         return r
 
     key = autotune.key_for([(H, W)], VIEWS_PER_STEP, N_INIT)
-    tile, times = autotune.pick_tile(make, wl.flat, gd, gn, wl.B.lambda_schedule(0), key)
+    tile, warps, times = autotune.pick_launch(make, wl.flat, gd, gn, wl.B.lambda_schedule(0), key)
     del wl
-    return tile, times
+    return tile, warps, times
 
 
 def time_replays(wl, first, K, flush):
@@ -390,11 +396,12 @@ def run_ours(args, rank, world, local_rank):
     device = "cuda:%d" % local_rank
     torch.cuda.set_device(local_rank)
     tuning = None
+    warps = args.warps
     if args.tile == "auto":
-        tile, tuning = autotune_tile(rank, device)
+        tile, warps, tuning = autotune_tile(rank, device)
     else:
         tile = tuple(int(x) for x in args.tile.split("x"))
-    wl = Workload(rank, tile, device)
+    wl = Workload(rank, tile, device, warps)
     wl.reset(args.start_ite)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
     nb = N_VIEWS // VIEWS_PER_STEP
@@ -459,6 +466,7 @@ def run_ours(args, rank, world, local_rank):
 
     cfg = workload_config(args, world)
     cfg["tile"] = "%dx%d" % tile
+    cfg["warps_per_cta"] = warps or 4
     if tuning:
         cfg["autotune_ms"] = {k: round(v, 4) for k, v in tuning.items()}
     cfg["launch"] = "captured CUDA graph per step" if use_graphs else "eager launches"
@@ -518,9 +526,10 @@ def run_batched(args, rank, device):
       batched_learned: network-proposed initialisation (inference time
                        included), batched.
     Besides the totals (capped rooms stop at the cap), every arm reports the
-    rooms it brings to 2 cm and, on the rooms that every arm reaches, the GPU
-    time until the last of them is done (room by room: the sum of their fit
-    times) and their mean iterations to 2 cm."""
+    rooms it brings to 2 cm; then the rooms that every arm reaches are fitted
+    again by each batched arm on their own (the batch's clock would otherwise
+    include the rooms that never converge), against the sum of their one-by-one
+    fit times, with their mean iterations to 2 cm."""
     import torch
     from paper_2412_03451_gb300 import autotune
     from paper_2412_03451_gb300 import batch as BT
@@ -531,16 +540,16 @@ def run_batched(args, rank, device):
     inits = [S.surface_init_nn(room, K, 4000 + 100 * rank + i) for i, (room, K) in enumerate(rooms)]
     ss = BT.SceneSet([r for r, _ in rooms], inits, device=device)
 
-    def make(tile):
-        ss.tile = tile
+    def make(tile, warps):
+        ss.tile, ss.warps = tile, warps
         r = ss.renderer()
         r.select(0)
         return r
 
     key = autotune.key_for([(rm.cams.H, rm.cams.W) for rm in ss.rooms], ss.vps * n, sum(ss.K))
-    tile, tuning = autotune.pick_tile(make, ss.flat_init(), ss.gt_depth, ss.gt_normal,
-                                      20.0 / 2.718281828459045, key)
-    ss.tile = tile
+    tile, warps, tuning = autotune.pick_launch(make, ss.flat_init(), ss.gt_depth, ss.gt_normal,
+                                               20.0 / 2.718281828459045, key)
+    ss.tile, ss.warps = tile, warps
     plain = [BT.fit_until(ss, [s], max_iters=args.batched_iters) for s in range(n)]
     bat = BT.fit_until(ss, list(range(n)), max_iters=args.batched_iters)
     off = BT.fit_until(ss, list(range(n)), max_iters=args.batched_iters,
@@ -555,7 +564,7 @@ def run_batched(args, rank, device):
            "speedup_batched": round(t_plain / t_bat, 3) if t_bat > 0 else None,
            "reached_plain": sum(p["done_at"][0] is not None for p in plain),
            "reached_batched": sum(d is not None for d in bat["done_at"]),
-           "iteration_cap": args.batched_iters, "tile": "%dx%d" % tile,
+           "iteration_cap": args.batched_iters, "tile": "%dx%d" % tile, "warps_per_cta": warps,
            "autotune_ms": {k: round(v, 4) for k, v in tuning.items()},
            "batched_offset_s": round(off["gpu_ms"] / 1e3, 3),
            "reached_batched_offset": sum(d is not None for d in off["done_at"]),
@@ -569,7 +578,7 @@ def run_batched(args, rank, device):
     c0 = r0.cams
     ST.propose_planes(net, r0, ss.gt_depth[:c0.H * c0.W].view(1, c0.H, c0.W),
                       ss.gt_normal[:c0.H * c0.W].view(1, c0.H, c0.W, 3), [0], max_planes=100)
-    learned, infer_ms = [], 0.0
+    learned, infer_ms, infer_room = [], 0.0, []
     for i, room in enumerate(ss.rooms):
         c = room.cams
         off = int(ss.gt_off[i][0])
@@ -583,8 +592,9 @@ def run_batched(args, rank, device):
         e1.record()
         torch.cuda.synchronize()
         infer_ms += e0.elapsed_time(e1)
+        infer_room.append(e0.elapsed_time(e1))
         learned.append(P)
-    ss_l = BT.SceneSet(ss.rooms, learned, device=device, tile=tile)
+    ss_l = BT.SceneSet(ss.rooms, learned, device=device, tile=tile, warps=warps)
     bl = BT.fit_until(ss_l, list(range(n)), max_iters=args.batched_iters,
                       lam_offset=ST.LEARNED_LAM_OFFSET)
     t_bl = bl["gpu_ms"] / 1e3 + infer_ms / 1e3
@@ -593,41 +603,49 @@ def run_batched(args, rank, device):
                 "reached_batched_learned": sum(d is not None for d in bl["done_at"]),
                 "learned_lambda_start_iteration": ST.LEARNED_LAM_OFFSET})
     arms["batched_learned"] = bl["done_at"]
-    out["common_rooms"] = common_room_times(arms, infer_ms / 1e3)
+    common, cr = common_rooms(arms)
+    if common:
+        cap = args.batched_iters
+        refit = {"plain": sum(plain[s]["gpu_ms"] for s in common)}
+        rb = BT.fit_until(ss, common, max_iters=cap)
+        ro = BT.fit_until(ss, common, max_iters=cap, lam_offset=ST.LEARNED_LAM_OFFSET)
+        rl = BT.fit_until(ss_l, common, max_iters=cap, lam_offset=ST.LEARNED_LAM_OFFSET)
+        refit.update({"batched": rb["gpu_ms"], "batched_offset": ro["gpu_ms"],
+                      "batched_learned": rl["gpu_ms"] + sum(infer_room[s] for s in common)})
+        for a, ms in refit.items():
+            cr[a]["seconds"] = round(ms / 1e3, 3)
+        for a in ("batched", "batched_offset", "batched_learned"):
+            cr[a]["speedup_vs_plain"] = round(refit["plain"] / max(refit[a], 1e-9), 3)
+        cr["refit_reached"] = {"batched": sum(d is not None for d in rb["done_at"]),
+                               "batched_offset": sum(d is not None for d in ro["done_at"]),
+                               "batched_learned": sum(d is not None for d in rl["done_at"])}
+    out["common_rooms"] = cr
     return out
 
 
-def common_room_times(arms, learned_extra_s=0.0):
-    """Per arm, on the rooms that every arm brings to 2 cm: the GPU seconds until
-    the last of them is done (the "plain" arm fits rooms one by one, so its time
-    is the sum of their fit times; batched arms report the batch's clock when the
-    last common room finished) and their mean iterations to 2 cm.  done_at entries
-    are (iteration, GPU ms) or None."""
+def common_rooms(arms):
+    """The rooms every arm brings to 2 cm, and per arm how many it reaches and the
+    mean iterations to 2 cm on the common rooms (done_at entries are (iteration,
+    GPU ms) or None)."""
     names = list(arms)
     n = len(arms[names[0]])
     common = [s for s in range(n) if all(arms[a][s] is not None for a in names)]
     out = {"rooms": len(common), "reached": {a: sum(d is not None for d in arms[a]) for a in names}}
     for a in names:
-        if not common:
-            break
-        its = [arms[a][s][0] for s in common]
-        ms = [arms[a][s][1] for s in common]
-        t = sum(ms) if a == "plain" else max(ms)
-        if a == "batched_learned":
-            t += learned_extra_s * 1e3
-        out[a] = {"seconds": round(t / 1e3, 3), "mean_iterations": round(sum(its) / len(its), 1)}
-    if common and "plain" in out:
-        for a in names[1:]:
-            out[a]["speedup_vs_plain"] = round(out["plain"]["seconds"] / max(out[a]["seconds"], 1e-9), 3)
-    return out
+        if common:
+            its = [arms[a][s][0] for s in common]
+            out[a] = {"mean_iterations": round(sum(its) / len(its), 1)}
+    return common, out
 
 
 def run_e2e(wl, args, first, world):
     """Same metric through host buffers: every step's ground-truth depth/normal
     maps come from pinned host memory and its loss sums go back to pinned host
-    memory, inside the timed region.  The copies of step s + 1 run on a second
-    stream while step s (a captured graph reading the other of two device
-    buffers) computes; events order each buffer's reuse."""
+    memory, inside the timed region.  The step's CUDA graph copies the next
+    step's supervision into the other of two device buffers on a parallel branch
+    (overlapping the step) and its loss sums to the host (Fitter.enable_graphs
+    with host_stream); the first step's supervision is copied in the timed
+    region before the first replay."""
     import torch
     dev = wl.flat.device
     nb = N_VIEWS // VIEWS_PER_STEP
@@ -637,54 +655,42 @@ def run_e2e(wl, args, first, world):
     bufs = [(torch.empty(n, dtype=torch.float32, device=dev),
              torch.empty((n, 3), dtype=torch.float32, device=dev)) for _ in range(2)]
     K = args.steps
-    out = torch.empty((K, VIEWS_PER_STEP, 4), dtype=torch.float64).pin_memory()
+    sums_host = torch.zeros((nb, VIEWS_PER_STEP, 4), dtype=torch.float64).pin_memory()
     for s in range(first, first + K):
         wl.grow_if_needed(s)
     wl.fit.ite = first
     # batch b always reads buffer b % 2 (the batch count is even)
-    wl.fit.enable_graphs(first + K + 8, list(range(nb)), [bufs[b % 2] for b in range(nb)])
+    offsets = [b * n for b in range(nb)]
+    wl.fit.enable_graphs(first + K + 8, list(range(nb)), [bufs[b % 2] for b in range(nb)],
+                         host_stream={"host_depth": host_d, "host_normal": host_n, "offsets": offsets,
+                                      "sums_host": sums_host})
     wl.r.status.zero_()
     main = torch.cuda.current_stream()
-    side = torch.cuda.Stream(device=dev)
-    ready = [torch.cuda.Event() for _ in range(2)]
-    free = [torch.cuda.Event() for _ in range(2)]
-
-    def copy_in(s):
-        p, b = s % 2, (s % nb) * VIEWS_PER_STEP
-        with torch.cuda.stream(side):
-            side.wait_event(free[p])
-            bufs[p][0].copy_(host_d[b * wl.hw:b * wl.hw + n], non_blocking=True)
-            bufs[p][1].copy_(host_n[b * wl.hw:b * wl.hw + n], non_blocking=True)
-            ready[p].record(side)
-
-    for p in range(2):
-        free[p].record(main)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     ev0.record(main)
-    copy_in(first)
+    b0 = first % nb
+    bufs[b0 % 2][0].copy_(host_d[offsets[b0]:offsets[b0] + n], non_blocking=True)
+    bufs[b0 % 2][1].copy_(host_n[offsets[b0]:offsets[b0] + n], non_blocking=True)
     for i in range(K):
-        s = first + i
-        if i + 1 < K:
-            copy_in(s + 1)
-        main.wait_event(ready[s % 2])
-        vs = wl.fit.replay(s % nb)
-        free[s % 2].record(main)
-        out[i].copy_(vs, non_blocking=True)
+        wl.fit.replay((first + i) % nb)
     ev1.record(main)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if int(wl.r.status.item()) & CAPACITY_BIT:
         raise RuntimeError("tile-list capacity overflow inside the e2e region")
+    if not bool(torch.isfinite(sums_host).all()):
+        raise RuntimeError("non-finite loss sums in the e2e region")
     ms = ev0.elapsed_time(ev1)
     t = RK.max_over_ranks(max(ms / 1e3, wall), dev)
     value = RK.job_throughput(RK.sum_over_ranks(VIEWS_PER_STEP * H * W * K, dev), t) / 1e6
     return {"value": round(value, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(n * 4 + n * 12), "d2h_bytes_per_step": VIEWS_PER_STEP * 4 * 8,
             "ms_per_step": round(t * 1e3 / K, 4),
-            "pipeline": "copies of step s+1 on a second stream overlap step s (two device buffers)",
+            "pipeline": "each step's graph copies the next step's supervision from pinned host memory "
+                        "(parallel branch, two device buffers) and its loss sums back to pinned memory",
             "l2": "not flushed: every step's supervision arrives from host memory"}
 
 
@@ -719,7 +725,7 @@ def run_regimes(wl, checkpoints, K, clocks, peaks):
                     "ms_per_step_eager": round(statistics.mean(per_step), 4),
                     "stage_ms": {k: round(statistics.mean(v), 4) for k, v in stages.items()},
                     "mean_abs_depth_err_m": round(float(vs[:, 2].sum() / max(vs[:, 3].sum(), 1.0)), 5),
-                    "roofline": roofline_entry(counts, stages, K, clocks, src_hash(), peaks)})
+                    "roofline": roofline_entry(counts, stages, K, clocks, src_hash(), peaks, regime=cp)})
     return out
 
 
@@ -928,7 +934,7 @@ def profile_case(args):
     import __graft_entry__
     __graft_entry__.build()
     tile = (16, 16) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
-    wl = Workload(0, tile, "cuda:0")
+    wl = Workload(0, tile, "cuda:0", args.warps)
     wl.reset(args.start_ite)
     last = max(3, args.profile_ite)
     nb = N_VIEWS // VIEWS_PER_STEP

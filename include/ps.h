@@ -103,7 +103,10 @@ typedef struct ps_settings {
     int tile_w, tile_h;    /* tile shape in pixels: 8x8, 16x16 or 32x8 */
     int flags;             /* PS_SINGLE_RADII | PS_HARD | PS_GAUSSIAN */
     float a_cos, a_l1n, a_depth;  /* Eq. 14 weights: alpha_1 = 5, alpha_1 = 5, alpha_2 = 1 */
-    int reserved;
+    int cta_warps;         /* launch shape of the splat kernels: warps per CTA, 2, 4 or 8 (0: 4).
+                              Each warp stages 32 plane records of its tile list per shared-memory
+                              batch, so a CTA holds 32 x cta_warps records at a time.  Results
+                              do not depend on it. */
     const ps_step_state* d_state; /* optional (device): if not NULL, lambda and delta are read
                                      from *d_state when the kernels run, not from the fields above */
 } ps_settings;

@@ -24,10 +24,11 @@ class SceneSet:
     """Scenes (rooms with initial planes), their resident ground truth and the
     per-step camera batches (views_per_step views of each scene per step)."""
 
-    def __init__(self, rooms, inits, device="cuda", tile=(16, 16), views_per_step=8, flags=0):
+    def __init__(self, rooms, inits, device="cuda", tile=(16, 16), views_per_step=8, flags=0, warps=0):
         self.rooms, self.inits = rooms, inits
         self.device = torch.device(device)
         self.tile = tile
+        self.warps = int(warps)       # warps per CTA of the splat kernels (0: the library default)
         self.flags = int(flags)       # ps_settings flags of the fit (PS_SINGLE_RADII, ...)
         self.S = len(rooms)
         self.vps = views_per_step
@@ -92,7 +93,7 @@ class SceneSet:
         K = [self.K[s] for s in scenes] if Ks is None else list(Ks)
         pptr = np.concatenate([[0], np.cumsum(K)]).astype(np.int32)
         r = SP.Renderer(H, W, sov, pptr, tile=self.tile, M=M, capacity=capacity,
-                        device=self.device, flags=self.flags)
+                        device=self.device, flags=self.flags, warps=self.warps)
         w2cs, intrs, gts = [], [], []
         for b in range(self.n_batches):
             vi = self.batch_views(b)

@@ -39,7 +39,7 @@ class PsSettings(ctypes.Structure):
                 ("delta", ctypes.c_double), ("M", ctypes.c_int),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("flags", ctypes.c_int),
                 ("a_cos", ctypes.c_float), ("a_l1n", ctypes.c_float), ("a_depth", ctypes.c_float),
-                ("reserved", ctypes.c_int), ("d_state", ctypes.c_void_p)]
+                ("cta_warps", ctypes.c_int), ("d_state", ctypes.c_void_p)]
 
 
 class PsStepState(ctypes.Structure):
@@ -183,7 +183,7 @@ def ps_plan_views(H, W, scene_of_view, plane_ptr, w2c, intr, tile_w, tile_h, gt_
 
 
 def make_settings(lam, delta, M=30, tile_w=16, tile_h=16, flags=0, w_min=1e-4, z_near=0.01,
-                  z_far=100.0, a_cos=5.0, a_l1n=5.0, a_depth=1.0, d_state=None) -> PsSettings:
+                  z_far=100.0, a_cos=5.0, a_l1n=5.0, a_depth=1.0, d_state=None, cta_warps=0) -> PsSettings:
     s = PsSettings()
     s.lambda_ = float(lam)
     s.w_min = float(w_min)
@@ -194,6 +194,7 @@ def make_settings(lam, delta, M=30, tile_w=16, tile_h=16, flags=0, w_min=1e-4, z
     s.tile_w, s.tile_h = int(tile_w), int(tile_h)
     s.flags = int(flags)
     s.a_cos, s.a_l1n, s.a_depth = float(a_cos), float(a_l1n), float(a_depth)
+    s.cta_warps = int(cta_warps)
     s.d_state = None if d_state is None else d_state.data_ptr()
     return s
 

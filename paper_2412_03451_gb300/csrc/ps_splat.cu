@@ -50,7 +50,19 @@ namespace {
 #endif
 constexpr int kPend = PS_KPEND;           // pending-pair buffer per pixel
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWarps = 4;                 // warps per CTA of the splat kernels
+// Warps per CTA of the splat kernels (ps_settings.cta_warps: 2, 4 or 8; 0 means 4).
+// Each warp stages 32 plane records of its tile list per shared-memory batch, so a
+// CTA holds 32 x warps records at a time; with the register budget below, 2 and 4
+// warps give the same warps per SM and 8 fewer, larger CTAs.
+constexpr int kDefaultWarps = 4;
+
+// Resident CTAs per SM the register allocation is sized for: 24 warps per SM for
+// the forward-only kernel (measured 8% faster than 20), 20 for the modes with the
+// backward, where 24 would spill.
+__host__ __device__ constexpr int min_blocks(int mode, int warps)
+{
+    return (mode == 0 ? 24 : 20) / warps;
+}
 
 // Kernel modes: forward only; backward from given dL/dD, dL/dN; or forward,
 // Eq. 14 loss and backward fused in one walk per pixel.
@@ -603,15 +615,13 @@ __device__ __forceinline__ void load_state(SplatArgs& a)
     }
 }
 
-// Forward-only launches need no stack and run 6 CTAs per SM (measured 8% faster than 5);
-// the modes with the backward stay at 5, where 6 would spill.
-template <int TW, int TH, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, MODE == kFwd ? 6 : 5) k_splat(SplatArgs a_in)
+template <int TW, int TH, int MODE, int NW>
+__global__ void __launch_bounds__(NW * 32, min_blocks(MODE, NW)) k_splat(SplatArgs a_in)
 {
     SplatArgs a = a_in;
     load_state(a);
-    __shared__ WarpStage stage[kWarps];
-    extern __shared__ int2 dyn_stk[];       // backward: [kWarps][M][32]
+    __shared__ WarpStage stage[NW];
+    extern __shared__ int2 dyn_stk[];       // backward: [NW][M][32]
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     int2* stk_warp = dyn_stk + (size_t)w * a.M * 32;
@@ -619,7 +629,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == kFwd ? 6 : 5) k_splat(Spl
     // are handed out in increasing order, so a warp meets each view in one run)
     int vcur = -1;
     float l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f;
-    const int slot = (blockIdx.x * kWarps + w) % kSlots;
+    const int slot = (blockIdx.x * NW + w) % kSlots;
     auto flush_loss = [&]() {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -919,12 +929,12 @@ struct LaunchCache {
     size_t dyn = 0;
 };
 
-template <int TW, int TH, int MODE>
+template <int TW, int TH, int MODE, int NW>
 cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool counter_zeroed)
 {
     constexpr int NS = TW * TH / 32;
     a.n_items = n_tiles * NS;
-    const size_t dyn = MODE != kFwd ? sizeof(int2) * (size_t)kWarps * M * 32 : 0;
+    const size_t dyn = MODE != kFwd ? sizeof(int2) * (size_t)NW * M * 32 : 0;
     static LaunchCache cache[8];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -933,12 +943,12 @@ cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool 
     if (c.dev != dev || c.dyn != dyn) {
         if (dyn > 0) {
             // static + dynamic shared memory above 48 KB needs the opt-in
-            e = cudaFuncSetAttribute(k_splat<TW, TH, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)dyn);
+            e = cudaFuncSetAttribute(k_splat<TW, TH, MODE, NW>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
             if (e != cudaSuccess) return e;
         }
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_splat<TW, TH, MODE>, kWarps * 32, dyn);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_splat<TW, TH, MODE, NW>, NW * 32, dyn);
         if (e != cudaSuccess) return e;
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -948,14 +958,14 @@ cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool 
         c.blocks_per_sm = (nb > 0 ? nb : 1) * sms;
     }
     int blocks = c.blocks_per_sm;
-    const int need = (a.n_items + kWarps - 1) / kWarps;
+    const int need = (a.n_items + NW - 1) / NW;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     if (!counter_zeroed) {
         e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
-    k_splat<TW, TH, MODE><<<blocks, kWarps * 32, dyn, st>>>(a);
+    k_splat<TW, TH, MODE, NW><<<blocks, NW * 32, dyn, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -973,6 +983,8 @@ ps_status check_common(const ps_frame* f, const ps_settings* s, const float* rec
     if ((s->flags & PS_GAUSSIAN) && (!(s->delta > 0.0) || (s->flags & PS_HARD))) return PS_ERR_ARG;
     const int tw = s->tile_w, th = s->tile_h;
     if (!((tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8))) return PS_ERR_ARG;
+    const int nw = s->cta_warps;
+    if (!(nw == 0 || nw == 2 || nw == 4 || nw == 8)) return PS_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(rec) & 15) return PS_ERR_ARG;
     return PS_OK;
 }
@@ -991,13 +1003,23 @@ SplatConst make_const(const ps_settings* s)
     return c;
 }
 
+template <int MODE, int NW>
+cudaError_t dispatch_tile(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
+                          bool counter_zeroed)
+{
+    if (s->tile_w == 16) return launch_splat<16, 16, MODE, NW>(a, n_tiles, s->M, st, counter_zeroed);
+    if (s->tile_w == 8) return launch_splat<8, 8, MODE, NW>(a, n_tiles, s->M, st, counter_zeroed);
+    return launch_splat<32, 8, MODE, NW>(a, n_tiles, s->M, st, counter_zeroed);
+}
+
 template <int MODE>
 cudaError_t dispatch(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
                      bool counter_zeroed = false)
 {
-    if (s->tile_w == 16) return launch_splat<16, 16, MODE>(a, n_tiles, s->M, st, counter_zeroed);
-    if (s->tile_w == 8) return launch_splat<8, 8, MODE>(a, n_tiles, s->M, st, counter_zeroed);
-    return launch_splat<32, 8, MODE>(a, n_tiles, s->M, st, counter_zeroed);
+    const int nw = s->cta_warps ? s->cta_warps : kDefaultWarps;
+    if (nw == 2) return dispatch_tile<MODE, 2>(a, s, n_tiles, st, counter_zeroed);
+    if (nw == 8) return dispatch_tile<MODE, 8>(a, s, n_tiles, st, counter_zeroed);
+    return dispatch_tile<MODE, 4>(a, s, n_tiles, st, counter_zeroed);
 }
 
 template <int TW, int TH>

@@ -43,7 +43,7 @@ class Renderer:
     scene plane counts) and runs the libps calls on the current stream."""
 
     def __init__(self, H, W, scene_of_view, plane_ptr, tile=(16, 16), M=30, capacity=None,
-                 device="cuda", flags=0):
+                 device="cuda", flags=0, warps=0):
         self.device = torch.device(device)
         self.H = np.asarray(H, np.int32).reshape(-1)
         self.W = np.asarray(W, np.int32).reshape(-1)
@@ -54,6 +54,7 @@ class Renderer:
         self.tile = (int(tile[0]), int(tile[1]))
         self.M = int(M)
         self.flags = int(flags)
+        self.warps = int(warps)       # warps per CTA of the splat kernels (0: the library default)
         # plan once with identity cameras to learn the totals
         eye = np.tile(np.concatenate([np.eye(3), np.zeros((3, 1))], 1).astype(np.float32),
                       (self.V, 1, 1))
@@ -145,7 +146,8 @@ class Renderer:
         else:
             delta = B.filter_margin(float(np.float32(lam)))
         self.settings = B.make_settings(lam, delta, M=self.M, tile_w=self.tile[0],
-                                        tile_h=self.tile[1], flags=fl, d_state=d_state)
+                                        tile_h=self.tile[1], flags=fl, d_state=d_state,
+                                        cta_warps=self.warps)
         return self.settings
 
     def planes_struct(self, flat: torch.Tensor) -> B.PsPlanes:
@@ -314,13 +316,22 @@ class Fitter:
                                   plane_scale=self.split_scale[batch or 0])
 
     # -- captured CUDA graphs ------------------------------------------------------
-    def enable_graphs(self, n_iters: int, batches, gt_slices):
+    def enable_graphs(self, n_iters: int, batches, gt_slices, host_stream=None):
         """Captures one CUDA graph per camera batch of a full optimisation step
         (schedule advance, projection, binning, fused splat/loss/backward, Adam),
         with lambda, the binning margin and Adam's bias corrections read from a
         device-side per-iteration schedule, so that replaying graph s % n_batches
         at iteration s reproduces the eager step.  Capacity must already suffice
-        (checked after replays through the status word)."""
+        (checked after replays through the status word).
+
+        host_stream (optional) streams the supervision from pinned host memory:
+        a dict with host_depth [n] and host_normal [n, 3] (pinned CPU tensors),
+        offsets (the first pixel of each batch's supervision in them) and
+        sums_host (pinned f64 [n_batches, V, 4]).  gt_slices are then two device
+        buffer pairs used alternately (batch b reads gt_slices[b]; consecutive
+        batches must use different buffers), and the graph of batch b also copies
+        the next batch's supervision into the other buffer on a parallel branch
+        (overlapping the step) and the step's loss sums to sums_host[b]."""
         dev = self.flat.device
         sched = B.step_schedule(n_iters, lam_offset=self.lam_offset)
         self.d_sched = torch.frombuffer(bytearray(sched), dtype=torch.uint8).to(dev)
@@ -344,11 +355,25 @@ class Fitter:
             self.d_iter.fill_(saved[3])
             if saved[4] is not None:
                 self.split_acc.copy_(saved[4])
+        side = torch.cuda.Stream(device=dev) if host_stream is not None else None
         for i, (b, (gd, gn)) in enumerate(zip(batches, gt_slices)):
             r.select(b)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                if host_stream is not None:
+                    j = (i + 1) % len(batches)
+                    nd, nn = gt_slices[j]
+                    if nd.data_ptr() == gd.data_ptr():
+                        raise ValueError("consecutive batches must read different supervision buffers")
+                    o, m = host_stream["offsets"][j], nd.numel()
+                    side.wait_stream(stream)
+                    with torch.cuda.stream(side):
+                        nd.copy_(host_stream["host_depth"][o:o + m], non_blocking=True)
+                        nn.copy_(host_stream["host_normal"][o:o + m], non_blocking=True)
                 self._graph_body(gd, gn, self.graph_sums[i], b)
+                if host_stream is not None:
+                    stream.wait_stream(side)
+                    host_stream["sums_host"][i].copy_(self.graph_sums[i], non_blocking=True)
             self.graphs.append(g)
         torch.cuda.synchronize()
 

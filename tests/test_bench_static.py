@@ -45,24 +45,27 @@ def test_roofline_entry_arithmetic():
     assert abs(r["other_roofs"]["mufu"]["peak"] - 5.034) < 1e-3
     # profile-derived roofs apply only to the source they were measured on
     assert r["traffic"] is None and "issue" not in r["other_roofs"] and "hbm" not in r["other_roofs"]
-    r2 = bench.roofline_entry((5e8, 2e8, 1e8), {"splat_fused": [1.0] * 10}, 10,
-                              {"sm_max_mhz": 2070.0}, bench.INSTR["src_sha"], {"hbm_gbs": 6790.0})
-    assert r2["traffic"] == bench.TRAFFIC["splat_fused"]
-    assert abs(r2["other_roofs"]["issue"]["achieved"] - bench.INSTR["splat_fused"] / 1e6) < 0.06
-    assert abs(r2["other_roofs"]["hbm"]["achieved"] - bench.TRAFFIC["splat_fused"] / 1e6) < 0.1
+    for regime in (0, 1000):
+        cap = bench.CAPTURES["splat_fused"][regime]
+        r2 = bench.roofline_entry((5e8, 2e8, 1e8), {"splat_fused": [1.0] * 10}, 10, {"sm_max_mhz": 2070.0},
+                                  bench.CAPTURES["src_sha"], {"hbm_gbs": 6790.0}, regime=regime)
+        assert r2["traffic"] == cap["dram_bytes"]
+        assert abs(r2["other_roofs"]["issue"]["achieved"] - cap["warp_instructions"] / 1e6) < 0.06
+        assert abs(r2["other_roofs"]["hbm"]["achieved"] - cap["dram_bytes"] / 1e6) < 0.1
+    # a regime without a capture reports no traffic
+    r3 = bench.roofline_entry((5e8, 2e8, 1e8), {"splat_fused": [1.0] * 10}, 10, {"sm_max_mhz": 2070.0},
+                              bench.CAPTURES["src_sha"], {"hbm_gbs": 6790.0}, regime=4000)
+    assert r3["traffic"] is None
 
 
 
-def test_common_room_times_compare_only_rooms_every_arm_reaches():
+def test_common_rooms_are_the_rooms_every_arm_reaches():
     import bench
     arms = {"plain": [(100, 50.0), (200, 80.0), None, (400, 10.0)],
             "batched": [(110, 40.0), (210, 60.0), (300, 90.0), (380, 95.0)],
             "batched_learned": [(50, 20.0), (100, 35.0), (120, 40.0), None]}
-    out = bench.common_room_times(arms, learned_extra_s=0.005)
+    common, out = bench.common_rooms(arms)
+    assert common == [0, 1]
     assert out["rooms"] == 2 and out["reached"] == {"plain": 3, "batched": 4, "batched_learned": 3}
-    # room by room: the sum of the common rooms' fit times; batched: the clock when the last is done
-    assert out["plain"]["seconds"] == 0.13 and out["batched"]["seconds"] == 0.06
-    assert out["batched_learned"]["seconds"] == 0.04          # 35 ms + 5 ms of inference
-    assert out["plain"]["mean_iterations"] == 150.0
-    assert out["batched"]["speedup_vs_plain"] == round(0.13 / 0.06, 3)
-    assert bench.common_room_times({"plain": [None], "batched": [(1, 1.0)]})["rooms"] == 0
+    assert out["plain"]["mean_iterations"] == 150.0 and out["batched_learned"]["mean_iterations"] == 75.0
+    assert bench.common_rooms({"plain": [None], "batched": [(1, 1.0)]})[1]["rooms"] == 0

@@ -616,3 +616,84 @@ def test_m_extremes_forward_backward(M):
     for k, ref in (("g_center", gc), ("g_quat", gq), ("g_radii", gr)):
         nbad, worst = grad_errors(g[k], ref)
         assert nbad == 0, (M, k, nbad, worst)
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16)])
+def test_warps_per_cta_do_not_change_results(tile):
+    # the launch shape the autotuner picks (2, 4 or 8 warps per CTA: 64, 128 or 256 plane
+    # records staged per shared-memory batch) changes speed only: maps and loss gradients are
+    # identical, plane gradients equal up to the order of float atomics
+    import torch
+    from paper_2412_03451_gb300 import splat as SP
+    room, init = tiny_init(2)
+    cams = room.cams
+    D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, cams.w2c, cams.intr, cams.H, cams.W)
+    gd = torch.from_numpy(D.astype(np.float32).reshape(-1)).cuda()
+    gn = torch.from_numpy(N.astype(np.float32).reshape(-1, 3)).cuda()
+    out = {}
+    for warps in (2, 4, 8):
+        V = cams.V
+        r = SP.Renderer([cams.H] * V, [cams.W] * V, [0] * V, [0, init.K], tile=tile, warps=warps)
+        r.set_cameras(cams.w2c, cams.intr)
+        flat = SP.planes_to_flat(init.center, init.quat, init.radii, "cuda")
+        r.ensure_capacity(flat, 20.0)
+        r.status.zero_()
+        r.project_bin(flat, 20.0)
+        g = torch.zeros_like(flat)
+        r.fused(flat, g, gd, gn, write_maps=True)
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        out[warps] = (r.depth.cpu().numpy(), r.normal.cpu().numpy(), r.dLdD.cpu().numpy(),
+                      r.view_sums.cpu().numpy(), g.cpu().numpy())
+    for warps in (2, 8):
+        a, b = out[warps], out[4]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+        assert np.allclose(a[3], b[3], rtol=1e-6)
+        assert np.linalg.norm(a[4] - b[4]) <= 1e-5 * np.linalg.norm(b[4]) + 1e-6
+
+
+def test_graphs_streaming_supervision_from_host_match_resident():
+    # Fitter.enable_graphs(host_stream=...): each step's graph copies the next batch's supervision
+    # from pinned host memory into the other of two device buffers and the step's loss sums back;
+    # the fit must be the one that reads resident supervision
+    import torch
+    from paper_2412_03451_gb300 import splat as SP
+    room, init = tiny_init()
+    cams = room.cams
+    V, H, W = cams.V, cams.H, cams.W
+    D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, cams.w2c, cams.intr, H, W)
+    gd = torch.from_numpy(D.astype(np.float32).reshape(-1)).cuda()
+    gn = torch.from_numpy(N.astype(np.float32).reshape(-1, 3)).cuda()
+    half = V // 2
+    n = half * H * W
+
+    def make():
+        r = SP.Renderer([H] * half, [W] * half, [0] * half, [0, init.K], capacity=1 << 15)
+        r.preplan([cams.w2c[:half], cams.w2c[half:]], [cams.intr[:half], cams.intr[half:]])
+        flat = SP.planes_to_flat(init.center, init.quat, init.radii, "cuda")
+        return r, SP.Fitter(r, flat)
+
+    r1, f1 = make()
+    f1.enable_graphs(20, [0, 1], [(gd[:n], gn[:n]), (gd[n:], gn[n:])])
+    ref = []
+    for s in range(5):
+        ref.append(f1.replay(s % 2).clone())
+    torch.cuda.synchronize()
+    r2, f2 = make()
+    hd, hn = gd.cpu().pin_memory(), gn.cpu().pin_memory()
+    sums_host = torch.zeros((2, half, 4), dtype=torch.float64).pin_memory()
+    bufs = [(torch.zeros(n, device="cuda"), torch.zeros((n, 3), device="cuda")) for _ in range(2)]
+    f2.enable_graphs(20, [0, 1], bufs, host_stream={"host_depth": hd, "host_normal": hn,
+                                                    "offsets": [0, n], "sums_host": sums_host})
+    bufs[0][0].copy_(hd[:n]); bufs[0][1].copy_(hn[:n])
+    got = []
+    for s in range(5):
+        f2.replay(s % 2)
+        torch.cuda.synchronize()
+        got.append(sums_host[s % 2].clone())
+    # the same kernels on the same data: equal up to the order of float atomics, which Adam's
+    # per-coordinate normalisation can turn into at most an lr-sized step per iteration
+    for a, b in zip(got, ref):
+        assert torch.allclose(a, b.cpu(), rtol=1e-5), (a, b)
+    d = (f2.flat - f1.flat).abs()
+    assert float(d.max()) <= 5 * 1.1e-3 and float(d.median()) <= 1e-6

@@ -21,15 +21,55 @@ def test_autotune_key_buckets_planes_and_sorts_sizes():
 def test_autotune_answers_from_the_file_cache_without_timing(tmp_path, monkeypatch):
     key = AT._key([(480, 640)], 8, 3000)
     path = tmp_path / "tune.json"
-    path.write_text(json.dumps({key: {"tile": [32, 8], "ms": {"32x8": 1.0}}}))
+    path.write_text(json.dumps({key: {"tile": [32, 8], "warps": 2, "ms": {"32x8/w2": 1.0}}}))
     monkeypatch.setenv("PS_AUTOTUNE_CACHE", str(path))
     monkeypatch.setattr(AT, "_cache", {})
 
-    def no_renderer(tile):
+    def no_renderer(tile, warps):
         raise AssertionError("a cached key must not be timed")
 
-    tile, ms = AT.pick_tile(no_renderer, None, None, None, 20.0, key)
-    assert tile == (32, 8) and ms == {"32x8": 1.0}
+    tile, warps, ms = AT.pick_launch(no_renderer, None, None, None, 20.0, key)
+    assert tile == (32, 8) and warps == 2 and ms == {"32x8/w2": 1.0}
+
+
+def test_autotune_searches_tiles_and_warps(monkeypatch):
+    # every (tile, warps) pair is timed on the caller's renderer and the fastest is kept
+    monkeypatch.setattr(AT, "_cache", {})
+    monkeypatch.delenv("PS_AUTOTUNE_CACHE", raising=False)
+    seen = []
+    t = {"now": 0.0}
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            self.at = 0.0
+
+        def record(self):
+            self.at = t["now"]
+
+        def elapsed_time(self, other):
+            return other.at - self.at
+
+    class FakeRenderer:
+        def __init__(self, tile, warps):
+            self.cost = 1.0 + (tile != (8, 8)) + 0.5 * (warps != 2)
+            seen.append((tile, warps))
+
+        def ensure_capacity(self, *a, **k):
+            return False
+
+        def project_bin(self, *a):
+            t["now"] += self.cost
+
+        def fused(self, *a):
+            pass
+
+    monkeypatch.setattr(AT.torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(AT.torch.cuda, "synchronize", lambda: None)
+    flat = torch.zeros(11)
+    tile, warps, ms = AT.pick_launch(FakeRenderer, flat, None, None, 20.0, "k")
+    assert (tile, warps) == ((8, 8), 2)
+    assert sorted(seen) == sorted((tl, w) for tl in AT.TILES for w in AT.WARPS)
+    assert set(ms) == {"%dx%d/w%d" % (tl[0], tl[1], w) for tl in AT.TILES for w in AT.WARPS}
 
 
 def test_scene_generators_are_seeded():
