@@ -113,17 +113,19 @@ def patch_targets(ids, depth, intr, w2c, planes_q, y0, x0, z_ref, min_pix=64):
     return t
 
 
-def make_dataset(n_rooms=32, seed0=5000, views=16, iters=1500, device="cuda", log=print, chunk=48):
+def make_dataset(n_rooms=32, seed0=5000, views=16, iters=1500, device="cuda", log=print, chunk=48,
+                 cut_views=None):
     """Fits n_rooms rooms with the method (batched, chunk rooms at a time) and
-    cuts their views into patches.  Returns (X [N, 64, 64, 4] float32,
-    T [N, 8, 12] float32)."""
+    cuts their views into patches (all views, or cut_views of them spread over
+    the trajectory: more rooms for the same number of patches).  Returns
+    (X [N, 64, 64, 4] float16, T [N, 8, 12] float32)."""
     t0 = time.time()
     rng = np.random.default_rng(seed0)
     Ks = [int(rng.integers(500, 3001)) for _ in range(n_rooms)]
     Xs, Ts = [], []
     for c0 in range(0, n_rooms, chunk):
         idx = list(range(c0, min(c0 + chunk, n_rooms)))
-        _cut_patches(idx, Ks, seed0, views, iters, device, Xs, Ts)
+        _cut_patches(idx, Ks, seed0, views, iters, device, Xs, Ts, cut_views)
         log("seed data: %d of %d rooms, %d patches, %.1f s" % (idx[-1] + 1, n_rooms, len(Xs),
                                                              time.time() - t0))
     X, T = np.stack(Xs), np.stack(Ts)
@@ -132,7 +134,7 @@ def make_dataset(n_rooms=32, seed0=5000, views=16, iters=1500, device="cuda", lo
     return X, T
 
 
-def _cut_patches(idx, Ks, seed0, views, iters, device, Xs, Ts):
+def _cut_patches(idx, Ks, seed0, views, iters, device, Xs, Ts, cut_views=None):
     rooms, inits = [], []
     for i in idx:
         room = S.large_room(seed0 + i, n_rect=2000, n_views=views)
@@ -154,12 +156,13 @@ def _cut_patches(idx, Ks, seed0, views, iters, device, Xs, Ts):
         n = c.V * c.H * c.W
         gd = ss.gt_depth[off:off + n].cpu().numpy().reshape(c.V, c.H, c.W)
         gn = ss.gt_normal[off:off + n].cpu().numpy().reshape(c.V, c.H, c.W, 3)
-        for v in range(c.V):
+        step = max(1, c.V // cut_views) if cut_views else 1
+        for v in range(0, c.V, step):
             for (y0, x0) in patch_grid(c.H, c.W):
                 x, z_ref = patch_inputs(gd[v], gn[v], y0, x0)
                 if x is None:
                     continue
-                Xs.append(x)
+                Xs.append(x.astype(np.float16))
                 Ts.append(patch_targets(ids[v], gd[v], c.intr[v], c.w2c[v], q, y0, x0, z_ref))
         del r
     del ss
@@ -361,7 +364,7 @@ def evaluate(net, n_rooms=8, seed0=9000, planes=3000, iters=5000, device="cuda",
                    ss_p.gt_normal[:c0.H * c0.W].view(1, c0.H, c0.W, 3), [0], seed=seed0, max_planes=100)
     torch.cuda.synchronize()
     for var in variants:
-        opts = {k: v for k, v in var.items() if k not in ("name", "lam_offset")}
+        opts = {k: v for k, v in var.items() if k not in ("name", "lam_offset", "net")}
         learned, infer_ms, n_l, n_f = [], 0.0, 0, 0
         for i, room in enumerate(rooms):
             c = room.cams
@@ -372,7 +375,7 @@ def evaluate(net, n_rooms=8, seed0=9000, planes=3000, iters=5000, device="cuda",
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            P, nl, nf = propose_planes(net, room, gd, gn, range(c.V), seed=seed0 + 200 + i,
+            P, nl, nf = propose_planes(var.get("net", net), room, gd, gn, range(c.V), seed=seed0 + 200 + i,
                                        max_planes=planes, **opts)
             e1.record()
             torch.cuda.synchronize()
@@ -384,7 +387,7 @@ def evaluate(net, n_rooms=8, seed0=9000, planes=3000, iters=5000, device="cuda",
         lo = var.get("lam_offset", 0)
         ll = [BT.fit_until(ss_l, [s], max_iters=iters, lam_offset=lo) for s in range(n_rooms)]
         lb = BT.fit_until(ss_l, list(range(n_rooms)), max_iters=iters, lam_offset=lo)
-        r = {"name": var.get("name"), "options": {k: v for k, v in var.items() if k != "name"},
+        r = {"name": var.get("name"), "options": {k: v for k, v in var.items() if k not in ("name", "net")},
              "planes_mean": round(float(np.mean([p.K for p in learned])), 1),
              "learned_seeds": n_l, "fallback_seeds": n_f, "inference_s": round(infer_ms / 1e3, 4),
              "one_by_one_s": round(sum(p["gpu_ms"] for p in ll) / 1e3 + infer_ms / 1e3, 3),
@@ -419,14 +422,21 @@ if __name__ == "__main__":
     from paper_2412_03451_gb300 import _build
     _build.build()
     n_rooms = int(os.environ.get("PS_SEED_ROOMS", "32"))
+    out = os.environ.get("PS_SEED_OUT", WEIGHTS)
+    previous = load()        # the weights in place before this run, if any
     if os.environ.get("PS_SEED_EVAL_ONLY", "0") == "1":
-        net = load()
+        net = previous
     else:
-        X, T = make_dataset(n_rooms=n_rooms)
+        cut = int(os.environ.get("PS_SEED_CUT_VIEWS", "0")) or None
+        X, T = make_dataset(n_rooms=n_rooms, cut_views=cut)
         net, hist = train(X, T, steps=int(os.environ.get("PS_SEED_STEPS", "3000")))
-        save(net, meta={"history": json.dumps(hist), "rooms": n_rooms, "patches": len(X)})
+        save(net, path=out, meta={"history": json.dumps(hist), "rooms": n_rooms, "patches": len(X)})
         print(json.dumps({"patches": len(X), "history": hist[-3:]}), flush=True)
     if os.environ.get("PS_SEED_EVAL", "1") == "1":
         variants = json.loads(os.environ.get("PS_SEED_VARIANTS", "null"))
+        if variants is None:
+            variants = [dict(name="learned", lam_offset=LEARNED_LAM_OFFSET)]
+            if previous is not None and previous is not net and os.environ.get("PS_SEED_COMPARE", "0") == "1":
+                variants.append(dict(name="previous weights", lam_offset=LEARNED_LAM_OFFSET, net=previous))
         ev = evaluate(net, n_rooms=int(os.environ.get("PS_SEED_EVAL_ROOMS", "8")), variants=variants)
         print(json.dumps(ev), flush=True)
