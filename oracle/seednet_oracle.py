@@ -88,14 +88,21 @@ def forward(params, x, cin=4, ch=64, out=96, bf16_acts=True):
     return o, dict(layers=layers, Wfc=Wfc, h=h, cache=cache, last=a)
 
 
-def backward(params, fwd_cache, dout, cin=4, ch=64, out=96):
-    """Gradient of sum(dout * out) w.r.t. the flat parameters."""
+def backward(params, fwd_cache, dout, cin=4, ch=64, out=96, bf16_grads=False):
+    """Gradient of sum(dout * out) w.r.t. the flat parameters.
+
+    With bf16_grads, the upstream gradient of every matrix product (dout, and
+    each layer's gradient behind its ReLU) is rounded to bf16 before it enters
+    the product, as on a tensor-core path whose operands are bf16; the bias
+    gradients sum the unrounded values.  Arithmetic stays FP64."""
     c = fwd_cache
     layers, Wfc, h = c["layers"], c["Wfc"], c["h"]
+    rnd = bf16_round if bf16_grads else (lambda a: a)
     grads = []
-    gWfc = dout.T @ h
+    dout_m = rnd(dout)
+    gWfc = dout_m.T @ h
     gbfc = dout.sum(axis=0)
-    dh = dout @ Wfc
+    dh = dout_m @ Wfc
     last = c["last"]
     Bn, Ho, Wo, _ = last.shape
     dy = np.repeat(dh[:, None, :] / (Ho * Wo), Ho * Wo, axis=1).reshape(-1, ch)
@@ -104,11 +111,12 @@ def backward(params, fwd_cache, dout, cin=4, ch=64, out=96):
         W, b = layers[i]
         shape, A, y = c["cache"][i]
         dz = dy * (y > 0)
-        gW = dz.T @ A
+        dz_m = rnd(dz)
+        gW = dz_m.T @ A
         gb = dz.sum(axis=0)
         conv_grads.append((gW, gb))
         if i > 0:
-            dA = dz @ W
+            dA = dz_m @ W
             dy = col2im(dA, shape).reshape(-1, shape[-1])
     conv_grads.reverse()
     for gW, gb in conv_grads:

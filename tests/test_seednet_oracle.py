@@ -75,6 +75,32 @@ def test_backward_matches_central_differences():
         assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-7), i
 
 
+def test_backward_with_bf16_gradient_operands():
+    # rounding the products' upstream gradients to bf16 (unit roundoff 2^-8) moves each
+    # parameter block by a few roundoffs of the exact (finite-difference-pinned) gradient;
+    # with a bf16-exact dout the linear layer's gradients do not move at all
+    params, x, cin, ch, out = _tiny(5)
+    rng = np.random.default_rng(6)
+    dout = SO.bf16_round(rng.normal(size=(2, out)))
+    o, cache = SO.forward(params, x, cin, ch, out, bf16_acts=False)
+    g = SO.backward(params, cache, dout, cin, ch, out)
+    gr = SO.backward(params, cache, dout, cin, ch, out, bf16_grads=True)
+    n_fc = out * ch + out
+    assert np.array_equal(g[-n_fc:], gr[-n_fc:])
+    o_ = 0
+    c = cin
+    moved = 0
+    for _ in range(4):
+        for n in (ch * 9 * c, ch):
+            a, b = gr[o_:o_ + n], g[o_:o_ + n]
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            assert rel < 4 * 2.0 ** -8, rel
+            moved += rel > 0
+            o_ += n
+        c = ch
+    assert moved >= 4
+
+
 def test_seed_loss_gradient_and_closed_forms():
     rng = np.random.default_rng(4)
     Bn, S = 3, 8
