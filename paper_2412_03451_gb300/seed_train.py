@@ -17,8 +17,9 @@ random surface point of the patch with random orientation).
 
 python -m paper_2412_03451_gb300.seed_train writes the trained weights and
 scores them on held-out rooms.  The committed weights came from
-PS_SEED_ROOMS=200 PS_SEED_STEPS=8000 PS_SEED_EVAL_ROOMS=100 (about 11 minutes
-on one GB300); PS_SEED_EVAL_ONLY=1 scores the committed weights alone.
+PS_SEED_ROOMS=2000 PS_SEED_CUT_VIEWS=4 PS_SEED_STEPS=16000 PS_SEED_EVAL_ROOMS=100
+(about 35 minutes on one GB300: 29 fitting the 2,000 rooms, 2 training);
+PS_SEED_EVAL_ONLY=1 scores the committed weights alone.
 """
 from __future__ import annotations
 
