@@ -1,8 +1,17 @@
 """Seed network on the GPU (tcgen05 GEMMs + libps kernels) against the FP64 oracle.
 
-The oracle stores activations in bf16 like the kernels and computes in FP64;
-remaining differences come from FP32 accumulation order and the bf16 copies of
-the gradients that feed the backward GEMMs."""
+The oracle stores activations in bf16 like the kernels, rounds the gradients
+that enter the backward matrix products to bf16 as the kernels do, and computes
+in FP64.  What remains is FP32 accumulation and the bf16 roundings that its
+small differences send the other way.  A bf16 rounding moves a value by at most
+u = 2^-9 of itself, and a value crosses at most four of them (one per layer) on
+its way to the output or, backwards, to the first layer's weights: the bar is
+4u = 7.8e-3 relative per block, the first-order effect of one unmatched rounding
+per layer.  Measured: output 3.7e-4, gradient blocks 4e-4 (linear layer) to
+2.0e-3 (first layer, the end of the longest chain), 1 - cosine <= 2e-6 (against
+the oracle without its rounding of the gradients: 1.4e-3 to 4.1e-3).  Wrong
+operands, layouts or layers give errors of order one."""
+REL_BAR = 4 * 2.0 ** -9
 import numpy as np
 import pytest
 
@@ -47,7 +56,7 @@ def test_forward_backward_and_loss_match_oracle(torch):
     params = net.params.cpu().numpy().astype(np.float64)
     o_ref, cache = SO.forward(params, x)
     assert int(net.err.item()) == 0
-    assert _rel(out.cpu().numpy(), o_ref) < 1e-2
+    assert _rel(out.cpu().numpy(), o_ref) < REL_BAR
     # backward with one upstream gradient on both sides
     rng = np.random.default_rng(6)
     dout = rng.normal(size=o_ref.shape).astype(np.float32)
@@ -55,13 +64,13 @@ def test_forward_backward_and_loss_match_oracle(torch):
     net.backward(torch.from_numpy(dout).cuda())
     torch.cuda.synchronize()
     g = net.grad.cpu().numpy().astype(np.float64)
-    g_ref = SO.backward(params, cache, dout.astype(np.float64))
+    g_ref = SO.backward(params, cache, dout.astype(np.float64), bf16_grads=True)
     o = 0
     for kind, shp in SN.param_shapes():
         n = int(np.prod(shp))
         a, b = g[o:o + n], g_ref[o:o + n]
         cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
-        assert cos > 0.999 and _rel(a, b) < 5e-2, (kind, shp, cos, _rel(a, b))
+        assert cos > 0.99999 and _rel(a, b) < REL_BAR, (kind, shp, cos, _rel(a, b))
         o += n
     # set loss on the GPU's own outputs
     t = torch.from_numpy(tgt).cuda()
