@@ -173,6 +173,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ttd", type=int, default=0,
                     help="also fit up to this many iterations and report time to depth error <= 2 cm")
+    ap.add_argument("--fit-iters", type=int, default=2000,
+                    help="also run the single-scene fit of the benchmark room for this many iterations "
+                         "from its initial planes, replayed from graphs (0: skip)")
     ap.add_argument("--start-ite", type=int, default=0, help="iteration (lambda schedule) to start at")
     ap.add_argument("--no-graphs", action="store_true", help="time eager launches instead of graph replays")
     ap.add_argument("--regimes", default="1000,2000,4000",
@@ -489,6 +492,8 @@ def run_ours(args, rank, world, local_rank):
     cps = [int(x) for x in args.regimes.split(",") if x.strip()]
     if cps:
         result["regimes"] = run_regimes(wl, cps, args.steps, clocks, measured_peaks())
+    if args.fit_iters > 0:
+        result["fit"] = run_fit(wl, args.fit_iters)
     if args.ttd:
         result["time_to_2cm"] = run_ttd(wl, args.ttd)
     if args.batched > 0:
@@ -699,7 +704,8 @@ def run_regimes(wl, checkpoints, K, clocks, peaks):
     room (Eq. 10 sharpens the weight: the lists shrink and more pairs are opaque).
     The room is fitted from its initial planes with eager steps; at each checkpoint
     K more steps are timed with per-stage CUDA events (L2 flushed between steps)
-    and their work counted exactly."""
+    and their work counted exactly, then K more are replayed from CUDA graphs
+    captured there (the step time a fit sees at that point)."""
     import torch
     wl.reset(0)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=wl.flat.device)
@@ -721,12 +727,71 @@ def run_regimes(wl, checkpoints, K, clocks, peaks):
         if int(wl.r.status.item()) & CAPACITY_BIT:
             raise RuntimeError("tile-list capacity overflow in the regime measurement")
         vs = wl.r.view_sums.cpu().numpy()
+        # the next K steps replayed from graphs captured at this point of the fit
+        for b in range(nb):
+            wl.grow_if_needed(wl.fit.ite + b)
+        wl.fit.enable_graphs(wl.fit.ite + K + 8, list(range(nb)), [wl.gt_slice(b) for b in range(nb)])
+        wl.r.status.zero_()
+        g_ms = statistics.mean(time_replays(wl, wl.fit.ite, K, flush))
+        if int(wl.r.status.item()) & CAPACITY_BIT:
+            raise RuntimeError("tile-list capacity overflow in the regime measurement")
         out.append({"iteration": first, "lambda": round(wl.B.lambda_schedule(first), 3),
+                    "ms_per_step_graph": round(g_ms, 4),
+                    "mpixel_views_per_s_graph": round(VIEWS_PER_STEP * H * W / g_ms / 1e3, 1),
                     "ms_per_step_eager": round(statistics.mean(per_step), 4),
                     "stage_ms": {k: round(statistics.mean(v), 4) for k, v in stages.items()},
                     "mean_abs_depth_err_m": round(float(vs[:, 2].sum() / max(vs[:, 3].sum(), 1.0)), 5),
                     "roofline": roofline_entry(counts, stages, K, clocks, src_hash(), peaks, regime=cp)})
     return out
+
+
+def depth_error_all_views(wl):
+    """Mean |D - D*| over the supervised pixels of all views (forward-only render)."""
+    from paper_2412_03451_gb300 import splat as SP
+    ev = SP.Renderer([H] * N_VIEWS, [W] * N_VIEWS, [0] * N_VIEWS, [0, N_INIT],
+                     tile=wl.r.tile, device=wl.flat.device)
+    ev.set_cameras(wl.room.cams.w2c, wl.room.cams.intr)
+    lam = SP.B.lambda_schedule(wl.fit.ite)
+    ev.ensure_capacity(wl.flat, lam)
+    ev.forward(wl.flat, lam, alpha=False)
+    valid = wl.gt_depth > 0
+    return float((ev.depth - wl.gt_depth).abs()[valid].mean().item())
+
+
+def run_fit(wl, n_iters):
+    """The single-scene fit of the benchmark room as a user runs it: n_iters
+    optimisation steps from the initial planes (Eq. 10 from iteration 0), each
+    replayed from its camera batch's CUDA graph, timed by CUDA events around the
+    whole fit (no L2 flush).  Tile-list capacity is sized before the fit with
+    headroom; if the status word reports an overflow the fit is run again with
+    more room.  Reports the mean depth error over all views after the fit."""
+    import torch
+    nb = N_VIEWS // VIEWS_PER_STEP
+    for headroom in (1.6, 2.5, 4.0):
+        wl.reset(0)
+        for b in range(nb):
+            wl.r.select(b)
+            wl.r.ensure_capacity(wl.flat, wl.B.lambda_schedule(0), headroom=headroom)
+        wl.fit.enable_graphs(n_iters + 8, list(range(nb)), [wl.gt_slice(b) for b in range(nb)])
+        wl.r.status.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record()
+        for s in range(n_iters):
+            wl.fit.replay(s % nb)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if not int(wl.r.status.item()) & CAPACITY_BIT:
+            ms = e0.elapsed_time(e1)
+            return {"iterations": n_iters, "device_s": round(ms / 1e3, 4), "wall_s": round(wall, 4),
+                    "ms_per_step": round(ms / n_iters, 4),
+                    "mpixel_views_per_s": round(VIEWS_PER_STEP * H * W * n_iters / ms / 1e3, 1),
+                    "capacity_headroom": headroom,
+                    "depth_err_m_after": round(depth_error_all_views(wl), 5)}
+    raise RuntimeError("tile-list capacity overflow in the single-scene fit")
 
 
 def run_ttd(wl, max_iters):

@@ -35,8 +35,8 @@
 //   3. scatter: one thread per pair writes its record id and entry key into a
 //      slot of its tile (unordered, via per-tile cursors);
 //   4. sort: each tile's slots by (key, record id): one warp per tile sorts up
-//      to 64 entries in registers and up to kWarpSortCap in its slice of shared
-//      memory (bitonic networks); persistent CTAs take the longer lists
+//      to kWarpSortCap entries in registers (a bitonic network over 1, 2, 4 or
+//      8 keys per lane); persistent CTAs take the longer lists
 //      (bitonic up to kSortCap entries, an O(n^2) rank sort beyond).
 // Every pair gets its own thread, so a plane covering a thousand tiles costs
 // no more latency than one covering a single tile.
@@ -47,7 +47,7 @@ using namespace ps;
 namespace {
 
 constexpr int kSortCap = 4096;     // entries sorted in shared memory by a CTA (32 KB of u64)
-constexpr int kWarpSortCap = 256;  // entries sorted by one warp (2 KB of u64 per warp: 8 blocks per SM)
+constexpr int kWarpSortCap = 256;  // entries sorted by one warp, in registers (8 per lane)
 constexpr int kSortWarps = 8;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 9;      // elements per thread per scan tile (odd: a thread's run
@@ -280,8 +280,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_one(ScanJob j0, ScanJob j
     __shared__ long long s_warp[32];
     const ScanJob& a = blockIdx.x == 0 ? j0 : j1;
     const int n = a.n;
-#pragma unroll 8
-    for (int j = threadIdx.x; j < n; j += kScanThreads) s_all[j] = a.in[j];
+    // 16-byte loads where the input allows them: fewer rounds of load latency
+    const int n4 = (reinterpret_cast<uintptr_t>(a.in) & 15) == 0 ? n >> 2 : 0;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < n4; j += kScanThreads)
+        reinterpret_cast<int4*>(s_all)[j] = __ldg(reinterpret_cast<const int4*>(a.in) + j);
+    for (int j = 4 * n4 + threadIdx.x; j < n; j += kScanThreads) s_all[j] = a.in[j];
     __syncthreads();
     // contiguous runs of an odd length: the runs of a warp's threads start in 32
     // different banks, so the strided shared-memory passes below are conflict-free
@@ -309,11 +313,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_one(ScanJob j0, ScanJob j
     }
     __syncthreads();
     const int last = (int)(total < a.capacity ? total : a.capacity);
-    for (int j = threadIdx.x; j < n; j += kScanThreads) {
+    const bool al = ((reinterpret_cast<uintptr_t>(a.out) | reinterpret_cast<uintptr_t>(a.cursor)) & 15) == 0;
+    const int m4 = al ? n >> 2 : 0;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < m4; j += kScanThreads) {
+        const int4 x = reinterpret_cast<const int4*>(s_all)[j];
+        reinterpret_cast<int4*>(a.out)[j] = x;
+        if (a.cursor) reinterpret_cast<int4*>(a.cursor)[j] = x;
+    }
+    for (int j = 4 * m4 + threadIdx.x; j < n; j += kScanThreads) {
         const int x = s_all[j];
         a.out[j] = x;
         if (a.cursor) a.cursor[j] = x;
-        if (a.chunk_first) {
+    }
+    if (a.chunk_first) {
+        for (int j = threadIdx.x; j < n; j += kScanThreads) {
+            const int x = s_all[j];
             const long long hi = j + 1 < n ? s_all[j + 1] : last;
             for (long long c = ((long long)x + kPairBlock - 1) / kPairBlock;
                  c < a.n_chunk && c * kPairBlock < hi; ++c)
@@ -506,6 +521,57 @@ __device__ __forceinline__ void put(int* __restrict__ tile_ent, float* __restric
     tile_key[j] = __uint_as_float((unsigned)(v >> 32));
 }
 
+// Bitonic network over 32 E keys held E per lane, key e * 32 + lane in v[e]:
+// partners closer than 32 are in other lanes (shuffles), farther ones in the
+// same lane (compare-exchange in registers).
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E], int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int je = j >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & je) == 0) {
+                        const bool up = ((e * 32 + lane) & k) == 0;
+                        const unsigned long long a = v[e], b = v[e + je];
+                        const bool sw = (a > b) == up;
+                        v[e] = sw ? b : a;
+                        v[e + je] = sw ? a : b;
+                    }
+                }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[e], j);
+                    const bool up = ((e * 32 + lane) & k) == 0;
+                    v[e] = (lower == up) ? (v[e] < o ? v[e] : o) : (v[e] < o ? o : v[e]);
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_list(const int* __restrict__ ent_tmp,
+                                               const float* __restrict__ key_tmp,
+                                               int* __restrict__ tile_ent, float* __restrict__ tile_key,
+                                               int b, int n, int lane)
+{
+    unsigned long long v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        v[e] = e * 32 + lane < n ? sort_key(key_tmp, ent_tmp, b + e * 32 + lane) : ~0ull;
+    warp_bitonic<E>(v, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (e * 32 + lane < n) put(tile_ent, tile_key, b + e * 32 + lane, v[e]);
+}
+
 // Short lists: one warp per tile.
 __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __restrict__ tile_ptr,
                                                                int n_tiles,
@@ -514,7 +580,6 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __rest
                                                                int* __restrict__ tile_ent,
                                                                float* __restrict__ tile_key)
 {
-    extern __shared__ unsigned long long s_warp_keys[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * kSortWarps + w;
     if (t >= n_tiles) return;
@@ -525,66 +590,10 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int* __rest
         if (lane == 0) { tile_ent[b] = ent_tmp[b]; tile_key[b] = key_tmp[b]; }
         return;
     }
-    if (n <= 32) {
-        unsigned long long v = lane < n ? sort_key(key_tmp, ent_tmp, b + lane) : ~0ull;
-#pragma unroll
-        for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
-                const bool up = (lane & k) == 0;
-                const bool lower = (lane & j) == 0;
-                v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
-            }
-        }
-        if (lane < n) put(tile_ent, tile_key, b + lane, v);
-        return;
-    }
-    if (n <= 64) {
-        // element lane in v0, element lane + 32 in v1
-        unsigned long long v0 = sort_key(key_tmp, ent_tmp, b + lane);
-        unsigned long long v1 = lane + 32 < n ? sort_key(key_tmp, ent_tmp, b + lane + 32) : ~0ull;
-#pragma unroll
-        for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                if (j == 32) {           // partners in the same lane (k = 64: ascending)
-                    const unsigned long long lo = v0 < v1 ? v0 : v1, hi = v0 < v1 ? v1 : v0;
-                    v0 = lo; v1 = hi;
-                } else {
-                    const unsigned long long o0 = __shfl_xor_sync(0xffffffffu, v0, j);
-                    const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, v1, j);
-                    const bool lower = (lane & j) == 0;
-                    const bool up0 = (lane & k) == 0;
-                    const bool up1 = ((lane + 32) & k) == 0;
-                    v0 = (lower == up0) ? (v0 < o0 ? v0 : o0) : (v0 < o0 ? o0 : v0);
-                    v1 = (lower == up1) ? (v1 < o1 ? v1 : o1) : (v1 < o1 ? o1 : v1);
-                }
-            }
-        }
-        put(tile_ent, tile_key, b + lane, v0);
-        if (lane + 32 < n) put(tile_ent, tile_key, b + lane + 32, v1);
-        return;
-    }
-    unsigned long long* s = s_warp_keys + (size_t)w * kWarpSortCap;
-    int N = 64;
-    while (N < n) N <<= 1;
-    for (int i = lane; i < N; i += 32) s[i] = i < n ? sort_key(key_tmp, ent_tmp, b + i) : ~0ull;
-    __syncwarp();
-    for (int k = 2; k <= N; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = lane; i < N; i += 32) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long x = s[i], y = s[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) { s[i] = y; s[ixj] = x; }
-                }
-            }
-            __syncwarp();
-        }
-    }
-    for (int i = lane; i < n; i += 32) put(tile_ent, tile_key, b + i, s[i]);
+    if (n <= 32) { warp_sort_list<1>(ent_tmp, key_tmp, tile_ent, tile_key, b, n, lane); return; }
+    if (n <= 64) { warp_sort_list<2>(ent_tmp, key_tmp, tile_ent, tile_key, b, n, lane); return; }
+    if (n <= 128) { warp_sort_list<4>(ent_tmp, key_tmp, tile_ent, tile_key, b, n, lane); return; }
+    warp_sort_list<8>(ent_tmp, key_tmp, tile_ent, tile_key, b, n, lane);
 }
 
 // Long lists: one CTA per tile (tiles with at most kWarpSortCap entries return at once).
@@ -730,15 +739,7 @@ extern "C" ps_status ps_bin_tiles(const ps_frame* frame, const ps_settings* s, c
                                                            frame->views, s->tile_w, s->tile_h, s->z_near,
                                                            w.chunk_first, nch);
         PS_LAUNCH_CHECK();
-        static int configured[64] = {0};   // dynamic shared memory attribute of k_sort_warp, per device
-        const int dyn = (int)(sizeof(unsigned long long) * kWarpSortCap * kSortWarps);
-        int dev = 0;
-        PS_CUDA_CHECK(cudaGetDevice(&dev));
-        if (dev < 0 || dev >= 64 || !configured[dev]) {
-            PS_CUDA_CHECK(cudaFuncSetAttribute(k_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
-            if (dev >= 0 && dev < 64) configured[dev] = 1;
-        }
-        k_sort_warp<<<(frame->n_tiles + kSortWarps - 1) / kSortWarps, kSortWarps * 32, dyn, st>>>(
+        k_sort_warp<<<(frame->n_tiles + kSortWarps - 1) / kSortWarps, kSortWarps * 32, 0, st>>>(
             tile_ptr, frame->n_tiles, w.ent_tmp, w.key_tmp, tile_ent, tile_key);
         PS_LAUNCH_CHECK();
         const int sort_blocks = (frame->n_tiles + 255) / 256;

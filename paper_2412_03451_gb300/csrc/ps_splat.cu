@@ -46,7 +46,7 @@ using namespace ps;
 namespace {
 
 #ifndef PS_KPEND
-#define PS_KPEND 5
+#define PS_KPEND 4
 #endif
 constexpr int kPend = PS_KPEND;           // pending-pair buffer per pixel
 constexpr unsigned kFull = 0xffffffffu;
