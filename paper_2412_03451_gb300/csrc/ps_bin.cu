@@ -42,6 +42,8 @@
 // no more latency than one covering a single tile.
 #include "ps_internal.cuh"
 
+#include <cooperative_groups.h>
+
 using namespace ps;
 
 namespace {
@@ -252,14 +254,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
     }
 }
 
-// Arrays of up to kScanOneMax elements: one CTA holds the whole array in
-// shared memory (one coalesced load pass with every load in flight), each
-// thread scans a contiguous run, a block scan joins the runs, one coalesced
-// store pass: one launch instead of three.  With `twice`, the array is first
-// replaced by its inclusive prefix (a difference array becomes the counts).
-// With chunk_first, the store pass also writes the chunk table of the pair
-// numbering (see k_chunk_first).  One launch runs one such job per CTA.
+// Arrays of up to kScanOneMax elements: one launch, one thread-block cluster
+// of kScanCtas CTAs per array.  Each CTA scans its own segment in shared memory
+// (each thread a contiguous run, a block scan joining the runs), publishes the
+// segment's aggregate in its shared memory, and after a cluster barrier reads
+// the aggregates of the lower-ranked CTAs through distributed shared memory to
+// get its carry.  With `twice`, the array is first replaced by its inclusive
+// prefix (a difference array becomes the counts): a segment's aggregate is then
+// (sum of its differences D, sum of its carry-free counts S, length L), and
+// segments compose in order as (D1 + D2, S1 + S2 + L2 D1, L1 + L2).  With
+// chunk_first, the store pass also writes the chunk table of the pair numbering
+// (see k_chunk_first).  One launch runs one or two such jobs (one cluster each).
 constexpr int kScanOneMax = 48 * 1024;
+constexpr int kScanCtas = 8;             // CTAs per cluster (the portable maximum)
 
 struct ScanJob {
     const int* in;
@@ -274,90 +281,100 @@ struct ScanJob {
     long long n_chunk;
 };
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_one(ScanJob j0, ScanJob j1)
+__global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads)
+k_scan_one(ScanJob j0, ScanJob j1)
 {
-    extern __shared__ int s_all[];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ int s_seg[];
     __shared__ long long s_warp[32];
-    const ScanJob& a = blockIdx.x == 0 ? j0 : j1;
+    __shared__ long long s_agg[3];
+    const int rank = (int)cl.block_rank();
+    const ScanJob& a = blockIdx.x < kScanCtas ? j0 : j1;
     const int n = a.n;
-    // 16-byte loads where the input allows them: fewer rounds of load latency
-    const int n4 = (reinterpret_cast<uintptr_t>(a.in) & 15) == 0 ? n >> 2 : 0;
-#pragma unroll 4
-    for (int j = threadIdx.x; j < n4; j += kScanThreads)
-        reinterpret_cast<int4*>(s_all)[j] = __ldg(reinterpret_cast<const int4*>(a.in) + j);
-    for (int j = 4 * n4 + threadIdx.x; j < n; j += kScanThreads) s_all[j] = a.in[j];
+    // segments of a multiple of 4 elements: 16-byte accesses stay aligned
+    const int seg = ((n + kScanCtas - 1) / kScanCtas + 3) & ~3;
+    const int lo = min(rank * seg, n), m = min(lo + seg, n) - lo;
+    const bool in_al = ((reinterpret_cast<uintptr_t>(a.in) | (size_t)lo * 4) & 15) == 0;
+    const int m4 = in_al ? m >> 2 : 0;
+    for (int j = threadIdx.x; j < m4; j += kScanThreads)
+        reinterpret_cast<int4*>(s_seg)[j] = __ldg(reinterpret_cast<const int4*>(a.in + lo) + j);
+    for (int j = 4 * m4 + threadIdx.x; j < m; j += kScanThreads) s_seg[j] = a.in[lo + j];
     __syncthreads();
     // contiguous runs of an odd length: the runs of a warp's threads start in 32
     // different banks, so the strided shared-memory passes below are conflict-free
-    const int per = ((n + kScanThreads - 1) / kScanThreads) | 1;
-    const int b = min((int)threadIdx.x * per, n), e = min(b + per, n);
+    const int per = ((m + kScanThreads - 1) / kScanThreads) | 1;
+    const int b = min((int)threadIdx.x * per, m), e = min(b + per, m);
+    long long D = 0;
     if (a.twice) {
         int run = 0;
-        for (int j = b; j < e; ++j) run += s_all[j];
-        long long tot;
-        long long c = block_scan_excl(run, s_warp, tot);
+        for (int j = b; j < e; ++j) run += s_seg[j];
+        long long c = block_scan_excl(run, s_warp, D);
         for (int j = b; j < e; ++j) {
-            c += s_all[j];
-            s_all[j] = (int)c;
+            c += s_seg[j];
+            s_seg[j] = (int)c;       // the count without the carry of the lower segments
         }
         __syncthreads();
     }
     long long sum = 0;
-    for (int j = b; j < e; ++j) sum += s_all[j];
-    long long total;
-    long long v = block_scan_excl(sum, s_warp, total);
+    for (int j = b; j < e; ++j) sum += s_seg[j];
+    long long S;
+    long long v = block_scan_excl(sum, s_warp, S);
+    if (threadIdx.x == 0) { s_agg[0] = D; s_agg[1] = S; s_agg[2] = m; }
+    cl.sync();
+    long long cD = 0, cC = 0;    // carries: differences and counts of the lower segments
+    for (int r = 0; r < rank; ++r) {
+        const long long* g = cl.map_shared_rank(s_agg, r);
+        cC += g[1] + g[2] * cD;
+        cD += g[0];
+    }
+    cl.sync();                   // every rank has read the aggregates before any exits
+    // offset of element j = cC + (j - lo) cD + (exclusive sum of the carry-free values)
+    v += cC + (long long)b * cD;
     for (int j = b; j < e; ++j) {
-        const int x = s_all[j];
-        s_all[j] = (int)(v < a.capacity ? v : a.capacity);
+        const long long x = s_seg[j] + cD;
+        s_seg[j] = (int)(v < a.capacity ? v : a.capacity);
         v += x;
     }
+    const long long seg_end = cC + (long long)m * cD + S;   // offset just past the segment
     __syncthreads();
-    const int last = (int)(total < a.capacity ? total : a.capacity);
-    const bool al = ((reinterpret_cast<uintptr_t>(a.out) | reinterpret_cast<uintptr_t>(a.cursor)) & 15) == 0;
-    const int m4 = al ? n >> 2 : 0;
-#pragma unroll 4
-    for (int j = threadIdx.x; j < m4; j += kScanThreads) {
-        const int4 x = reinterpret_cast<const int4*>(s_all)[j];
-        reinterpret_cast<int4*>(a.out)[j] = x;
-        if (a.cursor) reinterpret_cast<int4*>(a.cursor)[j] = x;
+    const long long cap_end = seg_end < a.capacity ? seg_end : a.capacity;
+    const bool out_al = ((reinterpret_cast<uintptr_t>(a.out) | reinterpret_cast<uintptr_t>(a.cursor) |
+                          (size_t)lo * 4) & 15) == 0;
+    const int s4 = out_al ? m >> 2 : 0;
+    for (int j = threadIdx.x; j < s4; j += kScanThreads) {
+        const int4 x = reinterpret_cast<const int4*>(s_seg)[j];
+        reinterpret_cast<int4*>(a.out + lo)[j] = x;
+        if (a.cursor) reinterpret_cast<int4*>(a.cursor + lo)[j] = x;
     }
-    for (int j = 4 * m4 + threadIdx.x; j < n; j += kScanThreads) {
-        const int x = s_all[j];
-        a.out[j] = x;
-        if (a.cursor) a.cursor[j] = x;
+    for (int j = 4 * s4 + threadIdx.x; j < m; j += kScanThreads) {
+        const int x = s_seg[j];
+        a.out[lo + j] = x;
+        if (a.cursor) a.cursor[lo + j] = x;
     }
     if (a.chunk_first) {
-        for (int j = threadIdx.x; j < n; j += kScanThreads) {
-            const int x = s_all[j];
-            const long long hi = j + 1 < n ? s_all[j + 1] : last;
+        for (int j = threadIdx.x; j < m; j += kScanThreads) {
+            const int x = s_seg[j];
+            const long long hi = j + 1 < m ? s_seg[j + 1] : cap_end;
             for (long long c = ((long long)x + kPairBlock - 1) / kPairBlock;
                  c < a.n_chunk && c * kPairBlock < hi; ++c)
-                a.chunk_first[c] = j;
+                a.chunk_first[c] = lo + j;
         }
     }
-    if (threadIdx.x == 0) {
-        a.out[n] = last;
-        if (a.d_total) *a.d_total = total;
-        if (a.status && total > a.capacity) set_status(a.status, PS_ERR_CAPACITY);
+    if (rank == kScanCtas - 1 && threadIdx.x == 0) {
+        a.out[n] = (int)cap_end;
+        if (a.d_total) *a.d_total = seg_end;
+        if (a.status && seg_end > a.capacity) set_status(a.status, PS_ERR_CAPACITY);
     }
 }
 
-// One or two single-CTA scans in one launch (both arrays <= kScanOneMax).
+// One or two cluster scans in one launch (both arrays <= kScanOneMax).
 cudaError_t scan_one(const ScanJob& j0, const ScanJob* j1, cudaStream_t st)
 {
-    static int configured[64] = {0};   // dynamic shared memory attribute, per device
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(k_scan_one, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(int) * kScanOneMax));
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) configured[dev] = 1;
-    }
     int n = j0.n > 0 ? j0.n : 1;
     if (j1 && j1->n > n) n = j1->n;
-    k_scan_one<<<j1 ? 2 : 1, kScanThreads, sizeof(int) * (size_t)n, st>>>(j0, j1 ? *j1 : j0);
+    const size_t seg = (size_t)((n + kScanCtas - 1) / kScanCtas + 3) & ~(size_t)3;
+    k_scan_one<<<(j1 ? 2 : 1) * kScanCtas, kScanThreads, sizeof(int) * seg, st>>>(j0, j1 ? *j1 : j0);
     return cudaGetLastError();
 }
 
