@@ -135,13 +135,17 @@ def scan_launches(n: int, twice: bool = False) -> int:
     return 6 if twice else 3
 
 
-def step_launches(n_records: int, n_tiles: int, fused: bool) -> int:
+def step_launches(n_records: int, n_tiles: int, fused: bool, graph: bool = True) -> int:
+    """Kernels of libps per optimisation step: schedule advance (graph only), projection,
+    binning (counts, scans, scatter, two sorts), splat (+ chain), Adam (one launch for all
+    parameters in the graph step, two eagerly)."""
     if 0 < n_records <= ONE_CTA_SCAN and n_tiles <= ONE_CTA_SCAN:
         scans = 1
     else:
         scans = (scan_launches(n_records) + 1 if n_records > 0 else 0) + scan_launches(n_tiles, True)
     binning = 1 + scans + 3
-    return (1 + 1 + binning + 2 + 2) if fused else (1 + binning + 4 + 2)
+    adam = 1 if graph else 2
+    return (int(graph) + 1 + binning + 2 + adam) if fused else (int(graph) + 1 + binning + 4 + adam)
 
 # DRAM bytes (read + write) and warp instructions (smsp__inst_executed.sum) per launch
 # of the fused splat kernel from the ncu captures summarised in
@@ -483,7 +487,7 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": round(wall, 4),
         "roofline": roofline, "clocks": clocks,
         "gpu_launches": step_launches(int(wl.r.frame.n_records), int(wl.r.frame.n_tiles),
-                                      wl.fit.fused) * args.steps,
+                                      wl.fit.fused, graph=use_graphs) * args.steps,
         "culling": {"tested_per_candidate": round(tested / max(cand, 1), 2)},
     }
 

@@ -427,10 +427,14 @@ ps_status ps_merge_planes(const float* params, int n_planes, const float* scene_
                           float max_angle_deg, float max_offset, int* group_of, int* rep_of_group,
                           int* d_groups, ps_stream stream);
 
-/* ps_adam_step with the step's bias corrections read from d_state (device). */
+/* ps_adam_step with the step's bias corrections read from d_state (device).
+   The clamp (unless clamp_min is NaN) applies to elements clamp_from .. n - 1
+   only, so that one launch updates a whole parameter block whose tail (the
+   radii) has a lower bound.  PS_ERR_ARG if clamp_from < 0 or n < 0. */
 ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v, long long n,
                              float lr, float b1, float b2, float eps,
-                             const ps_step_state* d_state, float clamp_min, ps_stream stream);
+                             const ps_step_state* d_state, float clamp_min, long long clamp_from,
+                             ps_stream stream);
 
 /* BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor memory)
    for the seed-proposal network (not part of the paper's renderer):

@@ -117,7 +117,7 @@ def load():
             "ps_seed_pool_bwd": ([P, I, I, I, P, P], I),
             "ps_seed_loss": ([P, P, I, I, P, P, P], I),
             "ps_cast_bf16": ([P, I, I, I, P, P], I),
-            "ps_adam_step_state": ([P, P, P, P, LL, F, F, F, F, P, F, P], I),
+            "ps_adam_step_state": ([P, P, P, P, LL, F, F, F, F, P, F, LL, P], I),
             "ps_radii_grad_accum": ([P, P, F, I, P, P], I),
             "ps_split_planes": ([P, P, P, I, P, I, P, I, F, P, P, P, P, I, P, P, P], I),
             "ps_merge_planes": ([P, I, P, F, F, P, P, P, P], I),
@@ -320,10 +320,11 @@ def ps_step_advance(d_state, d_sched, n_sched, d_iter, stream=None):
 
 
 def ps_adam_step_state(param, grad, m, v, lr, b1, b2, eps, d_state, clamp_min=float("nan"),
-                       stream=None):
+                       clamp_from=0, stream=None):
     _check(load().ps_adam_step_state(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
                                      float(lr), float(b1), float(b2), float(eps), _ptr(d_state),
-                                     float(clamp_min), _stream(stream)), "ps_adam_step_state")
+                                     float(clamp_min), int(clamp_from), _stream(stream)),
+           "ps_adam_step_state")
 
 
 def ps_radii_grad_accum(g_radii, acc, scale=1.0, plane_scale=None, stream=None):

@@ -424,21 +424,21 @@ __global__ void __launch_bounds__(256) k_chunk_first(const int* __restrict__ off
         chunk_first[c] = r;
 }
 
-// Pairs base .. base + kPairBlock - 1 of a block belong to records s_rng[0] ..
-// s_rng[1]: the chunk table gives the records holding this chunk's first pair
-// and the next chunk's (an upper bound); beyond the table two threads search
-// the whole record range.  The other threads search only that narrow range.
-__device__ __forceinline__ void block_record_range(const int* __restrict__ off, int R, int E,
-                                                   int base, const int* __restrict__ chunk_first,
-                                                   long long n_chunk, int* s_rng)
+// Pairs base .. base + kPairBlock - 1 of a block belong to records x .. y of the
+// result: the chunk table gives the records holding this chunk's first pair and
+// the next chunk's (an upper bound); beyond the table the whole record range is
+// searched.  Every thread of the block computes the same two values (broadcast
+// loads, no barrier) and then searches only that narrow range for its own pair.
+__device__ __forceinline__ int2 chunk_record_range(const int* __restrict__ off, int R, int E, int base,
+                                                   const int* __restrict__ chunk_first, long long n_chunk)
 {
-    if (threadIdx.x < 2) {
-        const long long c = base / kPairBlock + threadIdx.x;
-        const int i = threadIdx.x == 0 ? base : min(base + kPairBlock, E) - 1;
-        s_rng[threadIdx.x] = (c < n_chunk && c * kPairBlock < E) ? __ldg(&chunk_first[c])
-                                                                   : pair_record(off, 0, R - 1, i);
-    }
-    __syncthreads();
+    const long long c = base / kPairBlock;
+    const int lo = (c < n_chunk && c * kPairBlock < E) ? __ldg(&chunk_first[c])
+                                                       : pair_record(off, 0, R - 1, base);
+    const int hi = (c + 1 < n_chunk && (c + 1) * kPairBlock < E)
+                       ? __ldg(&chunk_first[c + 1])
+                       : pair_record(off, 0, R - 1, min(base + kPairBlock, E) - 1);
+    return make_int2(lo, hi);
 }
 
 // The entry key of the specification above.
@@ -494,13 +494,12 @@ __global__ void __launch_bounds__(kPairBlock) k_pair_scatter(const int* __restri
                                                        const int* __restrict__ chunk_first,
                                                        long long n_chunk)
 {
-    __shared__ int s_rng[2];
     const int E = __ldg(&rec_off[R]);
     for (int base = blockIdx.x * kPairBlock; base < E; base += gridDim.x * kPairBlock) {
-        block_record_range(rec_off, R, E, base, chunk_first, n_chunk, s_rng);
+        const int2 rg = chunk_record_range(rec_off, R, E, base, chunk_first, n_chunk);
         const int i = base + threadIdx.x;
         if (i < E) {
-            const int r = pair_record(rec_off, s_rng[0], s_rng[1], i);
+            const int r = pair_record(rec_off, rg.x, rg.y, i);
             const int4 info = __ldg(&rec_info[r]);
             const int j = i - __ldg(&rec_off[r]);
             const int t = info.x + (j / info.y) * info.z + (j % info.y);
@@ -519,7 +518,6 @@ __global__ void __launch_bounds__(kPairBlock) k_pair_scatter(const int* __restri
                 key_tmp[pos] = k;
             }
         }
-        __syncthreads();
     }
 }
 

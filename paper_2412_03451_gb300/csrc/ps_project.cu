@@ -312,7 +312,7 @@ __global__ void k_step_advance(ps_step_state* st, const ps_step_state* sched, in
 __global__ void k_adam_state(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                              float* __restrict__ v, long long n, float lr, float b1, float b2,
                              float eps, const ps_step_state* __restrict__ st, float clamp_min,
-                             int do_clamp)
+                             long long clamp_from)
 {
     const float bc1 = __ldg(&st->bc1), bc2 = __ldg(&st->bc2);
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -325,7 +325,7 @@ __global__ void k_adam_state(float* __restrict__ p, const float* __restrict__ g,
         v[i] = vi;
         const float mh = mi / bc1, vh = vi / bc2;
         float pi = p[i] - lr * mh / (sqrtf(vh) + eps);
-        if (do_clamp && pi < clamp_min) pi = clamp_min;
+        if (i >= clamp_from && pi < clamp_min) pi = clamp_min;
         p[i] = pi;
     }
 }
@@ -425,16 +425,17 @@ extern "C" ps_status ps_step_advance(ps_step_state* d_state, const ps_step_state
 extern "C" ps_status ps_adam_step_state(float* param, const float* grad, float* m, float* v,
                                         long long n, float lr, float b1, float b2, float eps,
                                         const ps_step_state* d_state, float clamp_min,
-                                        ps_stream stream)
+                                        long long clamp_from, ps_stream stream)
 {
-    if (n < 0 || !d_state) return PS_ERR_ARG;
+    if (n < 0 || !d_state || clamp_from < 0) return PS_ERR_ARG;
     if (n == 0) return PS_OK;
     if (!param || !grad || !m || !v) return PS_ERR_ARG;
-    const int do_clamp = isnan(clamp_min) ? 0 : 1;
+    // no clamp: a start past every element
+    if (isnan(clamp_min)) clamp_from = n;
     long long blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_adam_state<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        param, grad, m, v, n, lr, b1, b2, eps, d_state, clamp_min, do_clamp);
+        param, grad, m, v, n, lr, b1, b2, eps, d_state, clamp_min, clamp_from);
     PS_LAUNCH_CHECK();
     return PS_OK;
 }

@@ -385,10 +385,9 @@ class Fitter:
         self.grad.zero_()
         r.fused(self.flat, self.grad, gt_depth, gt_normal, view_sums=view_sums)
         self._accumulate(batch)
-        B.ps_adam_step_state(self.flat[:7 * P], self.grad[:7 * P], self.m[:7 * P], self.v[:7 * P],
-                             self.lr, self.b1, self.b2, self.eps, self.d_state)
-        B.ps_adam_step_state(self.flat[7 * P:], self.grad[7 * P:], self.m[7 * P:], self.v[7 * P:],
-                             self.lr, self.b1, self.b2, self.eps, self.d_state, clamp_min=R_MIN)
+        # one launch for all parameters; the radii (the last 4 P) are clamped below at R_MIN
+        B.ps_adam_step_state(self.flat, self.grad, self.m, self.v, self.lr, self.b1, self.b2, self.eps,
+                             self.d_state, clamp_min=R_MIN, clamp_from=7 * P)
 
     def replay(self, batch_index: int):
         """One optimisation step by graph replay (iteration counter on the device)."""
