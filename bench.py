@@ -150,12 +150,14 @@ def step_launches(n_records: int, n_tiles: int, fused: bool, graph: bool = True)
 # DRAM bytes (read + write) and warp instructions (smsp__inst_executed.sum) per launch
 # of the fused splat kernel from the ncu captures summarised in
 # profiles/k_splat_fused_room640_8x8_ite3.md (the benchmark's first lambda) and
-# .._ite1000.md (iteration 1,000 of the fit), keyed by the regime's iteration; reported
-# only while the kernel source is the one they were taken on.  The issue roof is
-# 152 SMs x 4 schedulers x one warp instruction per clock.
-CAPTURES = {"src_sha": "2eec71b5a47ed168",
-            "splat_fused": {0: {"dram_bytes": 51195904, "warp_instructions": 403849080},
-                            1000: {"dram_bytes": 44266496, "warp_instructions": 158483425}}}
+# .._ite1000.md, .._ite2000.md, .._ite4000.md (later points of the fit), keyed by the
+# regime's iteration; reported only while the kernel source is the one they were taken
+# on.  The issue roof is 152 SMs x 4 schedulers x one warp instruction per clock.
+CAPTURES = {"src_sha": "14ccebb7611eca05",
+            "splat_fused": {0: {"dram_bytes": 51164160, "warp_instructions": 396910440},
+                            1000: {"dram_bytes": 44220160, "warp_instructions": 154650296},
+                            2000: {"dram_bytes": 42901248, "warp_instructions": 124290616},
+                            4000: {"dram_bytes": 42440448, "warp_instructions": 111523963}}}
 SCHEDULERS_PER_SM = 4
 
 

@@ -45,7 +45,7 @@ def test_roofline_entry_arithmetic():
     assert abs(r["other_roofs"]["mufu"]["peak"] - 5.034) < 1e-3
     # profile-derived roofs apply only to the source they were measured on
     assert r["traffic"] is None and "issue" not in r["other_roofs"] and "hbm" not in r["other_roofs"]
-    for regime in (0, 1000):
+    for regime in (0, 1000, 2000, 4000):
         cap = bench.CAPTURES["splat_fused"][regime]
         r2 = bench.roofline_entry((5e8, 2e8, 1e8), {"splat_fused": [1.0] * 10}, 10, {"sm_max_mhz": 2070.0},
                                   bench.CAPTURES["src_sha"], {"hbm_gbs": 6790.0}, regime=regime)
@@ -54,7 +54,7 @@ def test_roofline_entry_arithmetic():
         assert abs(r2["other_roofs"]["hbm"]["achieved"] - cap["dram_bytes"] / 1e6) < 0.1
     # a regime without a capture reports no traffic
     r3 = bench.roofline_entry((5e8, 2e8, 1e8), {"splat_fused": [1.0] * 10}, 10, {"sm_max_mhz": 2070.0},
-                              bench.CAPTURES["src_sha"], {"hbm_gbs": 6790.0}, regime=4000)
+                              bench.CAPTURES["src_sha"], {"hbm_gbs": 6790.0}, regime=8000)
     assert r3["traffic"] is None
 
 
