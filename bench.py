@@ -197,6 +197,8 @@ def parse():
                     help="with --profile-case: fit this many iterations before the profiled step")
     ap.add_argument("--profile-case", action="store_true",
                     help="for ncu: set up, warm up 3 steps, run one step inside a profiler range, exit")
+    ap.add_argument("--stress", action="store_true",
+                    help="time the differentiation-stress room (10,000 planes, 256 views) and exit")
     ap.add_argument("--profile-gemm", action="store_true",
                     help="the seed network's tcgen05 GEMM (65,536 x 64 x 576): time it, then run one "
                          "inside a profiler range (for ncu), exit")
@@ -1027,6 +1029,65 @@ def profile_case(args):
     return 0 if status == 0 else 1
 
 
+def run_stress(args):
+    """The differentiation-stress configuration: one room with 10,000 planes and 256
+    views of 640x480 (78.6 M pixel-views) in one fused forward + loss + backward launch
+    per step, supervision from a hard-mode render of the ground-truth rectangles.
+    Times K fused steps (project, bin, fused kernel, by CUDA events, L2 flushed) at the
+    first lambda and at lambda 20, for 8x8 and 16x16 tiles."""
+    import statistics
+    import torch
+    import __graft_entry__
+    from paper_2412_03451_gb300 import binding as B
+    from paper_2412_03451_gb300 import scenes as S
+    from paper_2412_03451_gb300 import splat as SP
+    __graft_entry__.build()
+    dev = "cuda:0"
+    room = S.large_room(1300, n_rect=2000, n_views=256)
+    init = S.surface_init(room, 10000, seed=1301)
+    cams = room.cams
+    V = cams.V
+    gtr = SP.Renderer([H] * V, [W] * V, [0] * V, [0, room.gt.center.shape[0]], tile=(16, 16),
+                      device=dev, flags=B.PS_HARD)
+    gtr.set_cameras(cams.w2c, cams.intr)
+    gflat = SP.planes_to_flat(room.gt.center, room.gt.quat, room.gt.radii, dev)
+    gtr.ensure_capacity(gflat, 300.0)
+    gtr.forward(gflat, 300.0)
+    gd, gn = gtr.depth.clone(), gtr.normal.clone()
+    del gtr
+    flat = SP.planes_to_flat(init.center, init.quat, init.radii, dev)
+    g = torch.zeros_like(flat)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = []
+    for tile in ((8, 8), (16, 16)):
+        r = SP.Renderer([H] * V, [W] * V, [0] * V, [0, init.K], tile=tile, device=dev)
+        r.set_cameras(cams.w2c, cams.intr)
+        for lam in (B.lambda_schedule(0), 20.0):
+            r.ensure_capacity(flat, lam)
+            r.status.zero_()
+            ts = []
+            for i in range(args.steps + 1):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                r.project_bin(flat, lam)
+                r.fused(flat, g, gd, gn)
+                e1.record()
+                torch.cuda.synchronize()
+                if i > 0:
+                    ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            out.append({"tile": "%dx%d" % tile, "lambda": round(lam, 3), "ms_per_step": round(ms, 3),
+                        "mpixel_views_per_s": round(V * H * W / ms / 1e3, 1),
+                        "tile_entries": int(r.required), "status": int(r.status.item())})
+        del r
+        torch.cuda.empty_cache()
+    print(json.dumps({"stress": "10,000 planes, 256 views of %dx%d, fused forward + loss + backward" % (W, H),
+                      "runs": out}), flush=True)
+    return 0 if all(o["status"] == 0 for o in out) else 1
+
+
 def profile_gemm(args):
     """The seed network's inner-layer GEMM (im2col rows of 64 patches' 32x32
     outputs, 64 channels, K = 9 x 64): bf16 operands, FP32 output; 50 timed
@@ -1069,6 +1130,8 @@ def main():
         return profile_case(args)
     if args.profile_gemm:
         return profile_gemm(args)
+    if args.stress:
+        return run_stress(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
