@@ -112,6 +112,30 @@ def test_bins_bit_exact_beyond_one_scan_block(case):
     report("bins_large", case=case, n=n, entries=len(ent))
 
 
+def test_bins_bit_exact_every_sort_path():
+    # large planes over a small image: every tile list holds about as many entries as there
+    # are planes, so the cases reach each sort of the binning: one warp with 1, 2, 4 or 8
+    # keys per lane (up to 32, 64, 128, 256 entries), a CTA's shared-memory network (up to
+    # 4,096) and the rank sort beyond
+    seen = set()
+    for seed, n in ((41, 24), (42, 56), (43, 110), (44, 230), (45, 700), (46, 4600)):
+        p = S.random_planes_in_view(seed, n, depth_range=(1.0, 6.0), half=(3.0, 6.0))
+        cams = S.identity_cameras(2, 24, 40, 30.0, seed=seed, jitter=0.05)
+        g = gpu_run(p, cams, 20.0, tile=(8, 8))
+        rect, key32, ptr, ent, ekey = oracle_bins(p, cams, g["delta"], (8, 8))
+        assert g["status"] == 0
+        assert np.array_equal(g["tile_ptr"], ptr)
+        assert np.array_equal(g["tile_ent"], ent)
+        assert np.array_equal(g["tile_key"].view(np.uint32), ekey.view(np.uint32))
+        lens = np.diff(ptr)
+        for lo, hi, name in ((2, 32, "w1"), (33, 64, "w2"), (65, 128, "w4"), (129, 256, "w8"),
+                             (257, 4096, "cta"), (4097, 1 << 30, "rank")):
+            if ((lens >= lo) & (lens <= hi)).any():
+                seen.add(name)
+        report("bins_sort_paths", planes=n, longest=int(lens.max()))
+    assert seen == {"w1", "w2", "w4", "w8", "cta", "rank"}, seen
+
+
 def test_capacity_overflow_reports_required():
     room, init = tiny_init()
     g = gpu_run(init, room.cams, 20.0, capacity=100)
