@@ -95,6 +95,14 @@ def test_null_arguments_rejected_before_launch(lib):
                             None) == B.PS_ERR_ARG
     assert lib.ps_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, 0.0,
                             None) == B.PS_ERR_ARG
+    # the state form: no schedule, a negative clamp start, null parameter arrays
+    state = ctypes.create_string_buffer(64)
+    assert lib.ps_adam_step_state(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, None, 0.0, 0,
+                                  None) == B.PS_ERR_ARG
+    assert lib.ps_adam_step_state(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, state, 0.0, -1,
+                                  None) == B.PS_ERR_ARG
+    assert lib.ps_adam_step_state(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, state, 0.0, 0,
+                                  None) == B.PS_ERR_ARG
     assert B.ps_status_string(B.PS_ERR_CAPACITY) == "tile-list capacity exceeded"
 
 
