@@ -496,7 +496,10 @@ def run_ours(args, rank, world, local_rank):
     }
 
     if not args.no_e2e:
-        result["e2e"] = run_e2e(wl, args, first + args.steps, world)
+        # the same iterations as the headline, from the same state
+        wl.flat.copy_(saved[0]); wl.fit.m.copy_(saved[1]); wl.fit.v.copy_(saved[2])
+        wl.fit.ite = saved[3]
+        result["e2e"] = run_e2e(wl, args, first, world)
     cps = [int(x) for x in args.regimes.split(",") if x.strip()]
     if cps:
         result["regimes"] = run_regimes(wl, cps, args.steps, clocks, measured_peaks())
@@ -658,7 +661,8 @@ def run_e2e(wl, args, first, world):
     step's supervision into the other of two device buffers on a parallel branch
     (overlapping the step) and its loss sums to the host (Fitter.enable_graphs
     with host_stream); the first step's supervision is copied in the timed
-    region before the first replay."""
+    region before the first replay.  The caller restores the state at `first`,
+    so the same iterations as the device-resident measurement are timed."""
     import torch
     dev = wl.flat.device
     nb = N_VIEWS // VIEWS_PER_STEP
