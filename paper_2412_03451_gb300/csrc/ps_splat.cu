@@ -45,10 +45,15 @@ using namespace ps;
 
 namespace {
 
+// Pending-pair buffer per pixel: 4 deep for the rectangle weight (its opaque pairs cut
+// the lists early; 4 was 1-2.4% faster than 5 and up to 3.7% faster than 3), 6 deep for
+// the Eq. 5 weight, where every pair is partly transparent and more of them wait for the
+// list keys to pass (6 was 13% faster than 4 there).
 #ifndef PS_KPEND
 #define PS_KPEND 4
 #endif
-constexpr int kPend = PS_KPEND;           // pending-pair buffer per pixel
+constexpr int kPendRect = PS_KPEND;
+constexpr int kPendGauss = 6;
 constexpr unsigned kFull = 0xffffffffu;
 // Warps per CTA of the splat kernels (ps_settings.cta_warps: 2, 4 or 8; 0 means 4).
 // Each warp stages 32 plane records of its tile list per shared-memory batch, so a
@@ -128,24 +133,27 @@ __device__ __forceinline__ float key_t(CKey k) { return __uint_as_float((unsigne
 __device__ __forceinline__ int key_id(CKey k) { return (int)(unsigned)(k & 0xffffffffu); }
 
 // Per-pixel walk state.
+template <int KP>
 struct Walk {
     float T;
     int cnt;
     bool done;
     int nb;
-    CKey bk[kPend];   // pending candidates, ascending
-    float bw[kPend];
+    CKey bk[KP];      // pending candidates, ascending
+    float bw[KP];
     CKey floor_;      // last composited candidate (0: none yet)
     CKey ovf;         // smallest candidate dropped from a full buffer (kNoKey: none)
     CKey cut;         // nearest opaque (w = 1) candidate, or the M-th candidate (kNoKey: none)
 };
 
-__device__ __forceinline__ void drop_note(Walk& s, CKey k)
+template <int KP>
+__device__ __forceinline__ void drop_note(Walk<KP>& s, CKey k)
 {
     if (k < s.ovf) s.ovf = k;
 }
 
-__device__ __forceinline__ void set_cut(Walk& s, CKey k)
+template <int KP>
+__device__ __forceinline__ void set_cut(Walk<KP>& s, CKey k)
 {
     if (k < s.cut) s.cut = k;
     // pairs dropped from a full buffer that lie strictly behind the cut can never count
@@ -157,17 +165,18 @@ __device__ __forceinline__ void set_cut(Walk& s, CKey k)
 // opaque candidate becomes the cut and truncates the pending pairs behind it;
 // when composited + pending exceeds M the largest pending pair is beyond the
 // top M and goes, and the new M-th pair becomes the cut.
-__device__ __forceinline__ void pend_insert(Walk& s, CKey key, float w, int M)
+template <int KP>
+__device__ __forceinline__ void pend_insert(Walk<KP>& s, CKey key, float w, int M)
 {
     if (s.cut < key) return;     // strictly behind the cut
-    if (s.nb == kPend) {
-        if (!(key < s.bk[kPend - 1])) { drop_note(s, key); return; }
-        drop_note(s, s.bk[kPend - 1]);
-        s.nb = kPend - 1;
+    if (s.nb == KP) {
+        if (!(key < s.bk[KP - 1])) { drop_note(s, key); return; }
+        drop_note(s, s.bk[KP - 1]);
+        s.nb = KP - 1;
     }
     int pos = 0;
 #pragma unroll
-    for (int i = kPend - 1; i >= 1; --i) {
+    for (int i = KP - 1; i >= 1; --i) {
         if (i <= s.nb) {
             if (key < s.bk[i - 1]) {
                 s.bk[i] = s.bk[i - 1]; s.bw[i] = s.bw[i - 1];
@@ -186,16 +195,17 @@ __device__ __forceinline__ void pend_insert(Walk& s, CKey key, float w, int M)
         s.nb = M - s.cnt;
         CKey lk = s.bk[0];
 #pragma unroll
-        for (int i = 1; i < kPend; ++i)
+        for (int i = 1; i < KP; ++i)
             if (i < s.nb) lk = s.bk[i];
         set_cut(s, lk);
     }
 }
 
-__device__ __forceinline__ void pend_pop(Walk& s)
+template <int KP>
+__device__ __forceinline__ void pend_pop(Walk<KP>& s)
 {
 #pragma unroll
-    for (int i = 0; i < kPend - 1; ++i) {
+    for (int i = 0; i < KP - 1; ++i) {
         s.bk[i] = s.bk[i + 1]; s.bw[i] = s.bw[i + 1];
     }
     --s.nb;
@@ -213,8 +223,8 @@ struct Sink {
     int2* stk;        // this lane's column of the warp's stack [M][32]
 };
 
-template <int MODE>
-__device__ __forceinline__ void composite(Walk& s, Sink& k, const float4& n, float t, float w, int id,
+template <int MODE, int KP>
+__device__ __forceinline__ void composite(Walk<KP>& s, Sink& k, const float4& n, float t, float w, int id,
                                           int M)
 {
     if constexpr (MODE != kFwd) k.stk[s.cnt * 32] = make_int2(id, __float_as_int(s.T));
@@ -233,8 +243,8 @@ __device__ __forceinline__ void composite(Walk& s, Sink& k, const float4& n, flo
     if (s.cnt >= M || s.T == 0.f) s.done = true;
 }
 
-template <int MODE>
-__device__ __forceinline__ void flush(Walk& s, Sink& k, const float4* __restrict__ rec,
+template <int MODE, int KP>
+__device__ __forceinline__ void flush(Walk<KP>& s, Sink& k, const float4* __restrict__ rec,
                                       float bound, int M)
 {
     // every later candidate lies behind the cut: nothing else can enter (no cut: NaN, false)
@@ -254,8 +264,8 @@ __device__ __forceinline__ void flush(Walk& s, Sink& k, const float4* __restrict
 }
 
 // Walks one tile list for the warp's 32 pixels.
-template <int MODE>
-__device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Walk& s,
+template <int MODE, int KP>
+__device__ __forceinline__ void walk_strip(const SplatArgs& a, WarpStage& ws, Walk<KP>& s,
                                            Sink& k, float dx, float dy, const WarpRegion& g,
                                            int beg, int end)
 {
@@ -370,7 +380,7 @@ struct StripLoss {
     float sc, sl, sd, one;
 };
 
-template <int TW, int TH, int MODE>
+template <int TW, int TH, int MODE, int KP>
 __device__ __forceinline__ StripLoss run_strip(const SplatArgs& a, WarpStage& ws, int2* stk_warp,
                                                int item)
 {
@@ -407,7 +417,7 @@ __device__ __forceinline__ StripLoss run_strip(const SplatArgs& a, WarpStage& ws
     const int beg = (int)min((long long)__ldg(&a.tile_ptr[tile]), a.capacity);
     const int end = (int)min((long long)__ldg(&a.tile_ptr[tile + 1]), a.capacity);
 
-    Walk s;
+    Walk<KP> s;
     s.T = 1.f; s.cnt = 0; s.nb = 0;
     s.floor_ = 0ull; s.ovf = kNoKey; s.cut = kNoKey;
     s.done = !inside;
@@ -615,7 +625,7 @@ __device__ __forceinline__ void load_state(SplatArgs& a)
     }
 }
 
-template <int TW, int TH, int MODE, int NW>
+template <int TW, int TH, int MODE, int NW, int KP>
 __global__ void __launch_bounds__(NW * 32, min_blocks(MODE, NW)) k_splat(SplatArgs a_in)
 {
     SplatArgs a = a_in;
@@ -652,7 +662,7 @@ __global__ void __launch_bounds__(NW * 32, min_blocks(MODE, NW)) k_splat(SplatAr
         if (lane == 0) item = atomicAdd(a.counter, 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= a.n_items) break;
-        const StripLoss sl = run_strip<TW, TH, MODE>(a, stage[w], stk_warp, item);
+        const StripLoss sl = run_strip<TW, TH, MODE, KP>(a, stage[w], stk_warp, item);
         if constexpr (MODE == kFused) {
             if (sl.v != vcur) {
                 if (vcur >= 0) flush_loss();
@@ -929,7 +939,7 @@ struct LaunchCache {
     size_t dyn = 0;
 };
 
-template <int TW, int TH, int MODE, int NW>
+template <int TW, int TH, int MODE, int NW, int KP>
 cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool counter_zeroed)
 {
     constexpr int NS = TW * TH / 32;
@@ -943,12 +953,12 @@ cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool 
     if (c.dev != dev || c.dyn != dyn) {
         if (dyn > 0) {
             // static + dynamic shared memory above 48 KB needs the opt-in
-            e = cudaFuncSetAttribute(k_splat<TW, TH, MODE, NW>,
+            e = cudaFuncSetAttribute(k_splat<TW, TH, MODE, NW, KP>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
             if (e != cudaSuccess) return e;
         }
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_splat<TW, TH, MODE, NW>, NW * 32, dyn);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_splat<TW, TH, MODE, NW, KP>, NW * 32, dyn);
         if (e != cudaSuccess) return e;
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -965,7 +975,7 @@ cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool 
         e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
-    k_splat<TW, TH, MODE, NW><<<blocks, NW * 32, dyn, st>>>(a);
+    k_splat<TW, TH, MODE, NW, KP><<<blocks, NW * 32, dyn, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1003,23 +1013,31 @@ SplatConst make_const(const ps_settings* s)
     return c;
 }
 
-template <int MODE, int NW>
+template <int MODE, int NW, int KP>
 cudaError_t dispatch_tile(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
                           bool counter_zeroed)
 {
-    if (s->tile_w == 16) return launch_splat<16, 16, MODE, NW>(a, n_tiles, s->M, st, counter_zeroed);
-    if (s->tile_w == 8) return launch_splat<8, 8, MODE, NW>(a, n_tiles, s->M, st, counter_zeroed);
-    return launch_splat<32, 8, MODE, NW>(a, n_tiles, s->M, st, counter_zeroed);
+    if (s->tile_w == 16) return launch_splat<16, 16, MODE, NW, KP>(a, n_tiles, s->M, st, counter_zeroed);
+    if (s->tile_w == 8) return launch_splat<8, 8, MODE, NW, KP>(a, n_tiles, s->M, st, counter_zeroed);
+    return launch_splat<32, 8, MODE, NW, KP>(a, n_tiles, s->M, st, counter_zeroed);
+}
+
+template <int MODE, int KP>
+cudaError_t dispatch_warps(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
+                           bool counter_zeroed)
+{
+    const int nw = s->cta_warps ? s->cta_warps : kDefaultWarps;
+    if (nw == 2) return dispatch_tile<MODE, 2, KP>(a, s, n_tiles, st, counter_zeroed);
+    if (nw == 8) return dispatch_tile<MODE, 8, KP>(a, s, n_tiles, st, counter_zeroed);
+    return dispatch_tile<MODE, 4, KP>(a, s, n_tiles, st, counter_zeroed);
 }
 
 template <int MODE>
 cudaError_t dispatch(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
                      bool counter_zeroed = false)
 {
-    const int nw = s->cta_warps ? s->cta_warps : kDefaultWarps;
-    if (nw == 2) return dispatch_tile<MODE, 2>(a, s, n_tiles, st, counter_zeroed);
-    if (nw == 8) return dispatch_tile<MODE, 8>(a, s, n_tiles, st, counter_zeroed);
-    return dispatch_tile<MODE, 4>(a, s, n_tiles, st, counter_zeroed);
+    if (s->flags & PS_GAUSSIAN) return dispatch_warps<MODE, kPendGauss>(a, s, n_tiles, st, counter_zeroed);
+    return dispatch_warps<MODE, kPendRect>(a, s, n_tiles, st, counter_zeroed);
 }
 
 template <int TW, int TH>
