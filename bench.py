@@ -153,11 +153,11 @@ def step_launches(n_records: int, n_tiles: int, fused: bool, graph: bool = True)
 # .._ite1000.md, .._ite2000.md, .._ite4000.md (later points of the fit), keyed by the
 # regime's iteration; reported only while the kernel source is the one they were taken
 # on.  The issue roof is 152 SMs x 4 schedulers x one warp instruction per clock.
-CAPTURES = {"src_sha": "14ccebb7611eca05",
-            "splat_fused": {0: {"dram_bytes": 51164160, "warp_instructions": 396910440},
-                            1000: {"dram_bytes": 44220160, "warp_instructions": 154650296},
-                            2000: {"dram_bytes": 42901248, "warp_instructions": 124290616},
-                            4000: {"dram_bytes": 42440448, "warp_instructions": 111523963}}}
+CAPTURES = {"src_sha": "b714d7b252343723",
+            "splat_fused": {0: {"dram_bytes": 51161344, "warp_instructions": 396911532},
+                            1000: {"dram_bytes": 44231680, "warp_instructions": 154583250},
+                            2000: {"dram_bytes": 42896128, "warp_instructions": 123997305},
+                            4000: {"dram_bytes": 42449408, "warp_instructions": 111515444}}}
 SCHEDULERS_PER_SM = 4
 
 
