@@ -153,11 +153,11 @@ def step_launches(n_records: int, n_tiles: int, fused: bool, graph: bool = True)
 # .._ite1000.md, .._ite2000.md, .._ite4000.md (later points of the fit), keyed by the
 # regime's iteration; reported only while the kernel source is the one they were taken
 # on.  The issue roof is 152 SMs x 4 schedulers x one warp instruction per clock.
-CAPTURES = {"src_sha": "b714d7b252343723",
-            "splat_fused": {0: {"dram_bytes": 51161344, "warp_instructions": 396911532},
-                            1000: {"dram_bytes": 44231680, "warp_instructions": 154583250},
-                            2000: {"dram_bytes": 42896128, "warp_instructions": 123997305},
-                            4000: {"dram_bytes": 42449408, "warp_instructions": 111515444}}}
+CAPTURES = {"src_sha": "f57b7307b034ad09",
+            "splat_fused": {0: {"dram_bytes": 51238656, "warp_instructions": 392692133},
+                            1000: {"dram_bytes": 44233728, "warp_instructions": 152681978},
+                            2000: {"dram_bytes": 42898176, "warp_instructions": 122084604},
+                            4000: {"dram_bytes": 42422784, "warp_instructions": 109970373}}}
 SCHEDULERS_PER_SM = 4
 
 

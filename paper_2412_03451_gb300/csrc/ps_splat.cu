@@ -625,10 +625,14 @@ __device__ __forceinline__ void load_state(SplatArgs& a)
     }
 }
 
-template <int TW, int TH, int MODE, int NW, int KP>
+// G: the weight form of the instantiation (0: Eq. 7-9 rectangle weight, 1: Eq. 5 Gaussian),
+// fixed at compile time so that the other form's branches fold away.
+template <int TW, int TH, int MODE, int NW, int G>
 __global__ void __launch_bounds__(NW * 32, min_blocks(MODE, NW)) k_splat(SplatArgs a_in)
 {
+    constexpr int KP = G ? kPendGauss : kPendRect;
     SplatArgs a = a_in;
+    a.c.gauss = G;
     load_state(a);
     __shared__ WarpStage stage[NW];
     extern __shared__ int2 dyn_stk[];       // backward: [NW][M][32]
@@ -939,7 +943,7 @@ struct LaunchCache {
     size_t dyn = 0;
 };
 
-template <int TW, int TH, int MODE, int NW, int KP>
+template <int TW, int TH, int MODE, int NW, int G>
 cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool counter_zeroed)
 {
     constexpr int NS = TW * TH / 32;
@@ -953,12 +957,12 @@ cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool 
     if (c.dev != dev || c.dyn != dyn) {
         if (dyn > 0) {
             // static + dynamic shared memory above 48 KB needs the opt-in
-            e = cudaFuncSetAttribute(k_splat<TW, TH, MODE, NW, KP>,
+            e = cudaFuncSetAttribute(k_splat<TW, TH, MODE, NW, G>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
             if (e != cudaSuccess) return e;
         }
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_splat<TW, TH, MODE, NW, KP>, NW * 32, dyn);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_splat<TW, TH, MODE, NW, G>, NW * 32, dyn);
         if (e != cudaSuccess) return e;
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -975,7 +979,7 @@ cudaError_t launch_splat(SplatArgs a, int n_tiles, int M, cudaStream_t st, bool 
         e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
-    k_splat<TW, TH, MODE, NW, KP><<<blocks, NW * 32, dyn, st>>>(a);
+    k_splat<TW, TH, MODE, NW, G><<<blocks, NW * 32, dyn, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1013,31 +1017,31 @@ SplatConst make_const(const ps_settings* s)
     return c;
 }
 
-template <int MODE, int NW, int KP>
+template <int MODE, int NW, int G>
 cudaError_t dispatch_tile(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
                           bool counter_zeroed)
 {
-    if (s->tile_w == 16) return launch_splat<16, 16, MODE, NW, KP>(a, n_tiles, s->M, st, counter_zeroed);
-    if (s->tile_w == 8) return launch_splat<8, 8, MODE, NW, KP>(a, n_tiles, s->M, st, counter_zeroed);
-    return launch_splat<32, 8, MODE, NW, KP>(a, n_tiles, s->M, st, counter_zeroed);
+    if (s->tile_w == 16) return launch_splat<16, 16, MODE, NW, G>(a, n_tiles, s->M, st, counter_zeroed);
+    if (s->tile_w == 8) return launch_splat<8, 8, MODE, NW, G>(a, n_tiles, s->M, st, counter_zeroed);
+    return launch_splat<32, 8, MODE, NW, G>(a, n_tiles, s->M, st, counter_zeroed);
 }
 
-template <int MODE, int KP>
+template <int MODE, int G>
 cudaError_t dispatch_warps(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
                            bool counter_zeroed)
 {
     const int nw = s->cta_warps ? s->cta_warps : kDefaultWarps;
-    if (nw == 2) return dispatch_tile<MODE, 2, KP>(a, s, n_tiles, st, counter_zeroed);
-    if (nw == 8) return dispatch_tile<MODE, 8, KP>(a, s, n_tiles, st, counter_zeroed);
-    return dispatch_tile<MODE, 4, KP>(a, s, n_tiles, st, counter_zeroed);
+    if (nw == 2) return dispatch_tile<MODE, 2, G>(a, s, n_tiles, st, counter_zeroed);
+    if (nw == 8) return dispatch_tile<MODE, 8, G>(a, s, n_tiles, st, counter_zeroed);
+    return dispatch_tile<MODE, 4, G>(a, s, n_tiles, st, counter_zeroed);
 }
 
 template <int MODE>
 cudaError_t dispatch(const SplatArgs& a, const ps_settings* s, int n_tiles, cudaStream_t st,
                      bool counter_zeroed = false)
 {
-    if (s->flags & PS_GAUSSIAN) return dispatch_warps<MODE, kPendGauss>(a, s, n_tiles, st, counter_zeroed);
-    return dispatch_warps<MODE, kPendRect>(a, s, n_tiles, st, counter_zeroed);
+    if (s->flags & PS_GAUSSIAN) return dispatch_warps<MODE, 1>(a, s, n_tiles, st, counter_zeroed);
+    return dispatch_warps<MODE, 0>(a, s, n_tiles, st, counter_zeroed);
 }
 
 template <int TW, int TH>
