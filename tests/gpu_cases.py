@@ -146,13 +146,13 @@ def grad_errors(g_gpu, g_or, rel=1e-3, floor=1e-6):
 
 
 def gpu_fused_vs_split(planes: S.Planes, cams: S.Cameras, lam: float, gt_depth, gt_normal,
-                       tile=(16, 16), M=30):
+                       tile=(16, 16), M=30, flags=0):
     """Runs the fused forward+loss+backward and the separate fwd -> loss -> bwd
     calls on the same inputs; returns both results as numpy arrays."""
     import torch
     from paper_2412_03451_gb300 import splat as SP
     V = cams.V
-    r = SP.Renderer([cams.H] * V, [cams.W] * V, [0] * V, [0, planes.K], tile=tile, M=M)
+    r = SP.Renderer([cams.H] * V, [cams.W] * V, [0] * V, [0, planes.K], tile=tile, M=M, flags=flags)
     r.set_cameras(cams.w2c, cams.intr)
     flat = SP.planes_to_flat(planes.center, planes.quat, planes.radii, "cuda")
     r.ensure_capacity(flat, lam)

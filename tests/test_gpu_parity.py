@@ -448,13 +448,18 @@ def test_paper_scale_fused_equals_separate_kernels(big_case):
     report("fused_vs_split_big", views=int(cams.V), planes=int(K))
 
 
-@pytest.mark.parametrize("lam,tile", [(20.0 / np.e, (16, 16)), (20.0, (8, 8)), (300.0, (32, 8))])
-def test_fused_equals_separate_kernels(lam, tile):
+@pytest.mark.parametrize("lam,tile,gauss", [(20.0 / np.e, (16, 16), False), (20.0, (8, 8), False),
+                                            (300.0, (32, 8), False), (20.0, (8, 8), True)])
+def test_fused_equals_separate_kernels(lam, tile, gauss):
+    # each weight form has its own kernel instantiations (the Eq. 5 weight with its deeper
+    # pending buffer): both are checked
     from gpu_cases import gpu_fused_vs_split
+    from paper_2412_03451_gb300 import binding as B
     room, init = tiny_init()
     D, N, _ = O.raycast(room.gt.center, room.gt.quat, room.gt.radii, room.cams.w2c,
                         room.cams.intr, room.cams.H, room.cams.W)
-    sp, fu, status = gpu_fused_vs_split(init, room.cams, lam, D, N, tile=tile)
+    sp, fu, status = gpu_fused_vs_split(init, room.cams, lam, D, N, tile=tile,
+                                        flags=B.PS_GAUSSIAN if gauss else 0)
     assert status == 0
     # same walk, same arithmetic: maps and loss gradients are identical
     assert np.array_equal(sp["depth"], fu["depth"]) and np.array_equal(sp["normal"], fu["normal"])
@@ -465,7 +470,7 @@ def test_fused_equals_separate_kernels(lam, tile):
     for a, b in ((0, 3 * K), (3 * K, 7 * K), (7 * K, 11 * K)):
         gs, gf = sp["grad"][a:b], fu["grad"][a:b]
         assert np.linalg.norm(gs - gf) <= 1e-5 * np.linalg.norm(gs) + 1e-6
-    report("fused_vs_split", lam=lam, tile=tile)
+    report("fused_vs_split", lam=lam, tile=tile, gauss=gauss)
 
 
 @pytest.mark.parametrize("lam", [20.0 / np.e, 20.0])
